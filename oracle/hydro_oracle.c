@@ -1,0 +1,584 @@
+/*
+ * hydro_oracle.c -- plain, slow FP64 CPU oracle of the second-order
+ * compressible-Euler step of Paraiso (Muranushi, arXiv:1204.4779, section 4.1
+ * "The Target Program").
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the independent reference that the
+ * CUDA path is checked against.  Only tests/, __graft_entry__.smoke() and the
+ * CPU-baseline leg of bench.py may load it.  It shares no code, header, table or
+ * constant with the CUDA library: every formula below is written out here, from
+ * the paper, in the paper's order.
+ *
+ * Compile: gcc -O2 -ffp-contract=off [-fopenmp] -shared -fPIC (no fast-math), so
+ * every operation is one IEEE-754 round-to-nearest operation.
+ *
+ * Layout of the arrays passed in and out: structure of arrays, dim+2 planes
+ * (rho, m_0..m_{dim-1}, E) or (rho, v_0..v_{dim-1}, p), each plane n0*n1*n2
+ * doubles with axis 0 (x) fastest.  Inactive axes have n = 1.
+ *
+ * Readings of the paper used here (the paper is silent or garbled on them):
+ *  - flux row 1 is the mass flux rho*v_a and the PDE is dU/dt + d_a F_a = 0;
+ *    the sign of AddFlux (Eq. eqAddFlux) is the conservative one and is used.
+ *  - HLLC (cited, not written out, section 4.1): Davis wave-speed estimates
+ *    S_L = min(u_L - a_L, u_R - a_R), S_R = max(u_L + a_L, u_R + a_R); the
+ *    contact speed S* and the star states of Toro, Spruce & Speares (1994).
+ *    Branch tie-breaks: F_L if S_L >= 0, F*_L if S* >= 0, F*_R if S_R > 0,
+ *    else F_R.
+ *  - CFL (section 4.1 says only "determined by the CFL condition"):
+ *    dt = CFL / max_i sum_a (|v_a| + c_s) / dr_a, c_s = sqrt(gamma p / rho),
+ *    evaluated on the state at the start of the RK step and used by both stages.
+ *  - Interpolate (Eq. eqInterpolateSingle): dy = 0 if dy01*dy12 < 0, dy01 if
+ *    |dy01| < |dy12|, dy12 otherwise, applied to the primitive variables V
+ *    along the face normal only (Eq. eqInterpolateV).
+ *  - Boundaries: periodic wrap, or outflow = zero-gradient copy of the nearest
+ *    interior cell, into two ghost layers, refilled before every stage.
+ *  - Time: the last step is clipped so that t lands on t_end; a clipped step
+ *    sets t = t_end exactly.
+ *  - No positivity floors.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define NG 2 /* ghost layers per side on every active axis */
+
+enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_ENOMEM = 2, ORC_ENONFINITE = 3 };
+
+typedef struct {
+    int dim;         /* 1, 2 or 3 */
+    long n[3];       /* interior cells per axis (1 on inactive axes) */
+    long p[3];       /* padded extent per axis: n + 2*NG on active axes */
+    long g[3];       /* ghost offset per axis: NG on active axes, else 0 */
+    double dr[3];    /* cell size per axis */
+    double gamma;
+    int bc[3];       /* 0 periodic, 1 outflow */
+    long ncell;      /* interior cells */
+    long npad;       /* padded cells */
+} grid_t;
+
+static int make_grid(grid_t *G, int dim, const long n[3], const double dr[3],
+                     double gamma, const int bc[3]) {
+    if (dim < 1 || dim > 3 || !(gamma > 1.0)) return ORC_EINVAL;
+    memset(G, 0, sizeof *G);
+    G->dim = dim;
+    G->gamma = gamma;
+    G->ncell = 1;
+    G->npad = 1;
+    for (int a = 0; a < 3; ++a) {
+        int active = a < dim;
+        G->n[a] = active ? n[a] : 1;
+        if (G->n[a] < 1) return ORC_EINVAL;
+        G->g[a] = active ? NG : 0;
+        G->p[a] = G->n[a] + 2 * G->g[a];
+        G->dr[a] = active ? dr[a] : 1.0;
+        if (active && !(dr[a] > 0.0)) return ORC_EINVAL;
+        G->bc[a] = active ? bc[a] : 0;
+        G->ncell *= G->n[a];
+        G->npad *= G->p[a];
+    }
+    return ORC_OK;
+}
+
+/* linear index of interior coordinate (i0,i1,i2), ghosts at negative / >= n */
+static long pidx(const grid_t *G, long i0, long i1, long i2) {
+    return ((i2 + G->g[2]) * G->p[1] + (i1 + G->g[1])) * G->p[0] + (i0 + G->g[0]);
+}
+
+static long wrap(long i, long n) {
+    long r = i % n;
+    return r < 0 ? r + n : r;
+}
+
+/* ---------------------------------------------------------------- ghosts -- */
+
+/* Fill the NG ghost layers of one padded array along every active axis, axis
+ * by axis; each pass covers the full padded extent of the other axes. */
+static void fill_ghosts(const grid_t *G, double *q) {
+    for (int a = 0; a < G->dim; ++a) {
+        long lo[3], hi[3];
+        for (int b = 0; b < 3; ++b) {
+            lo[b] = -G->g[b];
+            hi[b] = G->n[b] + G->g[b];
+        }
+        for (long i2 = lo[2]; i2 < hi[2]; ++i2)
+            for (long i1 = lo[1]; i1 < hi[1]; ++i1)
+                for (long i0 = lo[0]; i0 < hi[0]; ++i0) {
+                    long c[3] = {i0, i1, i2};
+                    long ia = c[a];
+                    if (ia >= 0 && ia < G->n[a]) continue;
+                    long src[3] = {i0, i1, i2};
+                    if (G->bc[a] == 0)
+                        src[a] = wrap(ia, G->n[a]);
+                    else
+                        src[a] = ia < 0 ? 0 : G->n[a] - 1;
+                    q[pidx(G, i0, i1, i2)] = q[pidx(G, src[0], src[1], src[2])];
+                }
+    }
+}
+
+/* ------------------------------------------------- variables (Eqs. 1-2) -- */
+
+/* V(U): v_a = m_a / rho, p = (gamma-1) (E - 1/2 rho v^2)  (section 4.1) */
+static void prim_of_cons(int dim, double gamma, const double *U, double *V) {
+    double rho = U[0];
+    double kin = 0.0;
+    V[0] = rho;
+    for (int a = 0; a < dim; ++a) {
+        V[1 + a] = U[1 + a] / rho;
+        kin += U[1 + a] * V[1 + a];
+    }
+    V[dim + 1] = (gamma - 1.0) * (U[dim + 1] - 0.5 * kin);
+}
+
+/* U(V): m_a = rho v_a, E = p/(gamma-1) + 1/2 rho v^2  (section 4.1) */
+static void cons_of_prim(int dim, double gamma, const double *V, double *U) {
+    double rho = V[0];
+    double v2 = 0.0;
+    U[0] = rho;
+    for (int a = 0; a < dim; ++a) {
+        U[1 + a] = rho * V[1 + a];
+        v2 += V[1 + a] * V[1 + a];
+    }
+    U[dim + 1] = V[dim + 1] / (gamma - 1.0) + 0.5 * rho * v2;
+}
+
+/* Euler flux along normal axis a of primitive state V (section 4.1, F_a):
+ * (rho v_a, rho v_a v_b + p delta_ab, v_a (E + p)) */
+static void euler_flux(int dim, int a, double gamma, const double *V, double *F) {
+    double U[5];
+    cons_of_prim(dim, gamma, V, U);
+    double un = V[1 + a];
+    double p = V[dim + 1];
+    F[0] = U[0] * un;
+    for (int b = 0; b < dim; ++b) F[1 + b] = U[1 + b] * un + (b == a ? p : 0.0);
+    F[dim + 1] = un * (U[dim + 1] + p);
+}
+
+/* ------------------------------------- Interpolate, Eq. eqInterpolateSingle */
+
+void oracle_interpolate(double y0, double y1, double y2, double *left, double *right) {
+    double dy01 = y1 - y0;
+    double dy12 = y2 - y1;
+    double dy;
+    if (dy01 * dy12 < 0.0)
+        dy = 0.0;
+    else if (fabs(dy01) < fabs(dy12))
+        dy = dy01;
+    else
+        dy = dy12;
+    *left = y1 - 0.5 * dy;  /* value at the cell's lower face */
+    *right = y1 + 0.5 * dy; /* value at the cell's upper face */
+}
+
+/* ------------------------------------------------- HLLC (section 4.1) ----- */
+
+/* HLLC_a(VL, VR): flux through a face whose normal is axis a, from the
+ * primitive states on its lower (L) and upper (R) side. */
+void oracle_hllc(int dim, int a, double gamma, const double *VL, const double *VR,
+                 double *F) {
+    double rl = VL[0], ul = VL[1 + a], pl = VL[dim + 1];
+    double rr = VR[0], ur = VR[1 + a], pr = VR[dim + 1];
+    double UL[5], UR[5], FL[5], FR[5];
+    cons_of_prim(dim, gamma, VL, UL);
+    cons_of_prim(dim, gamma, VR, UR);
+    euler_flux(dim, a, gamma, VL, FL);
+    euler_flux(dim, a, gamma, VR, FR);
+
+    double al = sqrt(gamma * pl / rl);
+    double ar = sqrt(gamma * pr / rr);
+    double SL = fmin(ul - al, ur - ar);
+    double SR = fmax(ul + al, ur + ar);
+    double Ss = (pr - pl + rl * ul * (SL - ul) - rr * ur * (SR - ur)) /
+                (rl * (SL - ul) - rr * (SR - ur));
+
+    int nv = dim + 2;
+    if (0.0 <= SL) { /* whole fan moves right: F_L */
+        for (int k = 0; k < nv; ++k) F[k] = FL[k];
+        return;
+    }
+    if (!(0.0 <= Ss) && !(0.0 < SR)) { /* whole fan moves left: F_R */
+        for (int k = 0; k < nv; ++k) F[k] = FR[k];
+        return;
+    }
+    /* star region: F*_K = F_K + S_K (U*_K - U_K), K = L if S* >= 0 else R */
+    int left = 0.0 <= Ss;
+    const double *V = left ? VL : VR;
+    const double *U = left ? UL : UR;
+    const double *FK = left ? FL : FR;
+    double S = left ? SL : SR;
+    double r = V[0], u = V[1 + a], p = V[dim + 1];
+    /* star state of Toro, Spruce & Speares: rho_K (S_K-u_K)/(S_K-S*) times
+     * (1, velocity with normal part S*, E_K/rho_K + (S*-u_K)(S* + p_K/(rho_K (S_K-u_K)))) */
+    double chi = r * (S - u) / (S - Ss);
+    double Us[5];
+    Us[0] = chi;
+    for (int b = 0; b < dim; ++b) Us[1 + b] = chi * (b == a ? Ss : V[1 + b]);
+    Us[dim + 1] = chi * (U[dim + 1] / r + (Ss - u) * (Ss + p / (r * (S - u))));
+    for (int k = 0; k < nv; ++k) F[k] = FK[k] + S * (Us[k] - U[k]);
+}
+
+/* Euler flux, exported for the special-case pins (HLLC(V,V) = F(V)). */
+void oracle_euler_flux(int dim, int a, double gamma, const double *V, double *F) {
+    euler_flux(dim, a, gamma, V, F);
+}
+
+/* ------------------------------------------------------------ the step ---- */
+
+typedef struct {
+    grid_t G;
+    int nv;
+    double *U[5];      /* padded conserved planes (scratch copy of a stage input) */
+    double *V[5];      /* padded primitive planes */
+    double *VL[3][5];  /* face values, lower side, per axis */
+    double *VR[3][5];  /* face values, upper side, per axis */
+    double *F[3][5];   /* face fluxes per axis */
+    long nface[3];     /* faces per axis: (n_a + 1) * prod_{b != a} n_b */
+} work_t;
+
+static void free_work(work_t *W) {
+    for (int k = 0; k < 5; ++k) {
+        free(W->U[k]);
+        free(W->V[k]);
+        for (int a = 0; a < 3; ++a) {
+            free(W->VL[a][k]);
+            free(W->VR[a][k]);
+            free(W->F[a][k]);
+        }
+    }
+}
+
+static int alloc_work(work_t *W, const grid_t *G) {
+    memset(W, 0, sizeof *W);
+    W->G = *G;
+    W->nv = G->dim + 2;
+    for (int k = 0; k < W->nv; ++k) {
+        W->U[k] = calloc((size_t)G->npad, sizeof(double));
+        W->V[k] = calloc((size_t)G->npad, sizeof(double));
+        if (!W->U[k] || !W->V[k]) return ORC_ENOMEM;
+    }
+    for (int a = 0; a < G->dim; ++a) {
+        long nf = G->n[a] + 1;
+        for (int b = 0; b < 3; ++b)
+            if (b != a) nf *= G->n[b];
+        W->nface[a] = nf;
+        for (int k = 0; k < W->nv; ++k) {
+            W->VL[a][k] = calloc((size_t)nf, sizeof(double));
+            W->VR[a][k] = calloc((size_t)nf, sizeof(double));
+            W->F[a][k] = calloc((size_t)nf, sizeof(double));
+            if (!W->VL[a][k] || !W->VR[a][k] || !W->F[a][k]) return ORC_ENOMEM;
+        }
+    }
+    return ORC_OK;
+}
+
+/* face index on axis a for the face between interior cells c-e_a and c,
+ * where c[a] runs over 0..n_a (face c[a] - 1/2) */
+static long fidx(const grid_t *G, int a, const long c[3]) {
+    long e[3];
+    for (int b = 0; b < 3; ++b) e[b] = G->n[b] + (b == a ? 1 : 0);
+    return (c[2] * e[1] + c[1]) * e[0] + c[0];
+}
+
+/* Flux_a(U) for every axis: V = V(U); Interpolate -> (VR, VL); F = HLLC_a.
+ * U_int holds interior planes (unpadded, caller layout). */
+static void flux_all_axes(work_t *W, double *const *U_int) {
+    const grid_t *G = &W->G;
+    int nv = W->nv, dim = G->dim;
+    /* load the stage input into the padded scratch and fill the ghosts */
+    for (int k = 0; k < nv; ++k) {
+        for (long i2 = 0; i2 < G->n[2]; ++i2)
+            for (long i1 = 0; i1 < G->n[1]; ++i1)
+                for (long i0 = 0; i0 < G->n[0]; ++i0)
+                    W->U[k][pidx(G, i0, i1, i2)] =
+                        U_int[k][(i2 * G->n[1] + i1) * G->n[0] + i0];
+        fill_ghosts(G, W->U[k]);
+    }
+    /* V0 = V(U0) on interior and ghost cells */
+#pragma omp parallel for schedule(static)
+    for (long c = 0; c < G->npad; ++c) {
+        double u[5], v[5];
+        for (int k = 0; k < nv; ++k) u[k] = W->U[k][c];
+        prim_of_cons(dim, G->gamma, u, v);
+        for (int k = 0; k < nv; ++k) W->V[k][c] = v[k];
+    }
+    for (int a = 0; a < dim; ++a) {
+        /* Eq. eqInterpolateV: every cell i with -1 <= i_a <= n_a (interior on
+         * the other axes) yields VR at face i - 1/2 and VL at face i + 1/2 */
+        long lo[3] = {0, 0, 0}, hi[3] = {G->n[0], G->n[1], G->n[2]};
+        lo[a] = -1;
+        hi[a] = G->n[a] + 1;
+        long stride = a == 0 ? 1 : (a == 1 ? G->p[0] : G->p[0] * G->p[1]);
+#pragma omp parallel for collapse(2) schedule(static)
+        for (long i2 = lo[2]; i2 < hi[2]; ++i2)
+            for (long i1 = lo[1]; i1 < hi[1]; ++i1)
+                for (long i0 = lo[0]; i0 < hi[0]; ++i0) {
+                    long c[3] = {i0, i1, i2};
+                    long ci = pidx(G, i0, i1, i2);
+                    for (int k = 0; k < nv; ++k) {
+                        double lft, rgt;
+                        oracle_interpolate(W->V[k][ci - stride], W->V[k][ci],
+                                           W->V[k][ci + stride], &lft, &rgt);
+                        if (c[a] >= 0) { /* face c - 1/2 exists: VR there */
+                            W->VR[a][k][fidx(G, a, c)] = lft;
+                        }
+                        if (c[a] + 1 <= G->n[a]) { /* face c + 1/2: VL there */
+                            long cu[3] = {c[0], c[1], c[2]};
+                            cu[a] += 1;
+                            W->VL[a][k][fidx(G, a, cu)] = rgt;
+                        }
+                    }
+                }
+        /* F_a[i + 1/2] = HLLC_a(VL[i + 1/2], VR[i + 1/2]) */
+#pragma omp parallel for schedule(static)
+        for (long f = 0; f < W->nface[a]; ++f) {
+            double vl[5], vr[5], fl[5];
+            for (int k = 0; k < nv; ++k) {
+                vl[k] = W->VL[a][k][f];
+                vr[k] = W->VR[a][k][f];
+            }
+            oracle_hllc(dim, a, G->gamma, vl, vr, fl);
+            for (int k = 0; k < nv; ++k) W->F[a][k][f] = fl[k];
+        }
+    }
+}
+
+/* AddFlux(dt, F, Ubase) -> Uout, Eq. eqAddFlux:
+ * Uout[i] = Ubase[i] + sum_a (dt/dr_a) (F_a[i - 1/2] - F_a[i + 1/2]) */
+static void add_flux(work_t *W, double dt, double *const *Ubase, double *const *Uout) {
+    const grid_t *G = &W->G;
+    int nv = W->nv, dim = G->dim;
+    double coef[3];
+    for (int a = 0; a < dim; ++a) coef[a] = dt / G->dr[a];
+#pragma omp parallel for collapse(2) schedule(static)
+    for (long i2 = 0; i2 < G->n[2]; ++i2)
+        for (long i1 = 0; i1 < G->n[1]; ++i1)
+            for (long i0 = 0; i0 < G->n[0]; ++i0) {
+                long c[3] = {i0, i1, i2};
+                long li = (i2 * G->n[1] + i1) * G->n[0] + i0;
+                for (int k = 0; k < nv; ++k) {
+                    double sum = 0.0;
+                    for (int a = 0; a < dim; ++a) {
+                        long cu[3] = {c[0], c[1], c[2]};
+                        cu[a] += 1;
+                        double fm = W->F[a][k][fidx(G, a, c)];  /* F_a[i - 1/2] */
+                        double fp = W->F[a][k][fidx(G, a, cu)]; /* F_a[i + 1/2] */
+                        sum += coef[a] * (fm - fp);
+                    }
+                    Uout[k][li] = Ubase[k][li] + sum;
+                }
+            }
+}
+
+/* per-cell CFL signal sum_a (|v_a| + c_s) / dr_a; its maximum over cells */
+static double max_signal(const grid_t *G, double *const *U) {
+    double smax = 0.0;
+    int dim = G->dim;
+    for (long c = 0; c < G->ncell; ++c) {
+        double u[5], v[5];
+        for (int k = 0; k < dim + 2; ++k) u[k] = U[k][c];
+        prim_of_cons(dim, G->gamma, u, v);
+        double cs = sqrt(G->gamma * v[dim + 1] / v[0]);
+        double s = 0.0;
+        for (int a = 0; a < dim; ++a) s += (fabs(v[1 + a]) + cs) / G->dr[a];
+        if (!(s <= smax)) smax = s; /* NaN propagates */
+    }
+    return smax;
+}
+
+static int all_finite_positive(const grid_t *G, double *const *U) {
+    int dim = G->dim;
+    for (long c = 0; c < G->ncell; ++c) {
+        double u[5], v[5];
+        for (int k = 0; k < dim + 2; ++k) {
+            u[k] = U[k][c];
+            if (!isfinite(u[k])) return 0;
+        }
+        prim_of_cons(dim, G->gamma, u, v);
+        if (!(v[0] > 0.0) || !(v[dim + 1] > 0.0)) return 0;
+    }
+    return 1;
+}
+
+/* One midpoint RK step (section 4.1):
+ *   F0 = Flux(U0); U1 = AddFlux(dt/2, F0, U0); F1 = Flux(U1); U2 = AddFlux(dt, F1, U0)
+ * U (in/out) holds U0 on entry and U2 on return. */
+static void rk_step(work_t *W, double *const *U, double *const *U1, double dt) {
+    flux_all_axes(W, U);
+    add_flux(W, 0.5 * dt, U, U1);
+    flux_all_axes(W, U1);
+    add_flux(W, dt, U, U);
+}
+
+/* -------------------------------------------------------- exported API --- */
+
+static void split_planes(double *base, int nv, long ncell, double **planes) {
+    for (int k = 0; k < nv; ++k) planes[k] = base + (size_t)k * (size_t)ncell;
+}
+
+static void set_threads(int nthreads) {
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+}
+
+int oracle_has_openmp(void) {
+#ifdef _OPENMP
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+int oracle_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+int oracle_prim_to_cons(int dim, const long n[3], double gamma, const double *V, double *U) {
+    long ncell = 1;
+    for (int a = 0; a < dim; ++a) ncell *= n[a];
+    int nv = dim + 2;
+    for (long c = 0; c < ncell; ++c) {
+        double v[5], u[5];
+        for (int k = 0; k < nv; ++k) v[k] = V[(size_t)k * ncell + c];
+        cons_of_prim(dim, gamma, v, u);
+        for (int k = 0; k < nv; ++k) U[(size_t)k * ncell + c] = u[k];
+    }
+    return ORC_OK;
+}
+
+int oracle_cons_to_prim(int dim, const long n[3], double gamma, const double *U, double *V) {
+    long ncell = 1;
+    for (int a = 0; a < dim; ++a) ncell *= n[a];
+    int nv = dim + 2;
+    for (long c = 0; c < ncell; ++c) {
+        double v[5], u[5];
+        for (int k = 0; k < nv; ++k) u[k] = U[(size_t)k * ncell + c];
+        prim_of_cons(dim, gamma, u, v);
+        for (int k = 0; k < nv; ++k) V[(size_t)k * ncell + c] = v[k];
+    }
+    return ORC_OK;
+}
+
+/* dt = cfl / max_i sum_a (|v_a| + c_s)/dr_a on state U (SoA, dim+2 planes) */
+int oracle_cfl_dt(int dim, const long n[3], const double dr[3], double gamma,
+                  const double *U, double cfl, double *dt_out) {
+    grid_t G;
+    int bc[3] = {0, 0, 0};
+    int rc = make_grid(&G, dim, n, dr, gamma, bc);
+    if (rc) return rc;
+    double *P[5];
+    split_planes((double *)U, dim + 2, G.ncell, P);
+    *dt_out = cfl / max_signal(&G, P);
+    return ORC_OK;
+}
+
+/* Face fluxes Flux_a(U) of every axis, for the per-face pins.  F_out[a] points
+ * to (dim+2) planes of (n_a+1)*prod_{b!=a} n_b faces, face c-1/2 of cell c. */
+int oracle_fluxes(int dim, const long n[3], const double dr[3], double gamma,
+                  const int bc[3], const double *U, double **F_out) {
+    grid_t G;
+    int rc = make_grid(&G, dim, n, dr, gamma, bc);
+    if (rc) return rc;
+    work_t W;
+    rc = alloc_work(&W, &G);
+    if (rc) {
+        free_work(&W);
+        return rc;
+    }
+    double *P[5];
+    split_planes((double *)U, dim + 2, G.ncell, P);
+    flux_all_axes(&W, P);
+    for (int a = 0; a < dim; ++a)
+        for (int k = 0; k < dim + 2; ++k)
+            memcpy(F_out[a] + (size_t)k * W.nface[a], W.F[a][k],
+                   sizeof(double) * (size_t)W.nface[a]);
+    free_work(&W);
+    return ORC_OK;
+}
+
+/* Advance U (SoA, dim+2 planes, in/out) by up to n_steps RK steps.
+ * Each step: dt = cfl / max signal of the step's initial state; if t_end > 0,
+ * dt = min(dt, t_end - t) and a clipped step sets t = t_end; stop once
+ * t >= t_end.  Returns ORC_ENONFINITE if a step leaves a non-finite value,
+ * rho <= 0 or p <= 0 (the state then holds that step's output). */
+int oracle_run(int dim, const long n[3], const double dr[3], double gamma,
+               const int bc[3], double cfl, double *U, int n_steps, double t_end,
+               double *t_inout, int *steps_done, int nthreads) {
+    grid_t G;
+    int rc = make_grid(&G, dim, n, dr, gamma, bc);
+    if (rc) return rc;
+    set_threads(nthreads);
+    work_t W;
+    rc = alloc_work(&W, &G);
+    double *u1 = rc ? NULL : calloc((size_t)(dim + 2) * (size_t)G.ncell, sizeof(double));
+    if (rc || !u1) {
+        free_work(&W);
+        free(u1);
+        return ORC_ENOMEM;
+    }
+    double *P[5], *P1[5];
+    split_planes(U, dim + 2, G.ncell, P);
+    split_planes(u1, dim + 2, G.ncell, P1);
+    double t = t_inout ? *t_inout : 0.0;
+    int done = 0;
+    rc = ORC_OK;
+    for (int s = 0; s < n_steps; ++s) {
+        if (t_end > 0.0 && t >= t_end) break;
+        double dt = cfl / max_signal(&G, P);
+        int clipped = 0;
+        if (t_end > 0.0 && dt >= t_end - t) {
+            dt = t_end - t;
+            clipped = 1;
+        }
+        rk_step(&W, P, P1, dt);
+        t = clipped ? t_end : t + dt;
+        ++done;
+        if (!all_finite_positive(&G, P)) {
+            rc = ORC_ENONFINITE;
+            break;
+        }
+    }
+    if (t_inout) *t_inout = t;
+    if (steps_done) *steps_done = done;
+    free(u1);
+    free_work(&W);
+    return rc;
+}
+
+/* fixed-order pairwise sum of x[0..n) */
+static double pairwise_sum(const double *x, long n) {
+    if (n <= 8) {
+        double s = 0.0;
+        for (long i = 0; i < n; ++i) s += x[i];
+        return s;
+    }
+    long h = n / 2;
+    return pairwise_sum(x, h) + pairwise_sum(x + h, n - h);
+}
+
+/* Totals (mass, momentum_0..2, energy) = pairwise sums times the cell volume.
+ * Momenta of inactive axes are 0. */
+int oracle_totals(int dim, const long n[3], const double dr[3], const double *U,
+                  double out[5]) {
+    long ncell = 1;
+    double vol = 1.0;
+    for (int a = 0; a < dim; ++a) {
+        ncell *= n[a];
+        vol *= dr[a];
+    }
+    for (int k = 0; k < 5; ++k) out[k] = 0.0;
+    out[0] = pairwise_sum(U, ncell) * vol;
+    for (int a = 0; a < dim; ++a)
+        out[1 + a] = pairwise_sum(U + (size_t)(1 + a) * ncell, ncell) * vol;
+    out[4] = pairwise_sum(U + (size_t)(dim + 1) * ncell, ncell) * vol;
+    return ORC_OK;
+}
