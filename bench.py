@@ -1,0 +1,309 @@
+#!/usr/bin/env python3
+"""Throughput of the compressible-Euler RK step on GB300: cell-updates per second.
+
+One "step" is one midpoint-RK step of the whole hot path (CFL dt from the previous step's
+fused epilogue, two fused MinBee/HLLC stage kernels) over the 3D periodic 512^3 blast in FP32
+(uniform rho = 1, p = 1e-3, p = 10 within 8 cells of the centre, gamma = 1.4, CFL 0.4).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line on rank 0.  Under torchrun (N > 1) every rank advances its own replica of
+the grid (the step has no exchange between independent grids): value = all ranks' cell-updates
+divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s per RK step (512^3 FP32) vs plain FP64; % HBM roofline"
+N = 512
+GAMMA, CFL, RADIUS = 1.4, 0.4, 8.0
+WORKLOAD = "3D periodic 512^3 blast, FP32 stencil, FP64 dt/time/totals"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _kernel_digest() -> str:
+    h = hashlib.sha256()
+    for name in ("hydro_device.cuh", "stage_kernel.cuh", "stage_launch.cuh", "stage_f32_d3.cu"):
+        with open(os.path.join(ROOT, "paper_1204_4779_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was taken on
+    the current kernel source; else None."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+            rec = json.load(f)
+        if rec.get("kernel_digest") != _kernel_digest():
+            return None
+        return rec["per_launch_bytes"].get(kernel)
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.idx)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+        return False
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _gpu_index(local_rank: int) -> int:
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    ids = [v.strip() for v in vis.split(",") if v.strip()]
+    if ids and ids[min(local_rank, len(ids) - 1)].isdigit():
+        return int(ids[min(local_rank, len(ids) - 1)])
+    return local_rank
+
+
+def cpu_oracle_cups(budget_s: float = 12.0, n: int = 64, max_steps: int = 200):
+    """The FP64 CPU oracle as it stands, on a bounded sample of the workload: the same blast
+    at n^3 (radius 8 cells, periodic, CFL 0.4), all host cores, about `budget_s` of CPU work."""
+    import oracle
+    from paper_1204_4779_gb300 import inputs
+    U = oracle.prim_to_cons(inputs.blast_3d(n, radius_cells=RADIUS), GAMMA)
+    threads = oracle.max_threads()
+    t0 = time.perf_counter()
+    U, _, s1, _ = oracle.run(U, GAMMA, CFL, 1, bc=(0, 0, 0), threads=threads)
+    one = time.perf_counter() - t0
+    steps = max(1, min(max_steps, int(budget_s / max(one, 1e-6))))
+    t0 = time.perf_counter()
+    _, _, done, _ = oracle.run(U, GAMMA, CFL, steps, bc=(0, 0, 0), threads=threads)
+    el = time.perf_counter() - t0
+    return {"value": n ** 3 * done / el, "unit": "cell-updates/s", "cores": threads,
+            "kind": "oracle",
+            "sample": f"{n}^3 blast (radius {RADIUS:g} cells), {done} FP64 RK steps, "
+                      f"{el:.1f} s, OpenMP threads={threads}, host={os.uname().machine}"}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle on the host cores, each step one RK step of a bounded
+    64^3 sample of the blast workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from paper_1204_4779_gb300 import inputs
+    n = 64
+    U = oracle.prim_to_cons(inputs.blast_3d(n, radius_cells=RADIUS), GAMMA)
+    threads = oracle.max_threads()
+    U, *_ = oracle.run(U, GAMMA, CFL, args.warmup, bc=(0, 0, 0), threads=threads)
+    t0 = time.perf_counter()
+    _, _, done, _ = oracle.run(U, GAMMA, CFL, args.steps, bc=(0, 0, 0), threads=threads)
+    el = time.perf_counter() - t0
+    value = n ** 3 * done / el
+    line = {"metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(done, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "sample": f"{n}^3 blast per step on the host",
+                       "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": threads,
+                             "kind": "oracle",
+                             "sample": f"{n}^3 blast (radius {RADIUS:g} cells), {done} RK steps"},
+            "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1204_4779_gb300 import hydro, inputs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    ncell = N ** 3
+    V = inputs.blast_3d_torch(N, RADIUS, device=dev)
+    U = hydro.prim_to_cons(V, GAMMA).to(torch.float32).contiguous()
+    U_init = U.clone()
+    del V
+    S = hydro.Solver((N, N, N), GAMMA, bc="periodic", dtype=torch.float32, cfl=CFL)
+    S.step(U, args.warmup)
+    torch.cuda.synchronize()
+
+    # --- timed region: K RK steps, per-kernel CUDA events on the launching stream ----------
+    S.set_profiling(True)
+    S.kernel_times(reset=True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(_gpu_index(local)) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record()
+        t_sim, done = S.step(U, args.steps)
+        ev1.record()
+        torch.cuda.synchronize()
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    kt = S.kernel_times(reset=True)
+    S.set_profiling(False)
+    if done != args.steps:
+        raise RuntimeError(f"only {done} of {args.steps} steps ran")
+    t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * ncell * args.steps / (ms_max * 1e-3)
+
+    # --- roofline of the dominant kernel ---------------------------------------------------
+    hbm, peak_kind = _peaks()
+    nv = 5
+    alg = {"stage1": 2 * nv * 4 * ncell, "stage2": 3 * nv * 4 * ncell}  # bytes per launch
+    dom = max(("stage1", "stage2"), key=lambda k: kt[k][0])
+    avg_ms = kt[dom][0] / max(kt[dom][1], 1)
+    achieved = alg[dom] / (avg_ms * 1e-3) / 1e9
+    traffic = _traffic(dom)
+    kernels = {k: {"avg_ms": v[0] / max(v[1], 1), "launches": v[1],
+                   "alg_bytes_per_launch": alg.get(k, nv * 4 * ncell)} for k, v in kt.items()}
+
+    # --- end to end through the C ABI with host buffers -------------------------------------
+    e2e = None
+    if args.e2e_steps > 0:
+        host = U_init.cpu().pin_memory()
+        dev_state = torch.empty_like(U_init)
+        S.step_host(dev_state, host, host, 1)  # warm (copies + step)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(args.e2e_steps):
+            S.step_host(dev_state, host, host, 1)
+        e1.record()
+        torch.cuda.synchronize()
+        barrier()
+        te = torch.tensor([e0.elapsed_time(e1)], device=dev, dtype=torch.float64)
+        if world > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        nbytes = nv * 4 * ncell
+        e2e = {"value": world * ncell * args.e2e_steps / (float(te.item()) * 1e-3),
+               "unit": "cell-updates/s", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+               "steps": args.e2e_steps,
+               "call": "hydro_step_host: pinned host state in, 1 RK step, host state out"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_cups()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": [N, N, N], "gamma": GAMMA, "cfl": CFL,
+                       "blast_radius_cells": RADIUS, "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (2.5 GiB state vs 129 MB L2); no flush",
+                       "variant": {"tile": [32, 8], "march": 64, "split": "per-stage"}},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": traffic, "kernel": dom,
+                         "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"},
+            "kernels": kernels,
+            "gpu_launches": int(sum(v[1] for v in kt.values())),
+            "clocks": clk.summary(),
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "sim_time": t_sim,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,182 @@
+/*
+ * hydro.h -- C ABI of libhydro.so: the second-order finite-volume step of the compressible
+ * Euler equations (Paraiso, arXiv:1204.4779, section 4.1 "The Target Program") on one GB300
+ * (sm_103a), FP32 or FP64.
+ *
+ * The step (section 4.1): with V = (rho, v_a, p) the primitive and U = (rho, m_a, E) the
+ * conserved variables (Eqs. eqPrimitiveVars, eqConservedVars),
+ *     F0_a = Flux_a(U0);   U1 = AddFlux(dt/2, F0, U0);
+ *     F1_a = Flux_a(U1);   U2 = AddFlux(dt,   F1, U0),
+ * where Flux_a recovers V from U, reconstructs face values with the piecewise-linear MinBee
+ * limiter (Eqs. eqInterpolateV, eqInterpolateSingle) and evaluates the HLLC Riemann solver
+ * on each face, and AddFlux is the conservative update of Eq. eqAddFlux.  dt comes from the
+ * CFL condition, dt = cfl / max_i sum_a (|v_a| + c_s) / dr_a with c_s = sqrt(gamma p / rho),
+ * evaluated on the state at the start of each step (the paper says only that dt is
+ * "determined by the CFL condition"; this is the reading used).
+ *
+ * Layout of a state: structure of arrays, dim+2 planes (rho, m_x, [m_y, [m_z]], E), each a
+ * dense n[0]*n[1]*n[2] array of the context's element type with x fastest, then y, then z.
+ * Planes live in device memory owned by the caller; no ghost padding.
+ *
+ * Ownership: the library never allocates device memory.  The caller allocates the state
+ * planes and one workspace block of hydro_workspace_bytes() bytes (256-byte aligned) and keeps
+ * both alive while the context uses them.  The context owns only host memory, CUDA graphs,
+ * events and one private capture stream.
+ *
+ * Errors: every call returns an int status (HYDRO_OK = 0); no call aborts or throws.
+ * HYDRO_ENONFINITE means a step produced (or was given) a non-finite value, rho <= 0 or
+ * p <= 0; the state then holds the output of that step and no further step runs in the call.
+ *
+ * Streams: every call is ordered on the context's stream (set at create or by
+ * hydro_set_stream).  Calls that return host values (hydro_cfl_dt, hydro_totals, hydro_step
+ * with t_inout or steps_done, hydro_step_host, hydro_status) synchronise that stream.
+ * A context must not be used from two host threads at once.
+ */
+#ifndef HYDRO_H
+#define HYDRO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HYDRO_ABI_VERSION 1
+
+enum {
+    HYDRO_OK = 0,
+    HYDRO_EINVAL = 1,     /* bad argument: null pointer, bad grid/gamma/cfl/precision/variant,
+                             workspace too small or misaligned */
+    HYDRO_ECUDA = 2,      /* a CUDA runtime call failed (hydro_last_cuda_error tells which) */
+    HYDRO_ENONFINITE = 3, /* non-finite value, rho <= 0 or p <= 0 seen on the device */
+    HYDRO_ETIMEOUT = 4,   /* a bounded device-side wait gave up */
+    HYDRO_EUNSUPPORTED = 5 /* valid request that this build has no kernel for */
+};
+
+typedef enum { HYDRO_BC_PERIODIC = 0, HYDRO_BC_OUTFLOW = 1 } hydro_bc_t;
+typedef enum { HYDRO_F64 = 0, HYDRO_F32 = 1 } hydro_prec_t;
+
+/* Grid: dim in {1,2,3}; n[a] >= 1 cells on active axes (n[a] is ignored and taken as 1 on
+ * axes a >= dim); box [lo[a], hi[a]] with hi > lo, so dr_a = (hi[a] - lo[a]) / n[a].
+ * n[0]*n[1]*n[2] must be below 2^31. */
+typedef struct {
+    int32_t dim;
+    int32_t reserved;
+    int64_t n[3];
+    double lo[3];
+    double hi[3];
+} hydro_grid_t;
+
+/* Device pointers of the dim+2 conserved (or primitive) planes; entries >= dim+2 unused. */
+typedef struct {
+    void *plane[5];
+} hydro_state_t;
+
+/* Kernel variant (the tuning space).  Zero-initialised = library default.
+ *   tile_x, tile_y: in-plane CTA tile (cells); tile_y = 1 for dim 1.  The compiled shapes are
+ *                   listed by hydro_variant_supported().
+ *   march:          dim 3 only: z-planes one CTA marches through (>= 1).
+ *   split:          0 = one kernel per RK stage (the only split built).
+ */
+typedef struct {
+    int32_t tile_x;
+    int32_t tile_y;
+    int32_t march;
+    int32_t split;
+} hydro_variant_t;
+
+typedef struct hydro_ctx hydro_ctx_t;
+
+/* Library version (HYDRO_ABI_VERSION). */
+int hydro_version(void);
+
+/* Human-readable text of a status code; never NULL. */
+const char *hydro_strerror(int status);
+
+/* Text of the last failing CUDA call seen by this host thread ("" if none). */
+const char *hydro_last_cuda_error(void);
+
+/* 1 if this build has kernels for (prec, dim, variant); variant may be NULL (default). */
+int hydro_variant_supported(int32_t prec, int32_t dim, const hydro_variant_t *variant);
+
+/* Bytes of device workspace hydro_create needs for this grid and precision: the RK stage
+ * buffer U1 (dim+2 planes), the step control block and reduction partials. */
+int hydro_workspace_bytes(const hydro_grid_t *grid, int32_t prec, size_t *bytes_out);
+
+/* Create a solver context.
+ *   grid      grid and box (copied)
+ *   gamma     ratio of specific heats, > 1
+ *   bc        per-axis boundary condition (hydro_bc_t); entries >= dim ignored.  Periodic
+ *             wraps; outflow copies the nearest interior cell into the two ghost layers
+ *   prec      HYDRO_F32 (whole stencil in FP32; dt, time and totals in FP64) or HYDRO_F64
+ *   cfl       Courant number, 0 < cfl
+ *   variant   kernel variant or NULL for the default
+ *   workspace device pointer, 256-byte aligned, >= hydro_workspace_bytes(); caller-owned
+ *   stream    cudaStream_t the context issues work on (NULL = legacy default stream)
+ *   out       receives the context
+ * The current CUDA device at create is the context's device. */
+int hydro_create(const hydro_grid_t *grid, double gamma, const int32_t bc[3], int32_t prec,
+                 double cfl, const hydro_variant_t *variant, void *workspace,
+                 size_t workspace_bytes, void *stream, hydro_ctx_t **out);
+
+int hydro_destroy(hydro_ctx_t *ctx);
+
+/* Change the stream later calls are ordered on. */
+int hydro_set_stream(hydro_ctx_t *ctx, void *stream);
+
+/* Advance `state` (in place) by up to n_steps midpoint-RK steps (section 4.1).
+ *   t_end     > 0: the last step is clipped so that t lands exactly on t_end and no step
+ *             runs once t >= t_end; <= 0: no clipping
+ *   t_inout   in: time of `state` (NULL = 0); out: time after the call
+ *   steps_done out: steps actually taken (may be NULL)
+ * dt is computed on the device from the state at the start of each step (the first from
+ * `state` by a CFL pass, later ones in the epilogue of the previous step) and never leaves
+ * the device inside the call.  The steps run as CUDA graphs of captured launches.
+ * If both t_inout and steps_done are NULL the call is asynchronous and a device-side error
+ * is reported by the next synchronising call; otherwise it synchronises and returns
+ * HYDRO_ENONFINITE if a step failed. */
+int hydro_step(hydro_ctx_t *ctx, const hydro_state_t *state, int32_t n_steps, double t_end,
+               double *t_inout, int32_t *steps_done);
+
+/* Same as hydro_step, but the state comes from and goes back to HOST memory: the dim+2
+ * planes at host_in[k] are copied into the device planes of `dev_state`, stepped, and copied
+ * out to host_out[k] (host_out may equal host_in).  Pinned host memory gives full copy
+ * bandwidth.  Always synchronises. */
+int hydro_step_host(hydro_ctx_t *ctx, const hydro_state_t *dev_state,
+                    const void *const host_in[5], void *const host_out[5], int32_t n_steps,
+                    double t_end, double *t_inout, int32_t *steps_done);
+
+/* dt = cfl / max_i sum_a (|v_a| + c_s)/dr_a of `state` (FP64 result).  Synchronises. */
+int hydro_cfl_dt(hydro_ctx_t *ctx, const hydro_state_t *state, double *dt_out);
+
+/* Conserved totals integrated over the box, in FP64: out = (mass, M_x, M_y, M_z, energy),
+ * momenta of inactive axes 0.  Deterministic fixed-order two-level sum times the cell volume.
+ * Synchronises. */
+int hydro_totals(hydro_ctx_t *ctx, const hydro_state_t *state, double out[5]);
+
+/* Device status word of the last step call: HYDRO_OK or HYDRO_ENONFINITE.  Synchronises. */
+int hydro_status(hydro_ctx_t *ctx);
+
+/* Element-wise conversions between primitive (rho, v, p) and conserved (rho, m, E) planes
+ * (section 4.1: m_a = rho v_a, E = p/(gamma-1) + rho v^2/2) for ncell cells of precision
+ * prec, on `stream`.  in and out may be the same planes.  Context-free. */
+int hydro_prim_to_cons(int32_t dim, int64_t ncell, double gamma, int32_t prec,
+                       const hydro_state_t *prim_in, const hydro_state_t *cons_out, void *stream);
+int hydro_cons_to_prim(int32_t dim, int64_t ncell, double gamma, int32_t prec,
+                       const hydro_state_t *cons_in, const hydro_state_t *prim_out, void *stream);
+
+/* Per-kernel timing.  With profiling on, hydro_step launches its kernels directly (no graph)
+ * with CUDA events recorded on the context's stream around each launch.
+ * hydro_kernel_times fills, for each kernel kind k (0 = CFL pass, 1 = RK stage 1, 2 = RK
+ * stage 2 with the fused dt reduction), ms_out[k] = summed device time and launches_out[k] =
+ * launches since the last reset; it synchronises.  n = number of entries the arrays hold. */
+int hydro_set_profiling(hydro_ctx_t *ctx, int32_t on);
+int hydro_kernel_times(hydro_ctx_t *ctx, double *ms_out, int64_t *launches_out, int32_t n,
+                       int32_t reset);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HYDRO_H */

@@ -1,0 +1,570 @@
+// C ABI of libhydro.so (declared in include/hydro.h): argument checking, the solver context,
+// the CUDA-graph cache of step chunks and the per-kernel event timing.
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "../../include/hydro.h"
+#include "hydro_device.cuh"
+#include "hydro_internal.h"
+
+using hydro::Ctrl;
+
+namespace {
+
+thread_local char g_cuda_err[256] = "";
+
+int cuda_fail(cudaError_t e, const char *what) {
+    snprintf(g_cuda_err, sizeof g_cuda_err, "%s: %s (%d)", what, cudaGetErrorString(e), (int)e);
+    return HYDRO_ECUDA;
+}
+
+#define CK(call)                                            \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+constexpr size_t kAlign = 256;
+constexpr int kMaxChunk = 64;  // largest number of steps captured in one graph
+constexpr int kGraphSlots = 16;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+struct GraphEntry {
+    int chunk = 0;
+    void *planes[5] = {};
+    cudaGraphExec_t exec = nullptr;
+    unsigned long long last_use = 0;
+};
+
+struct Layout {
+    size_t ctrl_off, parts_off, u1_off, total;
+};
+
+bool grid_ok(const hydro_grid_t *g, long long *ncell) {
+    if (!g || g->dim < 1 || g->dim > 3) return false;
+    long long n = 1;
+    for (int a = 0; a < g->dim; ++a) {
+        if (g->n[a] < 1 || g->n[a] > (1LL << 31) - 1) return false;
+        if (!(g->hi[a] > g->lo[a])) return false;
+        n *= g->n[a];
+        if (n >= (1LL << 31)) return false;
+    }
+    *ncell = n;
+    return true;
+}
+
+Layout layout_for(int dim, long long ncell, int prec) {
+    Layout L;
+    const size_t esz = prec == HYDRO_F32 ? 4 : 8;
+    L.ctrl_off = 0;
+    L.parts_off = align_up(sizeof(Ctrl));
+    L.u1_off = align_up(L.parts_off + sizeof(double) * 5 * hydro::kTotalsParts);
+    const size_t plane = align_up((size_t)ncell * esz);
+    L.total = L.u1_off + plane * (size_t)(dim + 2);
+    return L;
+}
+
+bool tile_compiled(int prec, int dim, int bx, int by) {
+    for (int i = 0; i < hydro::kNumTiles; ++i) {
+        const hydro::TileShape &t = hydro::kTiles[i];
+        if (t.prec == prec && t.dim == dim && t.bx == bx && t.by == by) return true;
+    }
+    return false;
+}
+
+void default_variant(int prec, int dim, hydro_variant_t *v) {
+    v->split = 0;
+    v->march = 0;
+    if (dim == 1) {
+        v->tile_x = 128;
+        v->tile_y = 1;
+    } else {
+        v->tile_x = 32;
+        v->tile_y = 8;
+    }
+    if (dim == 3) v->march = 64;
+    (void)prec;
+}
+
+// Resolve a (possibly partial) variant against the defaults; false if not compiled.
+bool resolve_variant(int prec, int dim, const hydro_variant_t *in, hydro_variant_t *out) {
+    default_variant(prec, dim, out);
+    if (in) {
+        if (in->tile_x) out->tile_x = in->tile_x;
+        if (in->tile_y) out->tile_y = in->tile_y;
+        if (in->march) out->march = in->march;
+        out->split = in->split;
+    }
+    if (out->split != 0) return false;
+    if (dim == 3 && out->march < 1) return false;
+    if (dim < 3) out->march = 1;
+    return tile_compiled(prec, dim, out->tile_x, out->tile_y);
+}
+
+}  // namespace
+
+struct hydro_ctx {
+    int device = 0;
+    int dim = 1;
+    int prec = HYDRO_F64;
+    long long ncell = 0;
+    int n[3] = {1, 1, 1};
+    int periodic[3] = {1, 1, 1};
+    double dr[3] = {1, 1, 1};
+    double gamma = 1.4, cfl = 0.4;
+    hydro_variant_t var = {};
+    Layout lay = {};
+    unsigned char *ws = nullptr;
+    Ctrl *ctrl = nullptr;
+    double *parts = nullptr;
+    void *u1[5] = {};
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap = nullptr;  // private stream used only to capture graphs
+    GraphEntry graphs[kGraphSlots];
+    unsigned long long use_clock = 0;
+    bool profiling = false;
+    std::vector<cudaEvent_t> events;
+    double kms[3] = {0, 0, 0};
+    long long klaunch[3] = {0, 0, 0};
+};
+
+namespace {
+
+bool state_ok(const hydro_ctx *c, const hydro_state_t *s) {
+    if (!s) return false;
+    for (int k = 0; k < c->dim + 2; ++k)
+        if (!s->plane[k]) return false;
+    return true;
+}
+
+hydro::StageLaunch stage_args(const hydro_ctx *c, const hydro_state_t *s, int stage) {
+    hydro::StageLaunch L;
+    memset(&L, 0, sizeof L);
+    L.stage = stage;
+    for (int k = 0; k < c->dim + 2; ++k) {
+        L.uin[k] = stage == 1 ? s->plane[k] : c->u1[k];
+        L.ubase[k] = s->plane[k];
+        L.uout[k] = stage == 1 ? c->u1[k] : s->plane[k];
+    }
+    for (int a = 0; a < 3; ++a) {
+        L.n[a] = c->n[a];
+        L.periodic[a] = c->periodic[a];
+        L.dr[a] = c->dr[a];
+    }
+    L.march = c->var.march;
+    L.tile_x = c->var.tile_x;
+    L.tile_y = c->var.tile_y;
+    L.gamma = c->gamma;
+    L.ctrl = c->ctrl;
+    return L;
+}
+
+cudaError_t launch_stage(const hydro_ctx *c, const hydro::StageLaunch &L, cudaStream_t st,
+                         bool prepare_only = false) {
+    if (c->prec == HYDRO_F64) return hydro::stage_f64(c->dim, L, st, prepare_only);
+    switch (c->dim) {
+        case 1: return hydro::stage_f32_d1(L, st, prepare_only);
+        case 2: return hydro::stage_f32_d2(L, st, prepare_only);
+        default: return hydro::stage_f32_d3(L, st, prepare_only);
+    }
+}
+
+hydro::AuxArgs aux_args(const hydro_ctx *c, const hydro_state_t *s) {
+    hydro::AuxArgs A;
+    memset(&A, 0, sizeof A);
+    A.prec = c->prec;
+    A.dim = c->dim;
+    A.ncell = c->ncell;
+    for (int k = 0; k < c->dim + 2; ++k) A.u[k] = s->plane[k];
+    for (int a = 0; a < 3; ++a) A.dr[a] = c->dr[a];
+    A.gamma = c->gamma;
+    A.ctrl = c->ctrl;
+    return A;
+}
+
+// Reset the control block and run the CFL pass: dt of the first step from `s`.
+int begin_steps(hydro_ctx *c, const hydro_state_t *s, double t0, double t_end) {
+    Ctrl init;
+    memset(&init, 0, sizeof init);
+    init.t = t0;
+    init.t_end = t_end;
+    init.cfl = c->cfl;
+    CK(cudaMemcpyAsync(c->ctrl, &init, sizeof init, cudaMemcpyHostToDevice, c->stream));
+    if (c->profiling) {
+        while (c->events.size() < 2) {
+            cudaEvent_t e;
+            CK(cudaEventCreate(&e));
+            c->events.push_back(e);
+        }
+        CK(cudaEventRecord(c->events[0], c->stream));
+        CK(hydro::launch_cfl(aux_args(c, s), c->stream));
+        CK(cudaEventRecord(c->events[1], c->stream));
+        CK(cudaEventSynchronize(c->events[1]));
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, c->events[0], c->events[1]));
+        c->kms[0] += ms;
+        c->klaunch[0] += 1;
+        return HYDRO_OK;
+    }
+    CK(hydro::launch_cfl(aux_args(c, s), c->stream));
+    return HYDRO_OK;
+}
+
+int get_graph(hydro_ctx *c, const hydro_state_t *s, int chunk, cudaGraphExec_t *out) {
+    GraphEntry *free_slot = nullptr, *oldest = &c->graphs[0];
+    for (auto &g : c->graphs) {
+        if (g.exec && g.chunk == chunk) {
+            bool same = true;
+            for (int k = 0; k < c->dim + 2; ++k) same &= g.planes[k] == s->plane[k];
+            if (same) {
+                g.last_use = ++c->use_clock;
+                *out = g.exec;
+                return HYDRO_OK;
+            }
+        }
+        if (!g.exec && !free_slot) free_slot = &g;
+        if (g.last_use < oldest->last_use) oldest = &g;
+    }
+    GraphEntry *slot = free_slot ? free_slot : oldest;
+    if (slot->exec) {
+        cudaGraphExecDestroy(slot->exec);
+        slot->exec = nullptr;
+    }
+    const hydro::StageLaunch L1 = stage_args(c, s, 1), L2 = stage_args(c, s, 2);
+    CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+    cudaError_t le = cudaSuccess;
+    for (int i = 0; i < chunk && le == cudaSuccess; ++i) {
+        le = launch_stage(c, L1, c->cap);
+        if (le == cudaSuccess) le = launch_stage(c, L2, c->cap);
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(c->cap, &graph);
+    if (le != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_fail(le, "stage launch during capture");
+    }
+    if (ee != cudaSuccess) return cuda_fail(ee, "cudaStreamEndCapture");
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) return cuda_fail(ie, "cudaGraphInstantiate");
+    slot->exec = exec;
+    slot->chunk = chunk;
+    for (int k = 0; k < 5; ++k) slot->planes[k] = s->plane[k];
+    slot->last_use = ++c->use_clock;
+    *out = exec;
+    return HYDRO_OK;
+}
+
+int run_steps_profiled(hydro_ctx *c, const hydro_state_t *s, int n) {
+    const hydro::StageLaunch L1 = stage_args(c, s, 1), L2 = stage_args(c, s, 2);
+    const size_t need = (size_t)2 * n + 1;
+    while (c->events.size() < need) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        c->events.push_back(e);
+    }
+    CK(cudaEventRecord(c->events[0], c->stream));
+    for (int i = 0; i < n; ++i) {
+        CK(launch_stage(c, L1, c->stream));
+        CK(cudaEventRecord(c->events[2 * i + 1], c->stream));
+        CK(launch_stage(c, L2, c->stream));
+        CK(cudaEventRecord(c->events[2 * i + 2], c->stream));
+    }
+    CK(cudaEventSynchronize(c->events[2 * n]));
+    for (int i = 0; i < n; ++i) {
+        float m1 = 0, m2 = 0;
+        CK(cudaEventElapsedTime(&m1, c->events[2 * i], c->events[2 * i + 1]));
+        CK(cudaEventElapsedTime(&m2, c->events[2 * i + 1], c->events[2 * i + 2]));
+        c->kms[1] += m1;
+        c->kms[2] += m2;
+        c->klaunch[1] += 1;
+        c->klaunch[2] += 1;
+    }
+    return HYDRO_OK;
+}
+
+int run_steps(hydro_ctx *c, const hydro_state_t *s, int n) {
+    if (n <= 0) return HYDRO_OK;
+    if (c->profiling) return run_steps_profiled(c, s, n);
+    int left = n;
+    while (left > 0) {
+        int chunk = kMaxChunk;
+        while (chunk > left) chunk >>= 1;
+        cudaGraphExec_t g = nullptr;
+        int rc = get_graph(c, s, chunk, &g);
+        if (rc) return rc;
+        CK(cudaGraphLaunch(g, c->stream));
+        left -= chunk;
+    }
+    return HYDRO_OK;
+}
+
+int finish_steps(hydro_ctx *c, double *t_inout, int32_t *steps_done) {
+    if (!t_inout && !steps_done) return HYDRO_OK;
+    Ctrl h;
+    CK(cudaMemcpyAsync(&h, c->ctrl, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (t_inout) *t_inout = h.t;
+    if (steps_done) *steps_done = h.steps;
+    return (h.status & hydro::STATUS_NONFINITE) ? HYDRO_ENONFINITE : HYDRO_OK;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+int hydro_version(void) { return HYDRO_ABI_VERSION; }
+
+const char *hydro_strerror(int status) {
+    switch (status) {
+        case HYDRO_OK: return "ok";
+        case HYDRO_EINVAL: return "invalid argument";
+        case HYDRO_ECUDA: return "CUDA runtime error";
+        case HYDRO_ENONFINITE: return "non-finite value or non-positive density/pressure";
+        case HYDRO_ETIMEOUT: return "bounded device wait timed out";
+        case HYDRO_EUNSUPPORTED: return "no kernel compiled for this request";
+        default: return "unknown status";
+    }
+}
+
+const char *hydro_last_cuda_error(void) { return g_cuda_err; }
+
+int hydro_variant_supported(int32_t prec, int32_t dim, const hydro_variant_t *variant) {
+    if (prec != HYDRO_F32 && prec != HYDRO_F64) return 0;
+    if (dim < 1 || dim > 3) return 0;
+    hydro_variant_t v;
+    return resolve_variant(prec, dim, variant, &v) ? 1 : 0;
+}
+
+int hydro_workspace_bytes(const hydro_grid_t *grid, int32_t prec, size_t *bytes_out) {
+    long long ncell = 0;
+    if (!bytes_out || !grid_ok(grid, &ncell)) return HYDRO_EINVAL;
+    if (prec != HYDRO_F32 && prec != HYDRO_F64) return HYDRO_EINVAL;
+    *bytes_out = layout_for(grid->dim, ncell, prec).total;
+    return HYDRO_OK;
+}
+
+int hydro_create(const hydro_grid_t *grid, double gamma, const int32_t bc[3], int32_t prec,
+                 double cfl, const hydro_variant_t *variant, void *workspace,
+                 size_t workspace_bytes, void *stream, hydro_ctx_t **out) {
+    if (!out) return HYDRO_EINVAL;
+    *out = nullptr;
+    long long ncell = 0;
+    if (!grid_ok(grid, &ncell) || !bc || !workspace) return HYDRO_EINVAL;
+    if (prec != HYDRO_F32 && prec != HYDRO_F64) return HYDRO_EINVAL;
+    if (!(gamma > 1.0) || !(gamma < 1e300) || !(cfl > 0.0) || !(cfl < 1e300)) return HYDRO_EINVAL;
+    for (int a = 0; a < grid->dim; ++a)
+        if (bc[a] != HYDRO_BC_PERIODIC && bc[a] != HYDRO_BC_OUTFLOW) return HYDRO_EINVAL;
+    if (((uintptr_t)workspace) % kAlign) return HYDRO_EINVAL;
+    const Layout lay = layout_for(grid->dim, ncell, prec);
+    if (workspace_bytes < lay.total) return HYDRO_EINVAL;
+    hydro_variant_t var;
+    if (!resolve_variant(prec, grid->dim, variant, &var)) return HYDRO_EUNSUPPORTED;
+    // grid-dimension limits of the stage launch
+    if (grid->dim >= 2 && (grid->n[1] + var.tile_y - 1) / var.tile_y > 65535) return HYDRO_EUNSUPPORTED;
+    if (grid->dim == 3 && (grid->n[2] + var.march - 1) / var.march > 65535) return HYDRO_EUNSUPPORTED;
+
+    hydro_ctx *c = new (std::nothrow) hydro_ctx();
+    if (!c) return HYDRO_EINVAL;
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        delete c;
+        return cuda_fail(cudaGetLastError(), "cudaGetDevice");
+    }
+    c->dim = grid->dim;
+    c->prec = prec;
+    c->ncell = ncell;
+    for (int a = 0; a < 3; ++a) {
+        const bool act = a < grid->dim;
+        c->n[a] = act ? (int)grid->n[a] : 1;
+        c->periodic[a] = act ? (bc[a] == HYDRO_BC_PERIODIC) : 1;
+        c->dr[a] = act ? (grid->hi[a] - grid->lo[a]) / (double)grid->n[a] : 1.0;
+    }
+    if (c->dim == 3 && var.march > c->n[2]) var.march = c->n[2];
+    c->gamma = gamma;
+    c->cfl = cfl;
+    c->var = var;
+    c->lay = lay;
+    c->ws = static_cast<unsigned char *>(workspace);
+    c->ctrl = reinterpret_cast<Ctrl *>(c->ws + lay.ctrl_off);
+    c->parts = reinterpret_cast<double *>(c->ws + lay.parts_off);
+    const size_t plane = align_up((size_t)ncell * (prec == HYDRO_F32 ? 4 : 8));
+    for (int k = 0; k < c->dim + 2; ++k) c->u1[k] = c->ws + lay.u1_off + plane * (size_t)k;
+    c->stream = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        delete c;
+        return cuda_fail(e, "cudaStreamCreateWithFlags");
+    }
+    hydro_state_t dummy;
+    memset(&dummy, 0, sizeof dummy);
+    e = launch_stage(c, stage_args(c, &dummy, 1), c->stream, /*prepare_only=*/true);
+    if (e != cudaSuccess) {
+        cudaStreamDestroy(c->cap);
+        delete c;
+        return cuda_fail(e, "stage kernel attributes");
+    }
+    *out = c;
+    return HYDRO_OK;
+}
+
+int hydro_destroy(hydro_ctx_t *c) {
+    if (!c) return HYDRO_EINVAL;
+    DeviceGuard dg(c->device);
+    for (auto &g : c->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    for (auto e : c->events) cudaEventDestroy(e);
+    if (c->cap) cudaStreamDestroy(c->cap);
+    delete c;
+    return HYDRO_OK;
+}
+
+int hydro_set_stream(hydro_ctx_t *c, void *stream) {
+    if (!c) return HYDRO_EINVAL;
+    c->stream = static_cast<cudaStream_t>(stream);
+    return HYDRO_OK;
+}
+
+int hydro_step(hydro_ctx_t *c, const hydro_state_t *state, int32_t n_steps, double t_end,
+               double *t_inout, int32_t *steps_done) {
+    if (!c || !state_ok(c, state) || n_steps < 0) return HYDRO_EINVAL;
+    if (t_end != t_end) return HYDRO_EINVAL;
+    DeviceGuard dg(c->device);
+    const double t0 = t_inout ? *t_inout : 0.0;
+    if (t0 != t0) return HYDRO_EINVAL;
+    int rc = begin_steps(c, state, t0, t_end);
+    if (rc) return rc;
+    rc = run_steps(c, state, n_steps);
+    if (rc) return rc;
+    return finish_steps(c, t_inout, steps_done);
+}
+
+int hydro_step_host(hydro_ctx_t *c, const hydro_state_t *dev, const void *const host_in[5],
+                    void *const host_out[5], int32_t n_steps, double t_end, double *t_inout,
+                    int32_t *steps_done) {
+    if (!c || !state_ok(c, dev) || !host_in || !host_out || n_steps < 0) return HYDRO_EINVAL;
+    for (int k = 0; k < c->dim + 2; ++k)
+        if (!host_in[k] || !host_out[k]) return HYDRO_EINVAL;
+    DeviceGuard dg(c->device);
+    const size_t bytes = (size_t)c->ncell * (c->prec == HYDRO_F32 ? 4 : 8);
+    for (int k = 0; k < c->dim + 2; ++k)
+        CK(cudaMemcpyAsync(dev->plane[k], host_in[k], bytes, cudaMemcpyHostToDevice, c->stream));
+    double t = t_inout ? *t_inout : 0.0;
+    int32_t done = 0;
+    int rc = begin_steps(c, dev, t, t_end);
+    if (!rc) rc = run_steps(c, dev, n_steps);
+    if (rc) return rc;
+    for (int k = 0; k < c->dim + 2; ++k)
+        CK(cudaMemcpyAsync(host_out[k], dev->plane[k], bytes, cudaMemcpyDeviceToHost, c->stream));
+    rc = finish_steps(c, &t, &done);
+    if (t_inout) *t_inout = t;
+    if (steps_done) *steps_done = done;
+    return rc;
+}
+
+int hydro_cfl_dt(hydro_ctx_t *c, const hydro_state_t *state, double *dt_out) {
+    if (!c || !state_ok(c, state) || !dt_out) return HYDRO_EINVAL;
+    DeviceGuard dg(c->device);
+    int rc = begin_steps(c, state, 0.0, 0.0);
+    if (rc) return rc;
+    Ctrl h;
+    CK(cudaMemcpyAsync(&h, c->ctrl, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    *dt_out = h.dt;
+    return (h.status & hydro::STATUS_NONFINITE) ? HYDRO_ENONFINITE : HYDRO_OK;
+}
+
+int hydro_totals(hydro_ctx_t *c, const hydro_state_t *state, double out[5]) {
+    if (!c || !state_ok(c, state) || !out) return HYDRO_EINVAL;
+    DeviceGuard dg(c->device);
+    double vol = 1.0;
+    for (int a = 0; a < c->dim; ++a) vol *= c->dr[a];
+    CK(hydro::launch_totals(aux_args(c, state), c->parts, hydro::kTotalsParts, vol, c->stream));
+    CK(cudaMemcpyAsync(out, c->ctrl->totals, sizeof(double) * 5, cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return HYDRO_OK;
+}
+
+int hydro_status(hydro_ctx_t *c) {
+    if (!c) return HYDRO_EINVAL;
+    DeviceGuard dg(c->device);
+    unsigned int st = 0;
+    CK(cudaMemcpyAsync(&st, &c->ctrl->status, sizeof st, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return (st & hydro::STATUS_NONFINITE) ? HYDRO_ENONFINITE : HYDRO_OK;
+}
+
+static int convert(int32_t dim, int64_t ncell, double gamma, int32_t prec, const hydro_state_t *in,
+                   const hydro_state_t *out, void *stream, int to_cons) {
+    if (dim < 1 || dim > 3 || ncell < 0 || !in || !out || !(gamma > 1.0)) return HYDRO_EINVAL;
+    if (prec != HYDRO_F32 && prec != HYDRO_F64) return HYDRO_EINVAL;
+    if (ncell == 0) return HYDRO_OK;
+    hydro::AuxArgs A;
+    memset(&A, 0, sizeof A);
+    A.prec = prec;
+    A.dim = dim;
+    A.ncell = ncell;
+    A.gamma = gamma;
+    for (int k = 0; k < dim + 2; ++k) {
+        if (!in->plane[k] || !out->plane[k]) return HYDRO_EINVAL;
+        A.u[k] = in->plane[k];
+        A.out[k] = out->plane[k];
+    }
+    CK(hydro::launch_convert(A, to_cons, static_cast<cudaStream_t>(stream)));
+    return HYDRO_OK;
+}
+
+int hydro_prim_to_cons(int32_t dim, int64_t ncell, double gamma, int32_t prec,
+                       const hydro_state_t *prim_in, const hydro_state_t *cons_out, void *stream) {
+    return convert(dim, ncell, gamma, prec, prim_in, cons_out, stream, 1);
+}
+
+int hydro_cons_to_prim(int32_t dim, int64_t ncell, double gamma, int32_t prec,
+                       const hydro_state_t *cons_in, const hydro_state_t *prim_out, void *stream) {
+    return convert(dim, ncell, gamma, prec, cons_in, prim_out, stream, 0);
+}
+
+int hydro_set_profiling(hydro_ctx_t *c, int32_t on) {
+    if (!c) return HYDRO_EINVAL;
+    c->profiling = on != 0;
+    return HYDRO_OK;
+}
+
+int hydro_kernel_times(hydro_ctx_t *c, double *ms_out, int64_t *launches_out, int32_t n,
+                       int32_t reset) {
+    if (!c || n < 0 || (n > 0 && (!ms_out || !launches_out))) return HYDRO_EINVAL;
+    DeviceGuard dg(c->device);
+    CK(cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < n && k < 3; ++k) {
+        ms_out[k] = c->kms[k];
+        launches_out[k] = c->klaunch[k];
+    }
+    for (int k = 3; k < n; ++k) {
+        ms_out[k] = 0;
+        launches_out[k] = 0;
+    }
+    if (reset)
+        for (int k = 0; k < 3; ++k) {
+            c->kms[k] = 0;
+            c->klaunch[k] = 0;
+        }
+    return HYDRO_OK;
+}
+
+}  // extern "C"

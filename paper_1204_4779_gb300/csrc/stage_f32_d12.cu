@@ -1,0 +1,20 @@
+// FP32 RK-stage kernels, dims 1 and 2 (compiled with FMA contraction).
+#include "stage_launch.cuh"
+
+namespace hydro {
+
+cudaError_t stage_f32_d1(const StageLaunch &L, cudaStream_t st, bool prepare_only) {
+    HYDRO_STAGE_CASE(float, 1, 128, 1)
+    HYDRO_STAGE_CASE(float, 1, 256, 1)
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t stage_f32_d2(const StageLaunch &L, cudaStream_t st, bool prepare_only) {
+    HYDRO_STAGE_CASE(float, 2, 32, 8)
+    HYDRO_STAGE_CASE(float, 2, 64, 4)
+    HYDRO_STAGE_CASE(float, 2, 16, 16)
+    HYDRO_STAGE_CASE(float, 2, 32, 16)
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace hydro

@@ -1,0 +1,26 @@
+// FP64 RK-stage kernels, dims 1-3.  Compiled with --fmad=false: every operation of the
+// stencil is one correctly rounded IEEE-754 operation, in the order of the plain formulas.
+#include "stage_launch.cuh"
+
+namespace hydro {
+
+cudaError_t stage_f64(int dim, const StageLaunch &L, cudaStream_t st, bool prepare_only) {
+    if (dim == 1) {
+        HYDRO_STAGE_CASE(double, 1, 128, 1)
+    } else if (dim == 2) {
+        HYDRO_STAGE_CASE(double, 2, 32, 8)
+    } else if (dim == 3) {
+        HYDRO_STAGE_CASE(double, 3, 32, 8)
+    }
+    return cudaErrorInvalidValue;
+}
+
+const TileShape kTiles[] = {
+    {1, 1, 128, 1}, {1, 1, 256, 1},
+    {1, 2, 32, 8},  {1, 2, 64, 4},  {1, 2, 16, 16}, {1, 2, 32, 16},
+    {1, 3, 32, 8},  {1, 3, 32, 4},  {1, 3, 64, 4},  {1, 3, 16, 16}, {1, 3, 32, 16},
+    {0, 1, 128, 1}, {0, 2, 32, 8},  {0, 3, 32, 8},
+};
+const int kNumTiles = sizeof(kTiles) / sizeof(kTiles[0]);
+
+}  // namespace hydro

@@ -1,0 +1,346 @@
+// Fused RK-stage kernel of the compressible-Euler step (arXiv:1204.4779, section 4.1).
+//
+// One launch computes, for every cell i,
+//     U_out[i] = U_base[i] + sum_a (c dt / dr_a) (F_a[i - e_a/2] - F_a[i + e_a/2]),
+//     F_a = HLLC_a(MinBee faces of V(U_in)),
+// i.e. Flux_a followed by AddFlux (Eq. eqAddFlux):
+//     stage 1: U_in = U0, U_base = U0, U_out = U1, c = 1/2
+//     stage 2: U_in = U1, U_base = U0, U_out = U0 (in place), c = 1
+// Stage 2 also computes the CFL signal of every new cell and the dt of the next step
+// (warp shuffle -> CTA -> one atomic per CTA -> the last CTA finalises dt on the device).
+//
+// Tiling.  A CTA owns a BX x BY tile of the (x, y) plane (dim 1: a BX row).  In dim 3 it
+// marches through `march` z-planes.  Per plane:
+//   * V of the tile plus a cross-shaped halo of two cells (the stencil needs no corners) is
+//     recovered from U and staged in shared memory; the halo comes from global memory with
+//     the boundary condition applied by index remapping (no ghost cells in HBM);
+//   * every x- and y-face of the tile is evaluated ONCE (BX+1 per row, BY+1 per column),
+//     spread over all threads, the fluxes kept in shared memory;
+//   * the z-face above each column is evaluated by its own thread from a register pipeline
+//     of the column's V(z), V(z+1), V(z+2), carrying the z-slope and the flux of the face
+//     below from the previous plane, so z-faces are also evaluated once;
+//   * the next plane's loads (own column two planes ahead, halo, U_base) are issued before
+//     the current plane's flux work, hiding their latency.
+// HBM traffic per stage: read U_in and U_base, write U_out once; halo re-reads hit L2.
+#pragma once
+
+#include <type_traits>
+
+#include "hydro_device.cuh"
+
+namespace hydro {
+
+template <class T> struct StageArgs {
+    const T *uin[5];    // flux source (never written by this launch)
+    const T *ubase[5];  // U0
+    T *uout[5];         // U1 (stage 1) or U0 (stage 2, in place over ubase)
+    int n[3];
+    int periodic[3];
+    int march;          // z-planes per CTA (dim 3)
+    double dr[3];
+    Gas<T> gas;
+    Ctrl *ctrl;
+};
+
+template <class T, int D, int BX, int BY> struct StageShape {
+    static constexpr int NV = D + 2;
+    static constexpr int NT = BX * BY;
+    static constexpr int HX = BX + 4;
+    static constexpr int HY = (D >= 2) ? BY + 4 : 1;
+    static constexpr int PL = HY * HX;  // shared plane of one field
+    static constexpr int NFX = (BX + 1) * BY;
+    static constexpr int NFY = (D >= 2) ? BX * (BY + 1) : 0;
+    static constexpr int NF = NFX + NFY;
+    static constexpr int NH = (D >= 2) ? 4 * BY + 4 * BX : 4;
+    static constexpr int HPT = (NH + NT - 1) / NT;  // halo cells per thread
+    static constexpr int FPT = (NF + NT - 1) / NT;  // in-plane faces per thread
+    static constexpr size_t smem_bytes = sizeof(T) * (size_t)(NV * PL + NV * NF + 2 * (NT / 32));
+};
+
+// Flux of one in-plane face from the staged primitive plane.  `o`: shared index of the
+// first of the four cells q0..q3 along the normal, `s`: their stride, `a`: the normal axis
+// (0 or 1).  Face between q1 and q2.  Writes the flux in axis order to sF (field stride NF).
+template <class T, int D, int PL, int NF>
+__device__ __forceinline__ void inplane_face(const T *__restrict__ sV, T *__restrict__ sF, int o,
+                                             int s, int a, int f, const Gas<T> &G) {
+    constexpr int NV = D + 2;
+    // field of the normal velocity, then tangential ones in increasing axis order
+    int fld[D];
+    fld[0] = 1 + a;
+    if constexpr (D >= 2) fld[1] = 2 - a;
+    if constexpr (D == 3) fld[2] = 3;
+    T L[NV], R[NV];  // (rho, normal-first velocities, p)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        const int field = (k == 0) ? 0 : (k == NV - 1 ? NV - 1 : fld[k - 1]);
+        const T *q = sV + field * PL + o;
+        const T q0 = q[0], q1 = q[s], q2 = q[2 * s], q3 = q[3 * s];
+        const T d01 = q1 - q0, d12 = q2 - q1, d23 = q3 - q2;
+        L[k] = q1 + T(0.5) * minbee(d01, d12);
+        R[k] = q2 - T(0.5) * minbee(d12, d23);
+    }
+    T vl[D], vr[D], F[NV];
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+        vl[b] = L[1 + b];
+        vr[b] = R[1 + b];
+    }
+    hllc<T, D, false>(L[0], vl, L[NV - 1], R[0], vr, R[NV - 1], G, F);
+    sF[f] = F[0];
+#pragma unroll
+    for (int b = 0; b < D; ++b) sF[fld[b] * NF + f] = F[1 + b];
+    sF[(NV - 1) * NF + f] = F[NV - 1];
+}
+
+// Flux of the z-face between a column's cells z (lower) and z+1 (upper) from their primitive
+// states and MinBee slopes.  Returned normal-first: (mass, m_z, m_x, m_y, E).
+template <class T>
+__device__ __forceinline__ void fz_face(const T (&Vlo)[5], const T (&dlo)[5], const T (&Vhi)[5],
+                                        const T (&dhi)[5], const Gas<T> &G, T (&F)[5]) {
+    T L[5], R[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        L[k] = Vlo[k] + T(0.5) * dlo[k];
+        R[k] = Vhi[k] - T(0.5) * dhi[k];
+    }
+    const T vl[3] = {L[3], L[1], L[2]};
+    const T vr[3] = {R[3], R[1], R[2]};
+    hllc<T, 3, true>(L[0], vl, L[4], R[0], vr, R[4], G, F);
+}
+
+template <class T, int NT> struct MinBlocks {
+    static constexpr int value = (sizeof(T) == 4 && NT <= 256) ? 2 : 1;
+};
+
+template <class T, int D, int BX, int BY, int STAGE>
+__global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY>::value))
+    stage_kernel(const StageArgs<T> A) {
+    using S = StageShape<T, D, BX, BY>;
+    constexpr int NV = S::NV, NT = S::NT, HX = S::HX, PL = S::PL;
+    constexpr int NFX = S::NFX, NF = S::NF, NH = S::NH, HPT = S::HPT, FPT = S::FPT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sV = reinterpret_cast<T *>(smem_raw);
+    T *sF = sV + NV * PL;
+    T *sRed = sF + NV * NF;
+
+    Ctrl *ctrl = A.ctrl;
+    const double dt = __ldcg(&ctrl->dt);
+    if (!(dt > 0.0)) return;  // uniform over the grid: no step to take
+    const double dts = (STAGE == 1) ? 0.5 * dt : dt;
+    const T cx = T(dts / A.dr[0]);
+    const T cy = (D >= 2) ? T(dts / A.dr[1]) : T(0);
+    const T cz = (D == 3) ? T(dts / A.dr[2]) : T(0);
+    const Gas<T> G = A.gas;
+
+    const int tid = threadIdx.x;
+    const int tx = tid % BX, ty = tid / BX;
+    const int nx = A.n[0], ny = A.n[1], nz = A.n[2];
+    const int nxy = nx * ny;
+    const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
+    const int x = x0 + tx, y = y0 + ty;
+    const bool active = (x < nx) && (y < ny);
+    const int own_off = remap(y, ny, A.periodic[1]) * nx + remap(x, nx, A.periodic[0]);
+    const int own_s = (D >= 2) ? (ty + 2) * HX + (tx + 2) : (tx + 2);
+
+    // halo cells of this thread: plane offset and shared index
+    int h_off[HPT], h_s[HPT];
+    bool h_ok[HPT];
+#pragma unroll
+    for (int j = 0; j < HPT; ++j) {
+        const int h = tid + j * NT;
+        h_ok[j] = h < NH;
+        int lx, ly;
+        if constexpr (D >= 2) {
+            if (h < 4 * BY) {
+                const int c = h & 3;
+                ly = (h >> 2) + 2;
+                lx = c < 2 ? c : BX + c;
+            } else {
+                const int g = h - 4 * BY;
+                const int r = g / BX;
+                lx = g % BX + 2;
+                ly = r < 2 ? r : BY + r;
+            }
+        } else {
+            const int c = h & 3;
+            lx = c < 2 ? c : BX + c;
+            ly = 0;
+        }
+        if (!h_ok[j]) lx = ly = 0;
+        const int xg = remap(x0 + lx - 2, nx, A.periodic[0]);
+        const int yg = (D >= 2) ? remap(y0 + ly - 2, ny, A.periodic[1]) : 0;
+        h_off[j] = yg * nx + xg;
+        h_s[j] = ly * HX + lx;
+    }
+
+    // in-plane face tasks of this thread: shared base index, stride, normal axis
+    int f_o[FPT], f_s[FPT], f_a[FPT];
+#pragma unroll
+    for (int j = 0; j < FPT; ++j) {
+        const int f = tid + j * NT;
+        if (f < NFX) {  // x-face between tile cells (c-1, r) and (c, r)
+            const int r = f / (BX + 1), c = f % (BX + 1);
+            f_o[j] = ((D >= 2) ? (r + 2) * HX : 0) + c;
+            f_s[j] = 1;
+            f_a[j] = 0;
+        } else {  // y-face between (c, r-1) and (c, r)
+            const int g = f - NFX;
+            const int r = g / BX, c = g % BX;
+            f_o[j] = r * HX + c + 2;
+            f_s[j] = HX;
+            f_a[j] = 1;
+        }
+    }
+
+    const int zb = (D == 3) ? blockIdx.z * A.march : 0;
+    const int ze = (D == 3) ? min(zb + A.march, nz) : 1;
+    const int pz = A.periodic[2];
+
+    auto load_u = [&](T (&u)[NV], int zr, int off) {
+        const int i = zr * nxy + off;
+#pragma unroll
+        for (int k = 0; k < NV; ++k) u[k] = __ldg(A.uin[k] + i);
+    };
+
+    // register pipeline along z (dim 3): V(z), V(z+1), slope at z, flux of face z - 1/2
+    T Vc[NV], Vn[NV], dzc[NV], Fzm[NV];
+    T pown[NV];
+    T phalo[HPT][NV];
+    T pbase[NV];
+
+    if constexpr (D == 3) {
+        T u[NV], Vm2[NV], Vm1[NV], dzm[NV];
+        load_u(u, remap(zb - 2, nz, pz), own_off);
+        prim_of_cons<T, D>(u, Vm2, G);
+        load_u(u, remap(zb - 1, nz, pz), own_off);
+        prim_of_cons<T, D>(u, Vm1, G);
+        load_u(u, remap(zb, nz, pz), own_off);
+        prim_of_cons<T, D>(u, Vc, G);
+        load_u(u, remap(zb + 1, nz, pz), own_off);
+        prim_of_cons<T, D>(u, Vn, G);
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            dzm[k] = minbee(Vm1[k] - Vm2[k], Vc[k] - Vm1[k]);
+            dzc[k] = minbee(Vc[k] - Vm1[k], Vn[k] - Vc[k]);
+        }
+        fz_face(Vm1, dzm, Vc, dzc, G, Fzm);
+        load_u(pown, remap(zb + 2, nz, pz), own_off);
+    } else {
+        load_u(pown, 0, own_off);  // the cell itself
+    }
+#pragma unroll
+    for (int j = 0; j < HPT; ++j)
+        if (h_ok[j]) load_u(phalo[j], (D == 3) ? remap(zb, nz, pz) : 0, h_off[j]);
+    {
+        const int i = ((D == 3) ? zb * nxy : 0) + (active ? y * nx + x : 0);
+#pragma unroll
+        for (int k = 0; k < NV; ++k) pbase[k] = active ? A.ubase[k][i] : T(0);
+    }
+
+    T smax = T(0);
+    bool bad = false;
+
+    for (int z = zb; z < ze; ++z) {
+        T Vnn[NV];
+        if constexpr (D == 3) {
+            prim_of_cons<T, D>(pown, Vnn, G);
+        } else {
+            prim_of_cons<T, D>(pown, Vc, G);
+        }
+        // stage V of the plane: own cell and halo
+#pragma unroll
+        for (int k = 0; k < NV; ++k) sV[k * PL + own_s] = Vc[k];
+#pragma unroll
+        for (int j = 0; j < HPT; ++j) {
+            if (h_ok[j]) {
+                T vh[NV];
+                prim_of_cons<T, D>(phalo[j], vh, G);
+#pragma unroll
+                for (int k = 0; k < NV; ++k) sV[k * PL + h_s[j]] = vh[k];
+            }
+        }
+        T base[NV];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) base[k] = pbase[k];
+        if constexpr (D == 3) {
+            // prefetch the next plane
+            if (z + 1 < ze) {
+                load_u(pown, remap(z + 3, nz, pz), own_off);
+#pragma unroll
+                for (int j = 0; j < HPT; ++j)
+                    if (h_ok[j]) load_u(phalo[j], remap(z + 1, nz, pz), h_off[j]);
+                if (active) {
+                    const int i = (z + 1) * nxy + y * nx + x;
+#pragma unroll
+                    for (int k = 0; k < NV; ++k) pbase[k] = A.ubase[k][i];
+                }
+            }
+        }
+        __syncthreads();
+
+        // in-plane faces, each once
+#pragma unroll
+        for (int j = 0; j < FPT; ++j) {
+            const int f = tid + j * NT;
+            if (j < FPT - 1 || f < NF) inplane_face<T, D, PL, NF>(sV, sF, f_o[j], f_s[j], f_a[j], f, G);
+        }
+        // z-face above this column
+        T Fzp[NV], dzn[NV];
+        if constexpr (D == 3) {
+#pragma unroll
+            for (int k = 0; k < NV; ++k) dzn[k] = minbee(Vn[k] - Vc[k], Vnn[k] - Vn[k]);
+            fz_face(Vc, dzc, Vn, dzn, G, Fzp);
+        }
+        __syncthreads();
+
+        if (active) {
+            const int fxl = ty * (BX + 1) + tx;
+            const int fyb = NFX + ty * BX + tx;
+            T un[NV];
+#pragma unroll
+            for (int k = 0; k < NV; ++k) {
+                T sum = cx * (sF[k * NF + fxl] - sF[k * NF + fxl + 1]);
+                if constexpr (D >= 2) sum = sum + cy * (sF[k * NF + fyb] - sF[k * NF + fyb + BX]);
+                if constexpr (D == 3) {
+                    // z fluxes are normal-first: (mass, m_z, m_x, m_y, E)
+                    const int kk = (k == 0 || k == NV - 1) ? k : (k == 3 ? 1 : k + 1);
+                    sum = sum + cz * (Fzm[kk] - Fzp[kk]);
+                }
+                un[k] = base[k] + sum;
+            }
+            const int i = ((D == 3) ? z * nxy : 0) + y * nx + x;
+#pragma unroll
+            for (int k = 0; k < NV; ++k) A.uout[k][i] = un[k];
+            if constexpr (STAGE == 2) {
+                // CFL signal of the new state: sum_a (|v_a| + c_s) / dr_a
+                T v[NV];
+                prim_of_cons<T, D>(un, v, G);
+                T cs, s = T(0);
+                if constexpr (Arith<T>::exact) {
+                    cs = sqrt(G.g * v[NV - 1] / v[0]);
+#pragma unroll
+                    for (int a = 0; a < D; ++a) s = s + (fabs(v[1 + a]) + cs) / T(A.dr[a]);
+                } else {
+                    cs = Arith<float>::sqrt_(G.g * v[NV - 1] * Arith<float>::rcp(v[0]));
+#pragma unroll
+                    for (int a = 0; a < D; ++a) s = fmaf(fabsf(v[1 + a]) + cs, T(1.0 / A.dr[a]), s);
+                }
+                smax = (s > smax || s != s) ? s : smax;
+                bad |= !(v[0] > T(0)) || !(v[NV - 1] > T(0));
+            }
+        }
+        if constexpr (D == 3) {
+#pragma unroll
+            for (int k = 0; k < NV; ++k) {
+                Vc[k] = Vn[k];
+                Vn[k] = Vnn[k];
+                dzc[k] = dzn[k];
+                Fzm[k] = Fzp[k];
+            }
+        }
+    }
+
+    if constexpr (STAGE == 2) reduce_signal_and_finalize<T, NT>(ctrl, smax, bad, true, sRed);
+}
+
+}  // namespace hydro

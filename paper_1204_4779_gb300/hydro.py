@@ -1,0 +1,290 @@
+"""Python binding of libhydro.so (include/hydro.h): argument marshalling only.
+
+PyTorch supplies device memory and the current CUDA stream; every step of the solver runs in
+the library's kernels.  There is no CPU fallback: if libhydro.so cannot be loaded (or built
+with nvcc) the constructor raises.
+
+State tensors have shape (dim+2, [nz, [ny,]] nx), contiguous, planes (rho, m_x, [m_y, [m_z]],
+E) for conserved or (rho, v_x, [v_y, [v_z]], p) for primitive variables, dtype float32 or
+float64 on a CUDA device.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libhydro.so")
+
+HYDRO_OK, HYDRO_EINVAL, HYDRO_ECUDA, HYDRO_ENONFINITE, HYDRO_ETIMEOUT, HYDRO_EUNSUPPORTED = range(6)
+HYDRO_BC_PERIODIC, HYDRO_BC_OUTFLOW = 0, 1
+HYDRO_F64, HYDRO_F32 = 0, 1
+
+# every symbol include/hydro.h declares
+EXPORTS = (
+    "hydro_version", "hydro_strerror", "hydro_last_cuda_error", "hydro_variant_supported",
+    "hydro_workspace_bytes", "hydro_create", "hydro_destroy", "hydro_set_stream", "hydro_step",
+    "hydro_step_host", "hydro_cfl_dt", "hydro_totals", "hydro_status", "hydro_prim_to_cons",
+    "hydro_cons_to_prim", "hydro_set_profiling", "hydro_kernel_times",
+)
+
+
+class HydroError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        lib = _lib
+        msg = lib.hydro_strerror(status).decode() if lib else str(status)
+        if status == HYDRO_ECUDA and lib:
+            msg += ": " + lib.hydro_last_cuda_error().decode()
+        super().__init__(f"{what}: {msg}")
+        self.status = status
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("n", ctypes.c_int64 * 3), ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3)]
+
+
+class State(ctypes.Structure):
+    _fields_ = [("plane", ctypes.c_void_p * 5)]
+
+
+class Variant(ctypes.Structure):
+    _fields_ = [("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32),
+                ("march", ctypes.c_int32), ("split", ctypes.c_int32)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load_library(path: str = LIB_PATH, build_if_missing: bool = True):
+    """Load libhydro.so (building it with nvcc first if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path) and build_if_missing:
+            from . import _build
+            _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libhydro.so not found at {path}; build it with "
+                               "`python -m paper_1204_4779_gb300._build`")
+        lib = ctypes.CDLL(path)
+        vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        P = ctypes.POINTER
+        sig = {
+            "hydro_version": ([], ctypes.c_int),
+            "hydro_strerror": ([ctypes.c_int], ctypes.c_char_p),
+            "hydro_last_cuda_error": ([], ctypes.c_char_p),
+            "hydro_variant_supported": ([i32, i32, P(Variant)], ctypes.c_int),
+            "hydro_workspace_bytes": ([P(Grid), i32, P(ctypes.c_size_t)], ctypes.c_int),
+            "hydro_create": ([P(Grid), dbl, P(i32), i32, dbl, P(Variant), vp, ctypes.c_size_t, vp,
+                              P(vp)], ctypes.c_int),
+            "hydro_destroy": ([vp], ctypes.c_int),
+            "hydro_set_stream": ([vp, vp], ctypes.c_int),
+            "hydro_step": ([vp, P(State), i32, dbl, P(dbl), P(i32)], ctypes.c_int),
+            "hydro_step_host": ([vp, P(State), P(vp), P(vp), i32, dbl, P(dbl), P(i32)], ctypes.c_int),
+            "hydro_cfl_dt": ([vp, P(State), P(dbl)], ctypes.c_int),
+            "hydro_totals": ([vp, P(State), P(dbl)], ctypes.c_int),
+            "hydro_status": ([vp], ctypes.c_int),
+            "hydro_prim_to_cons": ([i32, i64, dbl, i32, P(State), P(State), vp], ctypes.c_int),
+            "hydro_cons_to_prim": ([i32, i64, dbl, i32, P(State), P(State), vp], ctypes.c_int),
+            "hydro_set_profiling": ([vp, i32], ctypes.c_int),
+            "hydro_kernel_times": ([vp, P(dbl), P(i64), i32, i32], ctypes.c_int),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def _check(rc: int, what: str):
+    if rc != HYDRO_OK:
+        raise HydroError(rc, what)
+
+
+def _prec(dtype) -> int:
+    if dtype == torch.float32:
+        return HYDRO_F32
+    if dtype == torch.float64:
+        return HYDRO_F64
+    raise ValueError(f"unsupported dtype {dtype}")
+
+
+def _stream_ptr(device) -> int:
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+def state_struct(t: torch.Tensor, nv: int) -> State:
+    """Plane pointers of a contiguous (nv, ...) tensor."""
+    if not t.is_contiguous():
+        raise ValueError("state tensors must be contiguous")
+    s = State()
+    plane_bytes = t[0].numel() * t.element_size()
+    base = t.data_ptr()
+    for k in range(nv):
+        s.plane[k] = base + k * plane_bytes
+    return s
+
+
+def variant_supported(dtype, dim: int, tile=(0, 0), march: int = 0) -> bool:
+    lib = load_library()
+    v = Variant(int(tile[0]), int(tile[1]), int(march), 0)
+    return bool(lib.hydro_variant_supported(_prec(dtype), dim, ctypes.byref(v)))
+
+
+def _convert(x: torch.Tensor, gamma: float, to_cons: bool) -> torch.Tensor:
+    lib = load_library()
+    dim = x.dim() - 1
+    out = torch.empty_like(x)
+    si, so = state_struct(x, dim + 2), state_struct(out, dim + 2)
+    fn = lib.hydro_prim_to_cons if to_cons else lib.hydro_cons_to_prim
+    _check(fn(dim, x[0].numel(), float(gamma), _prec(x.dtype), ctypes.byref(si), ctypes.byref(so),
+              _stream_ptr(x.device)), "convert")
+    return out
+
+
+def prim_to_cons(V: torch.Tensor, gamma: float) -> torch.Tensor:
+    """Conserved planes from primitive planes on the GPU (m = rho v, E = p/(g-1) + rho v^2/2)."""
+    return _convert(V.contiguous(), gamma, True)
+
+
+def cons_to_prim(U: torch.Tensor, gamma: float) -> torch.Tensor:
+    return _convert(U.contiguous(), gamma, False)
+
+
+class Solver:
+    """One context of libhydro.so on the current CUDA device.
+
+    shape: cells per axis (nx, [ny, [nz]]); bc: per-axis "periodic"/"outflow" (or 0/1);
+    variant: dict(tile=(bx, by), march=m) or None for the default.
+    """
+
+    def __init__(self, shape, gamma: float, bc="periodic", dtype=torch.float32, cfl: float = 0.4,
+                 variant=None, lo=None, hi=None, device=None):
+        self.lib = load_library()
+        self.dim = len(shape)
+        self.shape = tuple(int(s) for s in shape)
+        self.nv = self.dim + 2
+        self.gamma = float(gamma)
+        self.cfl = float(cfl)
+        self.dtype = dtype
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        if isinstance(bc, (str, int)):
+            bc = [bc] * self.dim
+        self.bc = [HYDRO_BC_PERIODIC if b in ("periodic", 0) else HYDRO_BC_OUTFLOW for b in bc]
+        g = Grid()
+        g.dim = self.dim
+        for a in range(3):
+            g.n[a] = self.shape[a] if a < self.dim else 1
+            g.lo[a] = 0.0 if lo is None else float(lo[a]) if a < self.dim else 0.0
+            g.hi[a] = 1.0 if hi is None else float(hi[a]) if a < self.dim else 1.0
+        self.grid = g
+        nbytes = ctypes.c_size_t()
+        _check(self.lib.hydro_workspace_bytes(ctypes.byref(g), _prec(dtype), ctypes.byref(nbytes)),
+               "hydro_workspace_bytes")
+        self.workspace = torch.empty(int(nbytes.value), dtype=torch.uint8, device=self.device)
+        var = None
+        if variant:
+            tile = variant.get("tile", (0, 0))
+            var = Variant(int(tile[0]), int(tile[1]), int(variant.get("march", 0)), 0)
+        bcs = (ctypes.c_int32 * 3)(*(self.bc + [0] * (3 - self.dim)))
+        ctx = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(self.lib.hydro_create(ctypes.byref(g), self.gamma, bcs, _prec(dtype), self.cfl,
+                                         ctypes.byref(var) if var is not None else None,
+                                         self.workspace.data_ptr(), int(nbytes.value),
+                                         _stream_ptr(self.device), ctypes.byref(ctx)), "hydro_create")
+        self.ctx = ctx
+
+    # -- lifetime --------------------------------------------------------------------------
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.hydro_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- helpers ---------------------------------------------------------------------------
+    def empty_state(self) -> torch.Tensor:
+        return torch.empty((self.nv,) + tuple(reversed(self.shape)), dtype=self.dtype,
+                           device=self.device)
+
+    def _state(self, U: torch.Tensor) -> State:
+        if U.dtype != self.dtype or U.device != self.device:
+            raise ValueError("state dtype/device does not match the solver")
+        if tuple(U.shape) != (self.nv,) + tuple(reversed(self.shape)):
+            raise ValueError(f"state shape {tuple(U.shape)} does not match the grid")
+        return state_struct(U, self.nv)
+
+    def _sync_stream(self):
+        self.lib.hydro_set_stream(self.ctx, _stream_ptr(self.device))
+
+    # -- the C ABI -------------------------------------------------------------------------
+    def step(self, U: torch.Tensor, n_steps: int, t_end: float = 0.0, t: float = 0.0,
+             sync: bool = True):
+        """Advance U in place; returns (t, steps_done) (None, None when sync=False)."""
+        self._sync_stream()
+        s = self._state(U)
+        if not sync:
+            _check(self.lib.hydro_step(self.ctx, ctypes.byref(s), int(n_steps), float(t_end), None,
+                                       None), "hydro_step")
+            return None, None
+        tt = ctypes.c_double(t)
+        done = ctypes.c_int32()
+        _check(self.lib.hydro_step(self.ctx, ctypes.byref(s), int(n_steps), float(t_end),
+                                   ctypes.byref(tt), ctypes.byref(done)), "hydro_step")
+        return tt.value, done.value
+
+    def step_host(self, U_dev: torch.Tensor, host_in: torch.Tensor, host_out: torch.Tensor,
+                  n_steps: int, t_end: float = 0.0, t: float = 0.0):
+        """Copy host_in -> U_dev, advance, copy U_dev -> host_out, in one library call."""
+        self._sync_stream()
+        s = self._state(U_dev)
+        hi = state_struct(host_in, self.nv)
+        ho = state_struct(host_out, self.nv)
+        pin = (ctypes.c_void_p * 5)(*hi.plane)
+        pout = (ctypes.c_void_p * 5)(*ho.plane)
+        tt = ctypes.c_double(t)
+        done = ctypes.c_int32()
+        _check(self.lib.hydro_step_host(self.ctx, ctypes.byref(s), pin, pout, int(n_steps),
+                                        float(t_end), ctypes.byref(tt), ctypes.byref(done)),
+               "hydro_step_host")
+        return tt.value, done.value
+
+    def cfl_dt(self, U: torch.Tensor) -> float:
+        self._sync_stream()
+        s = self._state(U)
+        dt = ctypes.c_double()
+        _check(self.lib.hydro_cfl_dt(self.ctx, ctypes.byref(s), ctypes.byref(dt)), "hydro_cfl_dt")
+        return dt.value
+
+    def totals(self, U: torch.Tensor):
+        self._sync_stream()
+        s = self._state(U)
+        out = (ctypes.c_double * 5)()
+        _check(self.lib.hydro_totals(self.ctx, ctypes.byref(s), out), "hydro_totals")
+        return list(out)
+
+    def status(self) -> int:
+        return self.lib.hydro_status(self.ctx)
+
+    def set_profiling(self, on: bool):
+        _check(self.lib.hydro_set_profiling(self.ctx, 1 if on else 0), "hydro_set_profiling")
+
+    def kernel_times(self, reset: bool = False):
+        """{kind: (total_ms, launches)} for kinds 'cfl', 'stage1', 'stage2'."""
+        ms = (ctypes.c_double * 3)()
+        n = (ctypes.c_int64 * 3)()
+        _check(self.lib.hydro_kernel_times(self.ctx, ms, n, 3, 1 if reset else 0),
+               "hydro_kernel_times")
+        return {k: (ms[i], n[i]) for i, k in enumerate(("cfl", "stage1", "stage2"))}

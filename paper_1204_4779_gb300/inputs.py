@@ -151,3 +151,20 @@ def batch_grid(nx: int, ny: int, seed: int, index: int) -> np.ndarray:
     |v| <= 0.2 per component (so |v| < 0.3)."""
     return smooth((int(nx), int(ny)), seed=seed * 7919 + index, rho=(0.5, 2.0),
                   p=(0.5, 2.0), vmax=0.2)
+
+
+def blast_3d_torch(n: int = 512, radius_cells: float = 8.0, p_in: float = 10.0,
+                   p_out: float = 1e-3, device="cuda", dtype=None):
+    """Same field as blast_3d, laid out directly in device memory by torch (for grids too large
+    to stage through host numpy arrays)."""
+    import torch
+    dtype = dtype or torch.float64
+    c = (torch.arange(n, device=device, dtype=torch.float64) + 0.5) / n - 0.5
+    h = 1.0 / n
+    r2 = c.view(1, 1, n) ** 2 + c.view(1, n, 1) ** 2 + c.view(n, 1, 1) ** 2  # x, y, z order
+    V = torch.zeros((5, n, n, n), device=device, dtype=dtype)
+    V[0] = 1.0
+    inside = r2 <= (radius_cells * h) ** 2
+    V[4] = p_out
+    V[4][inside] = p_in
+    return V

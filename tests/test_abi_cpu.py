@@ -1,0 +1,101 @@
+"""The C-ABI library loads without a GPU and exports every symbol include/hydro.h declares;
+argument checking that needs no device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1204_4779_gb300 import hydro
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "hydro.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(hydro_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = hydro.load_library()
+    syms = declared_symbols()
+    assert len(syms) >= 17
+    for s in syms:
+        assert hasattr(lib, s), s
+    assert set(syms) == set(hydro.EXPORTS)
+
+
+def test_version_and_strerror():
+    lib = hydro.load_library()
+    assert lib.hydro_version() == 1
+    for code in range(7):
+        assert lib.hydro_strerror(code)
+
+
+def _grid(dim, n, lo=0.0, hi=1.0):
+    g = hydro.Grid()
+    g.dim = dim
+    for a in range(3):
+        g.n[a] = n[a] if a < len(n) else 1
+        g.lo[a] = lo
+        g.hi[a] = hi
+    return g
+
+
+def test_workspace_bytes_and_bad_grids():
+    lib = hydro.load_library()
+    b = ctypes.c_size_t()
+    assert lib.hydro_workspace_bytes(ctypes.byref(_grid(3, (512, 512, 512))), hydro.HYDRO_F32,
+                                     ctypes.byref(b)) == 0
+    assert b.value >= 5 * 512 ** 3 * 4
+    for g in (_grid(0, (4,)), _grid(4, (4,)), _grid(2, (0, 4)), _grid(1, (8,), lo=1.0, hi=1.0),
+              _grid(3, (2048, 2048, 1024))):
+        assert lib.hydro_workspace_bytes(ctypes.byref(g), hydro.HYDRO_F32, ctypes.byref(b)) == \
+            hydro.HYDRO_EINVAL
+    assert lib.hydro_workspace_bytes(ctypes.byref(_grid(1, (8,))), 7, ctypes.byref(b)) == \
+        hydro.HYDRO_EINVAL
+    assert lib.hydro_workspace_bytes(None, 0, ctypes.byref(b)) == hydro.HYDRO_EINVAL
+
+
+def test_create_rejects_bad_arguments_before_touching_the_device():
+    lib = hydro.load_library()
+    g = _grid(2, (16, 16))
+    bc = (ctypes.c_int32 * 3)(0, 0, 0)
+    ctx = ctypes.c_void_p()
+    ws = ctypes.c_void_p(1 << 20)  # never dereferenced: every call below fails validation
+    E = hydro.HYDRO_EINVAL
+    assert lib.hydro_create(ctypes.byref(g), 1.0, bc, 1, 0.4, None, ws, 1 << 30, None, ctypes.byref(ctx)) == E
+    assert lib.hydro_create(ctypes.byref(g), 1.4, bc, 1, 0.0, None, ws, 1 << 30, None, ctypes.byref(ctx)) == E
+    assert lib.hydro_create(ctypes.byref(g), 1.4, bc, 1, 0.4, None, ws, 16, None, ctypes.byref(ctx)) == E
+    assert lib.hydro_create(ctypes.byref(g), 1.4, bc, 1, 0.4, None, ctypes.c_void_p((1 << 20) + 8),
+                            1 << 30, None, ctypes.byref(ctx)) == E
+    assert lib.hydro_create(ctypes.byref(g), 1.4, bc, 1, 0.4, None, None, 1 << 30, None, ctypes.byref(ctx)) == E
+    bad_bc = (ctypes.c_int32 * 3)(0, 5, 0)
+    assert lib.hydro_create(ctypes.byref(g), 1.4, bad_bc, 1, 0.4, None, ws, 1 << 30, None, ctypes.byref(ctx)) == E
+    v = hydro.Variant(7, 7, 0, 0)
+    assert lib.hydro_create(ctypes.byref(g), 1.4, bc, 1, 0.4, ctypes.byref(v), ws, 1 << 30, None,
+                            ctypes.byref(ctx)) == hydro.HYDRO_EUNSUPPORTED
+    assert lib.hydro_create(ctypes.byref(g), 1.4, bc, 1, 0.4, None, ws, 1 << 30, None, None) == E
+    assert not ctx.value
+
+
+def test_null_context_calls_fail_cleanly():
+    lib = hydro.load_library()
+    E = hydro.HYDRO_EINVAL
+    assert lib.hydro_step(None, None, 1, 0.0, None, None) == E
+    assert lib.hydro_cfl_dt(None, None, None) == E
+    assert lib.hydro_totals(None, None, None) == E
+    assert lib.hydro_destroy(None) == E
+    assert lib.hydro_status(None) == E
+    assert lib.hydro_set_profiling(None, 1) == E
+    assert lib.hydro_prim_to_cons(4, 10, 1.4, 0, None, None, None) == E
+
+
+def test_variant_table():
+    import torch
+    assert hydro.variant_supported(torch.float32, 3)
+    assert hydro.variant_supported(torch.float32, 3, (32, 8), 64)
+    assert hydro.variant_supported(torch.float64, 2, (32, 8))
+    assert not hydro.variant_supported(torch.float32, 3, (8, 8))
+    assert not hydro.variant_supported(torch.float32, 4)

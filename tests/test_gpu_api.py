@@ -1,0 +1,165 @@
+"""Behaviour of the C-ABI calls on the GPU: conversions, CFL dt, totals, time clipping,
+error reporting, host-buffer stepping, graph vs. direct launches, determinism."""
+import numpy as np
+import pytest
+
+import oracle
+from _helpers import gpu_run, gpu_state, oracle_run, shape_of
+from paper_1204_4779_gb300 import hydro, inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+F32, F64 = torch.float32, torch.float64
+
+
+@pytest.mark.parametrize("shape", [(33,), (20, 13), (9, 8, 7)])
+def test_conversions_match_oracle_bitwise(shape):
+    V = inputs.smooth(shape, seed=2)
+    U = hydro.prim_to_cons(torch.from_numpy(V).cuda(), 1.4).cpu().numpy()
+    Uo = oracle.prim_to_cons(V, 1.4)
+    assert np.array_equal(U, Uo)
+    V2 = hydro.cons_to_prim(torch.from_numpy(Uo).cuda(), 1.4).cpu().numpy()
+    assert np.array_equal(V2, oracle.cons_to_prim(Uo, 1.4))
+
+
+@pytest.mark.parametrize("shape", [(1024,), (64, 48), (20, 17, 9)])
+def test_cfl_dt_matches_oracle(shape):
+    V = inputs.smooth(shape, seed=3)
+    S = hydro.Solver(shape, 1.4, dtype=F64, cfl=0.4)
+    dt = S.cfl_dt(gpu_state(V, 1.4, F64))
+    assert dt == oracle.cfl_dt(oracle.prim_to_cons(V, 1.4), 1.4, 0.4)
+    S32 = hydro.Solver(shape, 1.4, dtype=F32, cfl=0.4)
+    dt32 = S32.cfl_dt(gpu_state(V, 1.4, F32))
+    assert abs(dt32 - dt) <= 2e-6 * dt
+
+
+@pytest.mark.parametrize("dtype", [F32, F64])
+def test_totals_match_oracle(dtype):
+    V = inputs.smooth((40, 30, 20), seed=5)
+    U = gpu_state(V, 1.4, dtype)
+    S = hydro.Solver((40, 30, 20), 1.4, dtype=dtype)
+    T = np.array(S.totals(U))
+    To = oracle.totals(U.double().cpu().numpy())
+    assert np.allclose(T, To, rtol=1e-13, atol=1e-13 * abs(To[4]))
+    S2 = hydro.Solver((40, 30), 1.4, dtype=dtype)
+    V2 = inputs.smooth((40, 30), seed=6)
+    T2 = np.array(S2.totals(gpu_state(V2, 1.4, dtype)))
+    assert T2[3] == 0.0
+
+
+@pytest.mark.parametrize("dtype,tol", [(F64, 1e-13), (F32, 2e-6)])
+def test_periodic_conservation(dtype, tol):
+    V = inputs.blast_3d(shape=(40, 36, 33), radius_cells=6.0)
+    U = gpu_state(V, 1.4, dtype)
+    S = hydro.Solver((40, 36, 33), 1.4, dtype=dtype)
+    T0 = np.array(S.totals(U))
+    S.step(U, 60)
+    T1 = np.array(S.totals(U))
+    assert abs(T1[0] - T0[0]) <= tol * T0[0]
+    assert abs(T1[4] - T0[4]) <= tol * T0[4]
+    assert np.all(np.abs(T1[1:4] - T0[1:4]) <= tol * T0[4])
+
+
+@pytest.mark.parametrize("dtype", [F32, F64])
+def test_uniform_state_is_bitwise_unchanged(dtype):
+    V = inputs.uniform((19, 12, 10), rho=1.3, v=(0.3, -0.2, 0.1), p=0.7)
+    U = gpu_state(V, 1.4, dtype)
+    U0 = U.clone()
+    S = hydro.Solver((19, 12, 10), 1.4, bc=["periodic", "outflow", "periodic"], dtype=dtype)
+    S.step(U, 5)
+    assert torch.equal(U, U0)
+
+
+def test_time_clipping_matches_oracle():
+    V = inputs.sod_1d(64)
+    G, t, steps = gpu_run(V, 1.4, (1,), F64, 0.4, 100000, t_end=0.05)
+    O, to, so, _ = oracle_run(V, 1.4, (1,), 0.4, 100000, t_end=0.05)
+    assert t == to == 0.05 and steps == so
+    # more steps requested than needed: the rest are no-ops
+    G2, t2, steps2 = gpu_run(V, 1.4, (1,), F64, 0.4, steps + 7, t_end=0.05)
+    assert steps2 == steps and np.array_equal(G2, G)
+    # t already at t_end: nothing happens
+    U = gpu_state(V, 1.4, F64)
+    S = hydro.Solver((64,), 1.4, bc="outflow", dtype=F64)
+    t3, s3 = S.step(U, 5, t_end=0.05, t=0.05)
+    assert s3 == 0 and t3 == 0.05
+
+
+def test_nonfinite_and_nonpositive_are_reported():
+    V = inputs.uniform((32,), rho=1.0, v=(0.0,), p=1.0)
+    for bad in ("nan", "negrho"):
+        U = gpu_state(V, 1.4, F64)
+        if bad == "nan":
+            U[0, 5] = float("nan")
+        else:
+            U[0, 5] = -1.0
+        S = hydro.Solver((32,), 1.4, dtype=F64)
+        with pytest.raises(hydro.HydroError) as ei:
+            S.step(U, 3)
+        assert ei.value.status == hydro.HYDRO_ENONFINITE
+        assert S.status() == hydro.HYDRO_ENONFINITE
+    # a blow-up during the run: an absurd CFL number makes the scheme unstable
+    V = inputs.smooth((64,), seed=1)
+    U = gpu_state(V, 1.4, F64)
+    S = hydro.Solver((64,), 1.4, dtype=F64, cfl=50.0)
+    with pytest.raises(hydro.HydroError):
+        S.step(U, 200)
+
+
+def test_graph_and_direct_launches_agree_bitwise():
+    V = inputs.kh_2d(96, seed=3, ny=80)
+    A, ta, sa = gpu_run(V, 5.0 / 3.0, (0, 0), F32, 0.4, 70)
+    B, tb, sb = gpu_run(V, 5.0 / 3.0, (0, 0), F32, 0.4, 70, profiling=True)
+    assert np.array_equal(A, B) and ta == tb and sa == sb
+
+
+def test_runs_are_deterministic():
+    V = inputs.blast_3d(shape=(48, 40, 36), radius_cells=6.0)
+    A, ta, _ = gpu_run(V, 1.4, (0, 0, 0), F32, 0.4, 30)
+    B, tb, _ = gpu_run(V, 1.4, (0, 0, 0), F32, 0.4, 30)
+    assert np.array_equal(A, B) and ta == tb
+
+
+def test_step_split_across_calls_matches_one_call():
+    V = inputs.smooth((50, 40), seed=8)
+    A, ta, _ = gpu_run(V, 1.4, (0, 0), F64, 0.4, 20)
+    U = gpu_state(V, 1.4, F64)
+    S = hydro.Solver((50, 40), 1.4, dtype=F64)
+    t = 0.0
+    for n in (7, 1, 12):
+        t, _ = S.step(U, n, t=t)
+    assert np.array_equal(U.cpu().numpy(), A) and t == ta
+
+
+def test_step_host_matches_device_step():
+    V = inputs.smooth((64, 40), seed=9)
+    A, ta, _ = gpu_run(V, 1.4, (0, 1), F32, 0.4, 15)
+    U = gpu_state(V, 1.4, F32)
+    host = U.cpu().pin_memory()
+    out = torch.empty_like(host).pin_memory()
+    dev = torch.empty_like(U)
+    S = hydro.Solver((64, 40), 1.4, bc=["periodic", "outflow"], dtype=F32)
+    t, n = S.step_host(dev, host, out, 15)
+    assert n == 15 and t == ta
+    assert np.array_equal(out.double().numpy(), A)
+
+
+def test_kernel_times_are_recorded():
+    V = inputs.smooth((64, 64, 32), seed=1)
+    U = gpu_state(V, 1.4, F32)
+    S = hydro.Solver((64, 64, 32), 1.4, dtype=F32)
+    S.set_profiling(True)
+    S.step(U, 4)
+    kt = S.kernel_times(reset=True)
+    assert kt["cfl"][1] == 1 and kt["stage1"][1] == 4 and kt["stage2"][1] == 4
+    assert all(v[0] > 0 for v in kt.values())
+    assert S.kernel_times()["stage1"] == (0.0, 0)
+
+
+def test_single_cell_axes_and_tiny_grids():
+    for shape, bc in (((1,), (0,)), ((2, 1), (0, 1)), ((3, 2, 1), (1, 0, 0)), ((5, 1, 4), (0, 0, 1))):
+        V = inputs.smooth(shape, seed=4)
+        G, tg, sg = gpu_run(V, 1.4, bc, F64, 0.3, 6)
+        O, to, so, _ = oracle_run(V, 1.4, bc, 0.3, 6)
+        assert sg == so and np.allclose(G, O, rtol=1e-12, atol=1e-12)

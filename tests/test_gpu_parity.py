@@ -1,0 +1,121 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+FP64: max relative error <= 1e-10 after the run (density and energy element-wise, momenta
+norm-wise).  FP32 (whole stencil in FP32 from the same FP64 initial data): L1 density error
+relative to the FP64 oracle <= 1e-4 after 100 steps.  Sizes span several tiles with ragged
+tails; the configs' full sizes are covered where the oracle finishes in seconds.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from _helpers import gpu_run, l1_rel, max_rel_err, oracle_run, shape_of
+from paper_1204_4779_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+F32, F64 = torch.float32, torch.float64
+
+
+def _compare64(V, gamma, bc, cfl, n, t_end=0.0, variant=None, tol=1e-10):
+    G, tg, sg = gpu_run(V, gamma, bc, F64, cfl, n, t_end=t_end, variant=variant)
+    O, to, so, _ = oracle_run(V, gamma, bc, cfl, n, t_end=t_end)
+    assert sg == so and tg == to, (sg, so, tg, to)
+    err = max_rel_err(G, O)
+    assert err <= tol, err
+    return err, G, O
+
+
+def test_sod_1024_fp64_full_config():
+    """1D Sod, 1024 cells, gamma 1.4, outflow, CFL 0.4, run to t = 0.2."""
+    V = inputs.sod_1d(1024)
+    err, G, O = _compare64(V, 1.4, (1,), 0.4, 100000, t_end=0.2)
+    assert not np.allclose(G, oracle.prim_to_cons(V, 1.4))
+
+
+@pytest.mark.parametrize("bc", [(0, 0), (1, 0), (0, 1)])
+def test_kh_ragged_fp64(bc):
+    V = inputs.kh_2d(100, seed=1204477901, ny=77)
+    _compare64(V, 5.0 / 3.0, bc, 0.4, 40)
+
+
+def test_kh_1024_fp64_full_config():
+    """2D 1024^2 shear layer, gamma 5/3, periodic, 100 steps, FP64."""
+    V = inputs.kh_2d(1024, seed=1204477901)
+    _compare64(V, 5.0 / 3.0, (0, 0), 0.4, 100)
+
+
+@pytest.mark.parametrize("bc", [(0, 0, 0), (1, 1, 1), (0, 1, 0)])
+def test_blast_ragged_fp64(bc):
+    V = inputs.blast_3d(shape=(37, 29, 23), radius_cells=5.0)
+    _compare64(V, 1.4, bc, 0.4, 12, variant=dict(march=8))
+
+
+def test_smooth_3d_march_chunks_fp64():
+    """z-chunk boundaries (march 5 over 19 planes, a ragged last chunk) change nothing."""
+    V = inputs.smooth((21, 18, 19), seed=4)
+    _compare64(V, 1.4, (0, 0, 1), 0.4, 10, variant=dict(march=5))
+
+
+@pytest.mark.slow
+def test_blast_128_fp64_100_steps():
+    """3D blast at 128^3 (radius 8 cells), periodic, 100 steps, FP64."""
+    V = inputs.blast_3d(128, radius_cells=8.0)
+    _compare64(V, 1.4, (0, 0, 0), 0.4, 100)
+
+
+# ------------------------------------------------------------------- FP32 ------------
+
+def _l1_32(V, gamma, bc, n, variant=None):
+    G, tg, sg = gpu_run(V, gamma, bc, F32, 0.4, n, variant=variant)
+    O, to, so, _ = oracle_run(V, gamma, bc, 0.4, n)
+    assert sg == so == n
+    assert abs(tg - to) <= 1e-5 * to
+    return l1_rel(G[0], O[0]), G, O
+
+
+def test_kh_1024_fp32_full_config():
+    V = inputs.kh_2d(1024, seed=1204477901)
+    e, G, O = _l1_32(V, 5.0 / 3.0, (0, 0), 100)
+    print(f"KH 1024^2 FP32 L1(rho) rel = {e:.3e}")
+    assert e <= 1e-4
+
+
+def test_blast_fp32_l1():
+    V = inputs.blast_3d(64, radius_cells=8.0)
+    e, G, O = _l1_32(V, 1.4, (0, 0, 0), 100)
+    print(f"blast 64^3 FP32 L1(rho) rel = {e:.3e}")
+    assert e <= 1e-4
+
+
+def test_sod_fp32_l1():
+    V = inputs.sod_1d(1024)
+    G, tg, sg = gpu_run(V, 1.4, (1,), F32, 0.4, 100000, t_end=0.2)
+    O, to, so, _ = oracle_run(V, 1.4, (1,), 0.4, 100000, t_end=0.2)
+    assert tg == to == 0.2
+    assert abs(sg - so) <= 1
+    e = l1_rel(G[0], O[0])
+    print(f"Sod 1024 FP32 L1(rho) rel = {e:.3e}")
+    assert e <= 1e-4
+
+
+@pytest.mark.parametrize("tile", [(32, 8), (32, 4), (64, 4), (16, 16), (32, 16)])
+def test_every_fp32_3d_tile(tile):
+    V = inputs.smooth((45, 38, 21), seed=11)
+    e, _, _ = _l1_32(V, 1.4, (0, 1, 0), 10, variant=dict(tile=tile, march=6))
+    assert e <= 2e-6
+
+
+@pytest.mark.parametrize("tile", [(32, 8), (64, 4), (16, 16), (32, 16)])
+def test_every_fp32_2d_tile(tile):
+    V = inputs.smooth((70, 45), seed=12)
+    e, _, _ = _l1_32(V, 1.4, (1, 0), 20, variant=dict(tile=tile))
+    assert e <= 2e-6
+
+
+@pytest.mark.parametrize("tile", [(128, 1), (256, 1)])
+def test_every_fp32_1d_tile(tile):
+    V = inputs.smooth((300,), seed=13)
+    e, _, _ = _l1_32(V, 1.4, (0,), 50, variant=dict(tile=tile))
+    assert e <= 2e-6
