@@ -62,7 +62,7 @@ def _traffic(kernel: str):
 
 
 class ClockSampler:
-    """nvidia-smi clocks/throttle reasons sampled every 200 ms during the timed region."""
+    """nvidia-smi clocks/throttle reasons sampled every 100 ms during the timed region."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -77,7 +77,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200", "-i", str(self.idx)],
+                 "-lms", "100", "-i", str(self.idx)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
@@ -192,12 +192,13 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
 
-    ncell = N ** 3
-    V = inputs.blast_3d_torch(N, RADIUS, device=dev)
+    n = args.size
+    ncell = n ** 3
+    V = inputs.blast_3d_torch(n, RADIUS, device=dev)
     U = hydro.prim_to_cons(V, GAMMA).to(torch.float32).contiguous()
     U_init = U.clone()
     del V
-    S = hydro.Solver((N, N, N), GAMMA, bc="periodic", dtype=torch.float32, cfl=CFL)
+    S = hydro.Solver((n, n, n), GAMMA, bc="periodic", dtype=torch.float32, cfl=CFL)
     S.step(U, args.warmup)
     torch.cuda.synchronize()
 
@@ -269,9 +270,10 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "grid": [N, N, N], "gamma": GAMMA, "cfl": CFL,
+            "config": {"workload": WORKLOAD if n == N else WORKLOAD.replace("512^3", f"{n}^3"),
+                       "grid": [n, n, n], "gamma": GAMMA, "cfl": CFL,
                        "blast_radius_cells": RADIUS, "parallelism": f"replicas x{world}",
-                       "l2": "inputs larger than L2 (2.5 GiB state vs 129 MB L2); no flush",
+                       "l2": f"inputs larger than L2 ({5 * 4 * ncell / 2**30:.2f} GiB state vs 129 MB L2); no flush",
                        "variant": {"tile": [32, 8], "march": 64, "split": "per-stage"}},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": traffic, "kernel": dom,
@@ -291,10 +293,11 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--size", type=int, default=N, help="cube side (the benchmark config is 512)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -17,6 +17,7 @@ template <class T> struct AuxT {
     T *out[5];
     long long ncell;
     double dr[3];
+    T inv_dr[3];
     Gas<T> gas;
     Ctrl *ctrl;
 };
@@ -28,7 +29,10 @@ template <class T> AuxT<T> make_aux(const AuxArgs &A) {
         a.out[k] = static_cast<T *>(A.out[k]);
     }
     a.ncell = A.ncell;
-    for (int d = 0; d < 3; ++d) a.dr[d] = A.dr[d];
+    for (int d = 0; d < 3; ++d) {
+        a.dr[d] = A.dr[d];
+        a.inv_dr[d] = T(1.0 / A.dr[d]);
+    }
     a.gas = make_gas<T>(A.gamma);
     a.ctrl = static_cast<Ctrl *>(A.ctrl);
     return a;
@@ -56,7 +60,7 @@ __global__ void __launch_bounds__(kAuxThreads) cfl_kernel(const AuxT<T> A) {
         } else {
             const T cs = Arith<float>::sqrt_(A.gas.g * v[NV - 1] * Arith<float>::rcp(v[0]));
 #pragma unroll
-            for (int a = 0; a < D; ++a) s = fmaf(fabsf(v[1 + a]) + cs, T(1.0 / A.dr[a]), s);
+            for (int a = 0; a < D; ++a) s = fmaf(fabsf(v[1 + a]) + cs, A.inv_dr[a], s);
         }
         smax = (s > smax || s != s) ? s : smax;
         bad |= !(v[0] > T(0)) || !(v[NV - 1] > T(0));

@@ -193,6 +193,7 @@ int begin_steps(hydro_ctx *c, const hydro_state_t *s, double t0, double t_end) {
     init.t = t0;
     init.t_end = t_end;
     init.cfl = c->cfl;
+    for (int a = 0; a < 3; ++a) init.dr[a] = c->dr[a];
     CK(cudaMemcpyAsync(c->ctrl, &init, sizeof init, cudaMemcpyHostToDevice, c->stream));
     if (c->profiling) {
         while (c->events.size() < 2) {

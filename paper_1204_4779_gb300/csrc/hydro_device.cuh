@@ -35,6 +35,8 @@ struct Ctrl {
     int clipped;            // the next step is clipped onto t_end
     int pad;
     double totals[5];       // output of the totals reduction
+    double dr[3];           // cell sizes (set by the host with t, t_end, cfl)
+    double coef[2][3];      // (dt/2)/dr_a and dt/dr_a of the next step, for RK stages 1 and 2
 };
 
 enum : unsigned int { STATUS_NONFINITE = 1u };
@@ -104,9 +106,19 @@ __device__ __forceinline__ void prim_of_cons(const T (&u)[D + 2], T (&v)[D + 2],
     }
 }
 
-// MinBee slope of Eq. eqInterpolateSingle from the two one-sided differences.
-template <class T> __device__ __forceinline__ T minbee(T d01, T d12) {
-    return (d01 * d12 < T(0)) ? T(0) : (fabs(d01) < fabs(d12) ? d01 : d12);
+// MinBee slope of Eq. eqInterpolateSingle from the two one-sided differences:
+// 0 if d01 d12 < 0, else the one of smaller magnitude (d12 on a tie).
+__device__ __forceinline__ double minbee(double d01, double d12) {
+    return (d01 * d12 < 0.0) ? 0.0 : (fabs(d01) < fabs(d12) ? d01 : d12);
+}
+// FP32 form in three ALU operations: min.xorsign.abs gives min(|a|, |b|) carrying a negative
+// sign exactly when the signs of a and b differ; clamping at zero yields 0 for opposite signs;
+// the sign of a restores the slope's sign.  Same values as the form above (up to the sign of
+// a zero slope).
+__device__ __forceinline__ float minbee(float d01, float d12) {
+    float m;
+    asm("min.xorsign.abs.f32 %0, %1, %2;" : "=f"(m) : "f"(d01), "f"(d12));
+    return copysignf(fmaxf(m, 0.0f), d01);
 }
 
 // HLLC flux through a face whose normal is axis a (Toro, Spruce & Speares; Davis wave-speed
@@ -182,9 +194,11 @@ __device__ __forceinline__ void hllc(T rl, const T (&vl)[D], T pl, T rr, const T
         chi = r * (S - u) / (S - Ss);
         eterm = U[D + 1] / r + (Ss - u) * (Ss + p / (r * (S - u)));
     } else {
+        // S - S* is non-zero in both star branches; outside them it is replaced by 1 so the
+        // (discarded) star state stays finite and the blend below can be a single FMA.
         const T ir = left ? irl : irr;
         const T m = r * (S - u);
-        chi = m * Arith<float>::rcp(S - Ss);
+        chi = m * Arith<float>::rcp(star ? S - Ss : T(1));
         eterm = fmaf(Ss - u, fmaf(p, Arith<float>::rcp(m), Ss), U[D + 1] * ir);
     }
     T Us[D + 2];
@@ -193,14 +207,13 @@ __device__ __forceinline__ void hllc(T rl, const T (&vl)[D], T pl, T rr, const T
 #pragma unroll
     for (int b = 1; b < D; ++b) Us[1 + b] = chi * v[b];
     Us[D + 1] = chi * eterm;
+    if constexpr (A::exact) {
 #pragma unroll
-    for (int k = 0; k < D + 2; ++k) {
-        T fs;
-        if constexpr (A::exact)
-            fs = FK[k] + S * (Us[k] - U[k]);
-        else
-            fs = fmaf(S, Us[k] - U[k], FK[k]);
-        F[k] = star ? fs : FK[k];
+        for (int k = 0; k < D + 2; ++k) F[k] = star ? FK[k] + S * (Us[k] - U[k]) : FK[k];
+    } else {
+        const T Se = star ? S : T(0);  // F_K + 0 (U* - U_K) = F_K outside the star branches
+#pragma unroll
+        for (int k = 0; k < D + 2; ++k) F[k] = fmaf(Se, Us[k] - U[k], FK[k]);
     }
 }
 
@@ -262,6 +275,11 @@ template <class T> __device__ void finalize_dt(Ctrl *c, bool advance) {
     if (atomicOr(&c->status, 0u) != 0u) dt = 0.0;
     vc->dt = dt;
     vc->clipped = clipped;
+    // AddFlux coefficients of both stages, in the order of Eq. eqAddFlux: (c dt) / dr_a
+    for (int a = 0; a < 3; ++a) {
+        vc->coef[0][a] = (0.5 * dt) / vc->dr[a];
+        vc->coef[1][a] = dt / vc->dr[a];
+    }
     __threadfence();
 }
 

@@ -19,8 +19,9 @@
 //   * the z-face above each column is evaluated by its own thread from a register pipeline
 //     of the column's V(z), V(z+1), V(z+2), carrying the z-slope and the flux of the face
 //     below from the previous plane, so z-faces are also evaluated once;
-//   * the next plane's loads (own column two planes ahead, halo, U_base) are issued before
-//     the current plane's flux work, hiding their latency.
+//   * the next plane's loads (own column three planes ahead, the halo of the plane after
+//     next) are issued before the current plane's flux work, hiding their latency; the
+//     shared planes are double-buffered, so a plane costs one barrier.
 // HBM traffic per stage: read U_in and U_base, write U_out once; halo re-reads hit L2.
 #pragma once
 
@@ -37,7 +38,8 @@ template <class T> struct StageArgs {
     int n[3];
     int periodic[3];
     int march;          // z-planes per CTA (dim 3)
-    double dr[3];
+    double dr[3];       // cell sizes (the FP64 CFL signal divides by them)
+    T inv_dr[3];        // 1 / dr in the element type (the FP32 CFL signal multiplies)
     Gas<T> gas;
     Ctrl *ctrl;
 };
@@ -53,8 +55,9 @@ template <class T, int D, int BX, int BY> struct StageShape {
     static constexpr int NF = NFX + NFY;
     static constexpr int NH = (D >= 2) ? 4 * BY + 4 * BX : 4;
     static constexpr int HPT = (NH + NT - 1) / NT;  // halo cells per thread
-    static constexpr int FPT = (NF + NT - 1) / NT;  // in-plane faces per thread
-    static constexpr size_t smem_bytes = sizeof(T) * (size_t)(NV * PL + NV * NF + 2 * (NT / 32));
+    static constexpr int FPT = (D >= 2) ? 3 : 2;  // in-plane face rounds per thread
+    static_assert((D >= 2 ? BX + BY : 1) <= NT, "the tile's extra faces must fit in one round");
+    static constexpr size_t smem_bytes = sizeof(T) * (size_t)(2 * NV * PL + 2 * NV * NF + 2 * (NT / 32));
 };
 
 // Flux of one in-plane face from the staged primitive plane.  `o`: shared index of the
@@ -118,18 +121,22 @@ __global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY>::value))
     using S = StageShape<T, D, BX, BY>;
     constexpr int NV = S::NV, NT = S::NT, HX = S::HX, PL = S::PL;
     constexpr int NFX = S::NFX, NF = S::NF, NH = S::NH, HPT = S::HPT, FPT = S::FPT;
+    // shared memory: two primitive planes and two flux planes, alternating between z-planes
+    // so that one barrier per plane suffices
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *sV = reinterpret_cast<T *>(smem_raw);
-    T *sF = sV + NV * PL;
-    T *sRed = sF + NV * NF;
+    T *const sV0 = reinterpret_cast<T *>(smem_raw);
+    T *const sV1 = sV0 + NV * PL;
+    T *const sF0 = sV1 + NV * PL;
+    T *const sF1 = sF0 + NV * NF;
+    T *const sRed = sF1 + NV * NF;
 
     Ctrl *ctrl = A.ctrl;
     const double dt = __ldcg(&ctrl->dt);
     if (!(dt > 0.0)) return;  // uniform over the grid: no step to take
-    const double dts = (STAGE == 1) ? 0.5 * dt : dt;
-    const T cx = T(dts / A.dr[0]);
-    const T cy = (D >= 2) ? T(dts / A.dr[1]) : T(0);
-    const T cz = (D == 3) ? T(dts / A.dr[2]) : T(0);
+    // (c dt)/dr_a, computed once per step in FP64 by the dt finaliser
+    const T cx = T(__ldcg(&ctrl->coef[STAGE - 1][0]));
+    const T cy = (D >= 2) ? T(__ldcg(&ctrl->coef[STAGE - 1][1])) : T(0);
+    const T cz = (D == 3) ? T(__ldcg(&ctrl->coef[STAGE - 1][2])) : T(0);
     const Gas<T> G = A.gas;
 
     const int tid = threadIdx.x;
@@ -142,12 +149,13 @@ __global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY>::value))
     const int own_off = remap(y, ny, A.periodic[1]) * nx + remap(x, nx, A.periodic[0]);
     const int own_s = (D >= 2) ? (ty + 2) * HX + (tx + 2) : (tx + 2);
 
-    // halo cells of this thread: plane offset and shared index
+    // halo cells of this thread: plane offset and shared index.  Halo work goes to the
+    // highest threads, the tile's extra row/column of faces (below) to the lowest.
     int h_off[HPT], h_s[HPT];
     bool h_ok[HPT];
 #pragma unroll
     for (int j = 0; j < HPT; ++j) {
-        const int h = tid + j * NT;
+        const int h = (NT - 1 - tid) + j * NT;
         h_ok[j] = h < NH;
         int lx, ly;
         if constexpr (D >= 2) {
@@ -173,22 +181,40 @@ __global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY>::value))
         h_s[j] = ly * HX + lx;
     }
 
-    // in-plane face tasks of this thread: shared base index, stride, normal axis
-    int f_o[FPT], f_s[FPT], f_a[FPT];
+    // in-plane face tasks of this thread: shared base index, stride, normal axis, face id.
+    // Round 0: the x-face on the low side of the own cell; round 1 (dim >= 2): the y-face on
+    // its low side; last round: the tile's high x-column (BY faces) and high y-row (BX faces),
+    // on the lowest threads.  Rounds 0 and 1 give each warp one row of unit-stride faces.
+    int f_o[FPT], f_s[FPT], f_a[FPT], f_id[FPT];
+    bool f_ok[FPT];
 #pragma unroll
     for (int j = 0; j < FPT; ++j) {
-        const int f = tid + j * NT;
-        if (f < NFX) {  // x-face between tile cells (c-1, r) and (c, r)
-            const int r = f / (BX + 1), c = f % (BX + 1);
+        int c, r, a;
+        bool ok = true;
+        if (j == 0) {
+            c = tx, r = ty, a = 0;
+        } else if (D >= 2 && j == 1) {
+            c = tx, r = ty, a = 1;
+        } else {
+            const int e = tid;
+            if (e < BY) {
+                c = BX, r = e, a = 0;
+            } else {
+                c = e - BY, r = BY, a = 1;
+                ok = (D >= 2) && e < BX + BY;
+            }
+        }
+        if (!ok) c = r = a = 0;
+        f_ok[j] = ok;
+        f_a[j] = a;
+        if (a == 0) {  // x-face between tile cells (c-1, r) and (c, r)
             f_o[j] = ((D >= 2) ? (r + 2) * HX : 0) + c;
             f_s[j] = 1;
-            f_a[j] = 0;
+            f_id[j] = r * (BX + 1) + c;
         } else {  // y-face between (c, r-1) and (c, r)
-            const int g = f - NFX;
-            const int r = g / BX, c = g % BX;
             f_o[j] = r * HX + c + 2;
             f_s[j] = HX;
-            f_a[j] = 1;
+            f_id[j] = NFX + r * BX + c;
         }
     }
 
@@ -201,12 +227,27 @@ __global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY>::value))
 #pragma unroll
         for (int k = 0; k < NV; ++k) u[k] = __ldg(A.uin[k] + i);
     };
+    // V of one plane into shared memory: the own cell from registers, the halo recovered
+    // from its prefetched conserved values
+    auto stage_plane = [&](T *sV, const T (&Vown)[NV], T (&ph)[HPT][NV]) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) sV[k * PL + own_s] = Vown[k];
+#pragma unroll
+        for (int j = 0; j < HPT; ++j) {
+            if (h_ok[j]) {
+                T vh[NV];
+                prim_of_cons<T, D>(ph[j], vh, G);
+#pragma unroll
+                for (int k = 0; k < NV; ++k) sV[k * PL + h_s[j]] = vh[k];
+            }
+        }
+    };
 
-    // register pipeline along z (dim 3): V(z), V(z+1), slope at z, flux of face z - 1/2
+    // register pipeline along z (dim 3): V(z), V(z+1), slope at z, flux of face z - 1/2,
+    // raw U of plane z+2 (own column) and of the next plane's halo
     T Vc[NV], Vn[NV], dzc[NV], Fzm[NV];
     T pown[NV];
     T phalo[HPT][NV];
-    T pbase[NV];
 
     if constexpr (D == 3) {
         T u[NV], Vm2[NV], Vm1[NV], dzm[NV];
@@ -226,70 +267,63 @@ __global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY>::value))
         fz_face(Vm1, dzm, Vc, dzc, G, Fzm);
         load_u(pown, remap(zb + 2, nz, pz), own_off);
     } else {
-        load_u(pown, 0, own_off);  // the cell itself
+        T u[NV];
+        load_u(u, 0, own_off);
+        prim_of_cons<T, D>(u, Vc, G);
     }
 #pragma unroll
     for (int j = 0; j < HPT; ++j)
         if (h_ok[j]) load_u(phalo[j], (D == 3) ? remap(zb, nz, pz) : 0, h_off[j]);
-    {
-        const int i = ((D == 3) ? zb * nxy : 0) + (active ? y * nx + x : 0);
+    stage_plane(sV0, Vc, phalo);
+    if constexpr (D == 3) {
+        if (zb + 1 < ze) {
 #pragma unroll
-        for (int k = 0; k < NV; ++k) pbase[k] = active ? A.ubase[k][i] : T(0);
+            for (int j = 0; j < HPT; ++j)
+                if (h_ok[j]) load_u(phalo[j], remap(zb + 1, nz, pz), h_off[j]);
+        }
     }
+    __syncthreads();
 
     T smax = T(0);
     bool bad = false;
 
     for (int z = zb; z < ze; ++z) {
+        const bool odd = ((z - zb) & 1) != 0;
+        T *const sVc = odd ? sV1 : sV0;
+        T *const sVn = odd ? sV0 : sV1;
+        T *const sF = odd ? sF1 : sF0;
+        // U_base of the plane, consumed after the barrier
+        T base[NV];
+        {
+            const int i = ((D == 3) ? z * nxy : 0) + (active ? y * nx + x : 0);
+#pragma unroll
+            for (int k = 0; k < NV; ++k) base[k] = active ? A.ubase[k][i] : T(0);
+        }
         T Vnn[NV];
         if constexpr (D == 3) {
-            prim_of_cons<T, D>(pown, Vnn, G);
-        } else {
-            prim_of_cons<T, D>(pown, Vc, G);
+            prim_of_cons<T, D>(pown, Vnn, G);  // V(z+2)
+            if (z + 1 < ze) load_u(pown, remap(z + 3, nz, pz), own_off);
         }
-        // stage V of the plane: own cell and halo
-#pragma unroll
-        for (int k = 0; k < NV; ++k) sV[k * PL + own_s] = Vc[k];
-#pragma unroll
-        for (int j = 0; j < HPT; ++j) {
-            if (h_ok[j]) {
-                T vh[NV];
-                prim_of_cons<T, D>(phalo[j], vh, G);
-#pragma unroll
-                for (int k = 0; k < NV; ++k) sV[k * PL + h_s[j]] = vh[k];
-            }
-        }
-        T base[NV];
-#pragma unroll
-        for (int k = 0; k < NV; ++k) base[k] = pbase[k];
-        if constexpr (D == 3) {
-            // prefetch the next plane
-            if (z + 1 < ze) {
-                load_u(pown, remap(z + 3, nz, pz), own_off);
-#pragma unroll
-                for (int j = 0; j < HPT; ++j)
-                    if (h_ok[j]) load_u(phalo[j], remap(z + 1, nz, pz), h_off[j]);
-                if (active) {
-                    const int i = (z + 1) * nxy + y * nx + x;
-#pragma unroll
-                    for (int k = 0; k < NV; ++k) pbase[k] = A.ubase[k][i];
-                }
-            }
-        }
-        __syncthreads();
 
-        // in-plane faces, each once
+        // in-plane faces of plane z, each once
 #pragma unroll
-        for (int j = 0; j < FPT; ++j) {
-            const int f = tid + j * NT;
-            if (j < FPT - 1 || f < NF) inplane_face<T, D, PL, NF>(sV, sF, f_o[j], f_s[j], f_a[j], f, G);
-        }
+        for (int j = 0; j < FPT; ++j)
+            if (f_ok[j]) inplane_face<T, D, PL, NF>(sVc, sF, f_o[j], f_s[j], f_a[j], f_id[j], G);
         // z-face above this column
         T Fzp[NV], dzn[NV];
         if constexpr (D == 3) {
 #pragma unroll
             for (int k = 0; k < NV; ++k) dzn[k] = minbee(Vn[k] - Vc[k], Vnn[k] - Vn[k]);
             fz_face(Vc, dzc, Vn, dzn, G, Fzp);
+            // stage plane z+1 into the other buffer, prefetch the halo of plane z+2
+            if (z + 1 < ze) {
+                stage_plane(sVn, Vn, phalo);
+                if (z + 2 < ze) {
+#pragma unroll
+                    for (int j = 0; j < HPT; ++j)
+                        if (h_ok[j]) load_u(phalo[j], remap(z + 2, nz, pz), h_off[j]);
+                }
+            }
         }
         __syncthreads();
 
@@ -319,11 +353,11 @@ __global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY>::value))
                 if constexpr (Arith<T>::exact) {
                     cs = sqrt(G.g * v[NV - 1] / v[0]);
 #pragma unroll
-                    for (int a = 0; a < D; ++a) s = s + (fabs(v[1 + a]) + cs) / T(A.dr[a]);
+                    for (int a = 0; a < D; ++a) s = s + (fabs(v[1 + a]) + cs) / A.dr[a];
                 } else {
                     cs = Arith<float>::sqrt_(G.g * v[NV - 1] * Arith<float>::rcp(v[0]));
 #pragma unroll
-                    for (int a = 0; a < D; ++a) s = fmaf(fabsf(v[1 + a]) + cs, T(1.0 / A.dr[a]), s);
+                    for (int a = 0; a < D; ++a) s = fmaf(fabsf(v[1 + a]) + cs, A.inv_dr[a], s);
                 }
                 smax = (s > smax || s != s) ? s : smax;
                 bad |= !(v[0] > T(0)) || !(v[NV - 1] > T(0));

@@ -43,6 +43,7 @@ template <class T> static StageArgs<T> make_stage_args(const StageLaunch &L) {
         A.n[a] = L.n[a];
         A.periodic[a] = L.periodic[a];
         A.dr[a] = L.dr[a];
+        A.inv_dr[a] = T(1.0 / L.dr[a]);
     }
     A.march = L.march;
     A.gas = make_gas<T>(L.gamma);
