@@ -175,6 +175,35 @@ int hydro_set_profiling(hydro_ctx_t *ctx, int32_t on);
 int hydro_kernel_times(hydro_ctx_t *ctx, double *ms_out, int64_t *launches_out, int32_t n,
                        int32_t reset);
 
+/* Size of the device scratch array of hydro_step_static: 4 MiB, held by every GPU that loads
+ * this library until the process exits. */
+#define HYDRO_STATIC_SCRATCH_BYTES (4u << 20)
+
+/* hydro_step for callers that cannot allocate device memory (no counterpart in the paper).
+ *
+ * Some callers cannot call cudaMalloc or give the library a workspace: code running inside
+ * another runtime that owns every allocation (a framework with its own caching allocator,
+ * or a stream capture in which allocating is forbidden), and embedded or real-time callers
+ * that must not allocate after start-up.  This call takes the grid, gamma, bc, prec and cfl of
+ * hydro_create plus the arguments of hydro_step, needs no context and no workspace, and
+ * allocates nothing: the RK stage buffer U1 and the step control block live in one
+ * file-scope device array of HYDRO_STATIC_SCRATCH_BYTES.  The caller still owns and passes the
+ * state planes (device memory, layout as for hydro_step).  Default kernel variant, direct
+ * launches (no graph).
+ *   Size limit: the control block (256 bytes) plus dim+2 planes of n[0]*n[1]*n[2] cells, each
+ *   rounded up to 256 bytes, must fit in HYDRO_STATIC_SCRATCH_BYTES (for example a 1D grid of
+ *   10^5 cells in FP64, or 59^3 cells in FP32); larger grids return HYDRO_EINVAL.
+ *   Set-up: the first call on each device (that device current) looks up the array's device
+ *   address with cudaGetSymbolAddress and sets kernel attributes; make that first call
+ *   before any stream capture.
+ *   Sharing: every call uses the same array, which keeps the last call's contents; each call
+ *   rewrites the control block before use.  Calls that overlap on the GPU race on the array:
+ *   order them (one stream, or events).
+ * Errors and synchronisation as for hydro_step (stream = cudaStream_t to issue on). */
+int hydro_step_static(const hydro_grid_t *grid, double gamma, const int32_t bc[3], int32_t prec,
+                      double cfl, const hydro_state_t *state, int32_t n_steps, double t_end,
+                      double *t_inout, int32_t *steps_done, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -29,6 +29,7 @@ UNITS = {
     "stage_f64.cu": ["--fmad=false"],
     "aux_kernels.cu": ["--fmad=false"],
     "hydro_abi.cu": [],
+    "static_step.cu": [],
 }
 HEADERS = ["hydro_device.cuh", "stage_kernel.cuh", "stage_launch.cuh", "hydro_internal.h"]
 

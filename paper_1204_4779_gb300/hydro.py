@@ -28,7 +28,7 @@ EXPORTS = (
     "hydro_version", "hydro_strerror", "hydro_last_cuda_error", "hydro_variant_supported",
     "hydro_workspace_bytes", "hydro_create", "hydro_destroy", "hydro_set_stream", "hydro_step",
     "hydro_step_host", "hydro_cfl_dt", "hydro_totals", "hydro_status", "hydro_prim_to_cons",
-    "hydro_cons_to_prim", "hydro_set_profiling", "hydro_kernel_times",
+    "hydro_cons_to_prim", "hydro_set_profiling", "hydro_kernel_times", "hydro_step_static",
 )
 
 
@@ -94,6 +94,8 @@ def load_library(path: str = LIB_PATH, build_if_missing: bool = True):
             "hydro_cons_to_prim": ([i32, i64, dbl, i32, P(State), P(State), vp], ctypes.c_int),
             "hydro_set_profiling": ([vp, i32], ctypes.c_int),
             "hydro_kernel_times": ([vp, P(dbl), P(i64), i32, i32], ctypes.c_int),
+            "hydro_step_static": ([P(Grid), dbl, P(i32), i32, dbl, P(State), i32, dbl, P(dbl), P(i32),
+                                   vp], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
