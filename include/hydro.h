@@ -175,6 +175,50 @@ int hydro_set_profiling(hydro_ctx_t *ctx, int32_t on);
 int hydro_kernel_times(hydro_ctx_t *ctx, double *ms_out, int64_t *launches_out, int32_t n,
                        int32_t reset);
 
+/* ---- Batched grids: many independent 2D grids of uneven size ----------------------------
+ * The grids are advanced together by one persistent launch per RK stage, steps captured in
+ * CUDA graphs.  Each grid is its own unit square (dr = 1/nx, 1/ny) with its own CFL dt and
+ * time, the same scheme as hydro_step.  All grids share gamma, cfl, the boundary conditions
+ * and the precision.
+ * Packed layout: 4 planes (rho, m_x, m_y, E); plane k is one device array of sum_g nx_g ny_g
+ * elements in which grid g occupies [offset_g, offset_g + nx_g ny_g), x fastest (offsets from
+ * hydro_batch_offsets, grids in the order given).
+ * Workspace: caller-owned, hydro_batch_workspace_bytes() bytes, 256-byte aligned: per-grid
+ * control blocks and geometry, the (grid, tile) work list and the packed U1 stage buffer. */
+typedef struct hydro_batch hydro_batch_t;
+
+/* Bytes of workspace for n_grids grids of nx[g] x ny[g] cells (variant: tile, or NULL). */
+int hydro_batch_workspace_bytes(int32_t n_grids, const int64_t *nx, const int64_t *ny,
+                                int32_t prec, const hydro_variant_t *variant, size_t *bytes_out);
+
+/* Create a batch (grid shapes copied; bc[0], bc[1] for x and y of every grid).  Uploads the
+ * work list into the workspace and synchronises `stream` once. */
+int hydro_batch_create(int32_t n_grids, const int64_t *nx, const int64_t *ny, double gamma,
+                       const int32_t bc[2], int32_t prec, double cfl,
+                       const hydro_variant_t *variant, void *workspace, size_t workspace_bytes,
+                       void *stream, hydro_batch_t **out);
+int hydro_batch_destroy(hydro_batch_t *batch);
+
+/* offsets_out[0..n_grids]: first cell of each grid in the packed planes, then the total. */
+int hydro_batch_offsets(const hydro_batch_t *batch, int64_t *offsets_out);
+int hydro_batch_set_stream(hydro_batch_t *batch, void *stream);
+
+/* Advance every grid by up to n_steps RK steps (each with its own dt).  t_inout: n_grids
+ * start times in, end times out (NULL: all start at 0); steps_done: n_grids counts (NULL ok).
+ * t_end as for hydro_step, per grid.  Synchronises when t_inout or steps_done is given and
+ * then returns HYDRO_ENONFINITE if any grid failed (that grid stops; the others go on). */
+int hydro_batch_step(hydro_batch_t *batch, const hydro_state_t *packed, int32_t n_steps,
+                     double t_end, double *t_inout, int32_t *steps_done);
+
+/* FP64 totals of every grid: out[5 g + (mass, M_x, M_y, 0, E)].  Synchronises. */
+int hydro_batch_totals(hydro_batch_t *batch, const hydro_state_t *packed, double *out);
+
+/* Per-kernel event timing as hydro_set_profiling / hydro_kernel_times (kinds 0 = CFL pass,
+ * 1 = RK stage 1, 2 = RK stage 2). */
+int hydro_batch_set_profiling(hydro_batch_t *batch, int32_t on);
+int hydro_batch_kernel_times(hydro_batch_t *batch, double *ms_out, int64_t *launches_out,
+                             int32_t n, int32_t reset);
+
 /* Size of the device scratch array of hydro_step_static: 4 MiB, held by every GPU that loads
  * this library until the process exits. */
 #define HYDRO_STATIC_SCRATCH_BYTES (4u << 20)

@@ -30,8 +30,12 @@ UNITS = {
     "aux_kernels.cu": ["--fmad=false"],
     "hydro_abi.cu": [],
     "static_step.cu": [],
+    "batch_f32.cu": ["-ftz=true"],
+    "batch_f64.cu": ["--fmad=false"],
+    "batch_abi.cu": [],
 }
-HEADERS = ["hydro_device.cuh", "stage_kernel.cuh", "stage_launch.cuh", "hydro_internal.h"]
+HEADERS = ["hydro_device.cuh", "stage_kernel.cuh", "stage_launch.cuh", "hydro_internal.h",
+           "batch_kernel.cuh"]
 
 
 def nvcc() -> str:

@@ -1,0 +1,273 @@
+// Batched RK-stage kernels: thousands of independent 2D grids of uneven size advanced by one
+// persistent launch per RK stage (the same midpoint-RK MinBee/HLLC step as stage_kernel.cuh,
+// arXiv:1204.4779 section 4.1, on every grid).
+//
+// Layout: the grids' planes are packed: plane k of the batch is one array in which grid g
+// occupies [off_g, off_g + nx_g ny_g), x fastest.  Work is a list of (grid, tile) items,
+// ordered grid by grid; a persistent grid of CTAs walks it with a fixed stride, so CTAs that
+// run at the same time work on neighbouring tiles of the same grid (halo reuse in L2).
+//
+// Each grid has its own control block (dt, time, CFL signal, status): every grid is its own
+// unit square with its own CFL dt.  In stage 2 each tile reduces the CFL signal of its new
+// cells and adds one atomic to its grid's block; the last of the grid's tiles to finish
+// finalises that grid's dt for the next step (no grid-wide barrier, no wait).
+#pragma once
+
+#include "hydro_device.cuh"
+#include "hydro_internal.h"
+#include "stage_kernel.cuh"
+
+namespace hydro {
+
+template <class T> struct BatchArgs {
+    const T *uin[4];
+    const T *ubase[4];
+    T *uout[4];
+    const BatchItem *items;
+    int n_items;
+    const BatchGrid *grids;
+    Ctrl *ctrl;  // one per grid
+    const double *t0;  // per-grid start time (init kernel), may be null
+    double t_end, cfl;
+    int periodic[2];
+    Gas<T> gas;
+};
+
+template <class T, int BX, int BY, int STAGE>
+__global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY>::value))
+    batch_stage_kernel(const BatchArgs<T> A) {
+    using S = StageShape<T, 2, BX, BY>;
+    constexpr int NV = 4, NT = S::NT, HX = S::HX, PL = S::PL;
+    constexpr int NFX = S::NFX, NF = S::NF, HPT = S::HPT, FPT = S::FPT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *const sV = reinterpret_cast<T *>(smem_raw);
+    T *const sF = sV + NV * PL;
+    T *const sRed = sF + NV * NF;
+    const Gas<T> G = A.gas;
+
+    const int tid = threadIdx.x;
+    const int tx = tid % BX, ty = tid / BX;
+    const int own_s = (ty + 2) * HX + (tx + 2);
+    int h_lx[HPT], h_ly[HPT];
+    bool h_ok[HPT];
+#pragma unroll
+    for (int j = 0; j < HPT; ++j) h_ok[j] = halo_task<2, BX, BY>((NT - 1 - tid) + j * NT, h_lx[j], h_ly[j]);
+    int f_o[FPT], f_s[FPT], f_a[FPT], f_id[FPT];
+    bool f_ok[FPT];
+#pragma unroll
+    for (int j = 0; j < FPT; ++j) f_ok[j] = face_task<2, BX, BY>(tid, j, f_o[j], f_s[j], f_a[j], f_id[j]);
+
+    for (int it = blockIdx.x; it < A.n_items; it += gridDim.x) {
+        const BatchItem W = A.items[it];
+        const BatchGrid R = A.grids[W.g];
+        Ctrl *ctrl = A.ctrl + W.g;
+        const double dt = __ldcg(&ctrl->dt);
+        if (!(dt > 0.0)) continue;  // this grid takes no step (same for the whole CTA)
+        const T cx = T(__ldcg(&ctrl->coef[STAGE - 1][0]));
+        const T cy = T(__ldcg(&ctrl->coef[STAGE - 1][1]));
+        const int nx = R.nx, ny = R.ny;
+        const int x = W.x0 + tx, y = W.y0 + ty;
+        const bool active = (x < nx) && (y < ny);
+        const long long off = R.off;
+
+        // stage V of the tile and its halo
+        {
+            T u[NV], v[NV];
+            const long long i = off + remap(y, ny, A.periodic[1]) * nx + remap(x, nx, A.periodic[0]);
+#pragma unroll
+            for (int k = 0; k < NV; ++k) u[k] = __ldg(A.uin[k] + i);
+            prim_of_cons<T, 2>(u, v, G);
+#pragma unroll
+            for (int k = 0; k < NV; ++k) sV[k * PL + own_s] = v[k];
+        }
+#pragma unroll
+        for (int j = 0; j < HPT; ++j) {
+            if (h_ok[j]) {
+                const int xg = remap(W.x0 + h_lx[j] - 2, nx, A.periodic[0]);
+                const int yg = remap(W.y0 + h_ly[j] - 2, ny, A.periodic[1]);
+                const long long i = off + (long long)yg * nx + xg;
+                T u[NV], v[NV];
+#pragma unroll
+                for (int k = 0; k < NV; ++k) u[k] = __ldg(A.uin[k] + i);
+                prim_of_cons<T, 2>(u, v, G);
+#pragma unroll
+                for (int k = 0; k < NV; ++k) sV[k * PL + h_ly[j] * HX + h_lx[j]] = v[k];
+            }
+        }
+        T base[NV];
+        {
+            const long long i = off + (active ? (long long)y * nx + x : 0);
+#pragma unroll
+            for (int k = 0; k < NV; ++k) base[k] = active ? A.ubase[k][i] : T(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < FPT; ++j)
+            if (f_ok[j]) inplane_face<T, 2, PL, NF>(sV, sF, f_o[j], f_s[j], f_a[j], f_id[j], G);
+        __syncthreads();
+
+        T smax = T(0);
+        bool bad = false;
+        if (active) {
+            const int fxl = ty * (BX + 1) + tx;
+            const int fyb = NFX + ty * BX + tx;
+            T un[NV];
+#pragma unroll
+            for (int k = 0; k < NV; ++k) {
+                T sum = cx * (sF[k * NF + fxl] - sF[k * NF + fxl + 1]);
+                sum = sum + cy * (sF[k * NF + fyb] - sF[k * NF + fyb + BX]);
+                un[k] = base[k] + sum;
+            }
+            const long long i = off + (long long)y * nx + x;
+#pragma unroll
+            for (int k = 0; k < NV; ++k) A.uout[k][i] = un[k];
+            if constexpr (STAGE == 2) {
+                T v[NV];
+                prim_of_cons<T, 2>(un, v, G);
+                T cs, s = T(0);
+                if constexpr (Arith<T>::exact) {
+                    cs = sqrt(G.g * v[3] / v[0]);
+                    s = s + (fabs(v[1]) + cs) / R.dr[0];
+                    s = s + (fabs(v[2]) + cs) / R.dr[1];
+                } else {
+                    cs = Arith<float>::sqrt_(G.g * v[3] * Arith<float>::rcp(v[0]));
+                    s = fmaf(fabsf(v[1]) + cs, R.inv_dr[0], s);
+                    s = fmaf(fabsf(v[2]) + cs, R.inv_dr[1], s);
+                }
+                smax = s;
+                bad = !(v[0] > T(0)) || !(v[3] > T(0));
+            }
+        }
+        if constexpr (STAGE == 2)
+            reduce_signal_and_finalize<T, NT>(ctrl, smax, bad, true, sRed, (unsigned)R.ntiles);
+    }
+}
+
+// Per-grid start of a step call: control block of grid g reset, time t0[g] (or 0).
+static __global__ void batch_init_kernel(Ctrl *ctrl, const BatchGrid *grids, int n_grids,
+                                  const double *t0, double t_end, double cfl) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n_grids) return;
+    Ctrl z = {};
+    z.t = t0 ? t0[g] : 0.0;
+    z.t_end = t_end;
+    z.cfl = cfl;
+    z.dr[0] = grids[g].dr[0];
+    z.dr[1] = grids[g].dr[1];
+    z.dr[2] = 1.0;
+    ctrl[g] = z;
+}
+
+// CFL pass over every tile: the first dt of each grid.
+template <class T, int BX, int BY>
+__global__ void __launch_bounds__(BX * BY) batch_cfl_kernel(const BatchArgs<T> A) {
+    constexpr int NT = BX * BY;
+    __shared__ T sRed[2 * NT / 32];
+    const int tx = threadIdx.x % BX, ty = threadIdx.x / BX;
+    for (int it = blockIdx.x; it < A.n_items; it += gridDim.x) {
+        const BatchItem W = A.items[it];
+        const BatchGrid R = A.grids[W.g];
+        const int x = W.x0 + tx, y = W.y0 + ty;
+        T smax = T(0);
+        bool bad = false;
+        if (x < R.nx && y < R.ny) {
+            const long long i = R.off + (long long)y * R.nx + x;
+            T u[4], v[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) u[k] = A.uin[k][i];
+            prim_of_cons<T, 2>(u, v, A.gas);
+            T s = T(0);
+            if constexpr (Arith<T>::exact) {
+                const T cs = sqrt(A.gas.g * v[3] / v[0]);
+                s = s + (fabs(v[1]) + cs) / R.dr[0];
+                s = s + (fabs(v[2]) + cs) / R.dr[1];
+            } else {
+                const T cs = Arith<float>::sqrt_(A.gas.g * v[3] * Arith<float>::rcp(v[0]));
+                s = fmaf(fabsf(v[1]) + cs, R.inv_dr[0], s);
+                s = fmaf(fabsf(v[2]) + cs, R.inv_dr[1], s);
+            }
+            smax = s;
+            bad = !(v[0] > T(0)) || !(v[3] > T(0));
+        }
+        reduce_signal_and_finalize<T, NT>(A.ctrl + W.g, smax, bad, false, sRed, (unsigned)R.ntiles);
+    }
+}
+
+// Conserved totals of every grid in FP64: one CTA per grid, fixed per-thread strides and a
+// fixed shared-memory tree (deterministic), times the cell volume, into ctrl[g].totals.
+template <class T>
+__global__ void __launch_bounds__(256) batch_totals_kernel(const BatchArgs<T> A, int n_grids) {
+    __shared__ double s[256];
+    const int g = blockIdx.x;
+    if (g >= n_grids) return;
+    const BatchGrid R = A.grids[g];
+    const long long n = (long long)R.nx * R.ny;
+    const double vol = R.dr[0] * R.dr[1];
+    for (int k = 0; k < 4; ++k) {
+        double acc = 0.0;
+        for (long long i = threadIdx.x; i < n; i += 256) acc += (double)A.uin[k][R.off + i];
+        s[threadIdx.x] = acc;
+        __syncthreads();
+        for (int w = 128; w > 0; w >>= 1) {
+            if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) A.ctrl[g].totals[k == 3 ? 4 : k] = s[0] * vol;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) A.ctrl[g].totals[3] = 0.0;
+}
+
+template <class T> BatchArgs<T> make_batch_args(const BatchLaunch &L) {
+    BatchArgs<T> A;
+    for (int k = 0; k < 4; ++k) {
+        A.uin[k] = static_cast<const T *>(L.uin[k]);
+        A.ubase[k] = static_cast<const T *>(L.ubase[k]);
+        A.uout[k] = static_cast<T *>(L.uout[k]);
+    }
+    A.items = L.items;
+    A.n_items = L.n_items;
+    A.grids = L.grids;
+    A.ctrl = static_cast<Ctrl *>(L.ctrl);
+    A.t0 = L.t0;
+    A.t_end = L.t_end;
+    A.cfl = L.cfl;
+    A.periodic[0] = L.periodic[0];
+    A.periodic[1] = L.periodic[1];
+    A.gas = make_gas<T>(L.gamma);
+    return A;
+}
+
+// Dispatch for one precision: kind 0 = init, 1 = CFL pass, 2/3 = RK stage 1/2, 4 = totals;
+// prepare_only sets the shared-memory attribute and returns the resident CTAs per SM of the
+// stage kernel in *blocks_per_sm.
+template <class T, int BX, int BY>
+cudaError_t batch_dispatch_tile(const BatchLaunch &L, cudaStream_t st, int kind, bool prepare_only,
+                                int *blocks_per_sm) {
+    using S = StageShape<T, 2, BX, BY>;
+    const size_t smem = sizeof(T) * (size_t)(4 * S::PL + 4 * S::NF + 2 * (S::NT / 32));
+    if (prepare_only) {
+        cudaError_t e = cudaFuncSetAttribute(batch_stage_kernel<T, BX, BY, 1>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(batch_stage_kernel<T, BX, BY, 2>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess && blocks_per_sm)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm,
+                                                              batch_stage_kernel<T, BX, BY, 2>,
+                                                              S::NT, smem);
+        return e;
+    }
+    const BatchArgs<T> A = make_batch_args<T>(L);
+    switch (kind) {
+        case 0: batch_init_kernel<<<(L.n_grids + 255) / 256, 256, 0, st>>>(A.ctrl, A.grids, L.n_grids, A.t0, A.t_end, A.cfl); break;
+        case 1: batch_cfl_kernel<T, BX, BY><<<L.n_blocks, S::NT, 0, st>>>(A); break;
+        case 2: batch_stage_kernel<T, BX, BY, 1><<<L.n_blocks, S::NT, smem, st>>>(A); break;
+        case 3: batch_stage_kernel<T, BX, BY, 2><<<L.n_blocks, S::NT, smem, st>>>(A); break;
+        case 4: batch_totals_kernel<T><<<L.n_grids, 256, 0, st>>>(A, L.n_grids); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace hydro

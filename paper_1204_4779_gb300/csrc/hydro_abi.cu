@@ -21,6 +21,12 @@ int cuda_fail(cudaError_t e, const char *what) {
     return HYDRO_ECUDA;
 }
 
+}  // namespace
+
+int hydro::record_cuda_error(cudaError_t e, const char *what) { return cuda_fail(e, what); }
+
+namespace {
+
 #define CK(call)                                            \
     do {                                                    \
         cudaError_t e_ = (call);                            \

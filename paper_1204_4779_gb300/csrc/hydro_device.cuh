@@ -284,10 +284,12 @@ template <class T> __device__ void finalize_dt(Ctrl *c, bool advance) {
 }
 
 // Block-wide max of a non-negative value (NaN propagates as the largest bit pattern), then
-// one atomic per CTA; the last CTA to finish finalises dt.  Call from all threads.
+// one atomic per CTA; the last of `nblocks` contributions (0: every CTA of the launch)
+// finalises dt.  Call from all threads.
 template <class T, int NT>
 __device__ __forceinline__ void reduce_signal_and_finalize(Ctrl *ctrl, T smax, bool bad,
-                                                           bool advance, T *sred) {
+                                                           bool advance, T *sred,
+                                                           unsigned int nblocks = 0) {
     // warp max on the bit patterns (order-free and exact)
     using U = typename std::conditional<sizeof(T) == 4, unsigned int, unsigned long long>::type;
     U bits;
@@ -317,7 +319,7 @@ __device__ __forceinline__ void reduce_signal_and_finalize(Ctrl *ctrl, T smax, b
         push_signal<T>(ctrl, bm);
         if (anybad) atomicOr(&ctrl->status, STATUS_NONFINITE);
         __threadfence();
-        const unsigned int nblocks = gridDim.x * gridDim.y * gridDim.z;
+        if (nblocks == 0) nblocks = gridDim.x * gridDim.y * gridDim.z;
         const unsigned int prev = atomicAdd(&ctrl->blocks_done, 1u);
         if (prev == nblocks - 1) {
             __threadfence();

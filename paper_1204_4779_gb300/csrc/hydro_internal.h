@@ -7,6 +7,9 @@
 
 namespace hydro {
 
+// Record the text of a failed CUDA call for hydro_last_cuda_error(); returns HYDRO_ECUDA.
+int record_cuda_error(cudaError_t e, const char *what);
+
 // Arguments of one RK-stage launch (precision-free; the launcher casts).
 struct StageLaunch {
     int stage;          // 1 or 2
@@ -56,5 +59,39 @@ cudaError_t launch_totals(const AuxArgs &A, double *partials, int nparts, double
 cudaError_t launch_convert(const AuxArgs &A, int to_cons, cudaStream_t st);
 
 constexpr int kTotalsParts = 1024;
+
+// ---- batched 2D grids (batch_kernel.cuh) ----
+struct BatchItem {  // one tile of one grid
+    int g, x0, y0, pad;
+};
+struct BatchGrid {  // geometry of one grid of the batch
+    long long off;    // first cell of the grid in every packed plane
+    int nx, ny;
+    int ntiles;       // work items of this grid
+    int pad;
+    double dr[2];
+    float inv_dr[2];
+};
+struct BatchLaunch {
+    const void *uin[4];
+    const void *ubase[4];
+    void *uout[4];
+    const BatchItem *items;
+    int n_items;
+    const BatchGrid *grids;
+    int n_grids;
+    void *ctrl;          // n_grids control blocks
+    const double *t0;    // per-grid start times (init), may be null
+    double t_end, cfl, gamma;
+    int periodic[2];
+    int n_blocks;        // persistent grid size
+    int tile_x, tile_y;
+};
+// kind: 0 init, 1 CFL pass, 2 RK stage 1, 3 RK stage 2 (+ per-grid dt), 4 per-grid totals.
+// prepare_only: set kernel attributes and report resident CTAs per SM of the stage kernel.
+cudaError_t batch_f32(const BatchLaunch &L, cudaStream_t st, int kind, bool prepare_only,
+                      int *blocks_per_sm);
+cudaError_t batch_f64(const BatchLaunch &L, cudaStream_t st, int kind, bool prepare_only,
+                      int *blocks_per_sm);
 
 }  // namespace hydro

@@ -111,6 +111,72 @@ __device__ __forceinline__ void fz_face(const T (&Vlo)[5], const T (&dlo)[5], co
     hllc<T, 3, true>(L[0], vl, L[4], R[0], vr, R[4], G, F);
 }
 
+// Shared-memory position (lx, ly) of halo task h of a BX x BY tile (the cross-shaped two-cell
+// halo: two columns left and right of the tile rows, two rows below and above the tile
+// columns); false if h is past the last task.
+template <int D, int BX, int BY>
+__device__ __forceinline__ bool halo_task(int h, int &lx, int &ly) {
+    constexpr int NH = (D >= 2) ? 4 * BY + 4 * BX : 4;
+    if (h >= NH) {
+        lx = ly = 0;
+        return false;
+    }
+    if constexpr (D >= 2) {
+        if (h < 4 * BY) {
+            const int c = h & 3;
+            ly = (h >> 2) + 2;
+            lx = c < 2 ? c : BX + c;
+        } else {
+            const int g = h - 4 * BY;
+            const int r = g / BX;
+            lx = g % BX + 2;
+            ly = r < 2 ? r : BY + r;
+        }
+    } else {
+        const int c = h & 3;
+        lx = c < 2 ? c : BX + c;
+        ly = 0;
+    }
+    return true;
+}
+
+// In-plane face task j of thread tid: shared base index o, stride s, normal axis a, face id.
+// Round 0: the x-face on the low side of the thread's cell; round 1 (dim >= 2): the y-face on
+// its low side; last round: the tile's high x-column (BY faces) and high y-row (BX faces), on
+// the lowest threads.  Rounds 0 and 1 give each warp one row of unit-stride faces.
+template <int D, int BX, int BY>
+__device__ __forceinline__ bool face_task(int tid, int j, int &o, int &s, int &a, int &id) {
+    constexpr int HX = BX + 4;
+    constexpr int NFX = (BX + 1) * BY;
+    const int tx = tid % BX, ty = tid / BX;
+    int c, r;
+    bool ok = true;
+    if (j == 0) {
+        c = tx, r = ty, a = 0;
+    } else if (D >= 2 && j == 1) {
+        c = tx, r = ty, a = 1;
+    } else {
+        const int e = tid;
+        if (e < BY) {
+            c = BX, r = e, a = 0;
+        } else {
+            c = e - BY, r = BY, a = 1;
+            ok = (D >= 2) && e < BX + BY;
+        }
+    }
+    if (!ok) c = r = a = 0;
+    if (a == 0) {  // x-face between tile cells (c-1, r) and (c, r)
+        o = ((D >= 2) ? (r + 2) * HX : 0) + c;
+        s = 1;
+        id = r * (BX + 1) + c;
+    } else {  // y-face between (c, r-1) and (c, r)
+        o = r * HX + c + 2;
+        s = HX;
+        id = NFX + r * BX + c;
+    }
+    return ok;
+}
+
 template <class T, int NT> struct MinBlocks {
     static constexpr int value = (sizeof(T) == 4 && NT <= 256) ? 2 : 1;
 };
@@ -120,7 +186,7 @@ __global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY>::value))
     stage_kernel(const StageArgs<T> A) {
     using S = StageShape<T, D, BX, BY>;
     constexpr int NV = S::NV, NT = S::NT, HX = S::HX, PL = S::PL;
-    constexpr int NFX = S::NFX, NF = S::NF, NH = S::NH, HPT = S::HPT, FPT = S::FPT;
+    constexpr int NFX = S::NFX, NF = S::NF, HPT = S::HPT, FPT = S::FPT;
     // shared memory: two primitive planes and two flux planes, alternating between z-planes
     // so that one barrier per plane suffices
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -150,73 +216,24 @@ __global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY>::value))
     const int own_s = (D >= 2) ? (ty + 2) * HX + (tx + 2) : (tx + 2);
 
     // halo cells of this thread: plane offset and shared index.  Halo work goes to the
-    // highest threads, the tile's extra row/column of faces (below) to the lowest.
+    // highest threads, the tile's extra row/column of faces to the lowest.
     int h_off[HPT], h_s[HPT];
     bool h_ok[HPT];
 #pragma unroll
     for (int j = 0; j < HPT; ++j) {
-        const int h = (NT - 1 - tid) + j * NT;
-        h_ok[j] = h < NH;
         int lx, ly;
-        if constexpr (D >= 2) {
-            if (h < 4 * BY) {
-                const int c = h & 3;
-                ly = (h >> 2) + 2;
-                lx = c < 2 ? c : BX + c;
-            } else {
-                const int g = h - 4 * BY;
-                const int r = g / BX;
-                lx = g % BX + 2;
-                ly = r < 2 ? r : BY + r;
-            }
-        } else {
-            const int c = h & 3;
-            lx = c < 2 ? c : BX + c;
-            ly = 0;
-        }
-        if (!h_ok[j]) lx = ly = 0;
+        h_ok[j] = halo_task<D, BX, BY>((NT - 1 - tid) + j * NT, lx, ly);
         const int xg = remap(x0 + lx - 2, nx, A.periodic[0]);
         const int yg = (D >= 2) ? remap(y0 + ly - 2, ny, A.periodic[1]) : 0;
         h_off[j] = yg * nx + xg;
         h_s[j] = ly * HX + lx;
     }
 
-    // in-plane face tasks of this thread: shared base index, stride, normal axis, face id.
-    // Round 0: the x-face on the low side of the own cell; round 1 (dim >= 2): the y-face on
-    // its low side; last round: the tile's high x-column (BY faces) and high y-row (BX faces),
-    // on the lowest threads.  Rounds 0 and 1 give each warp one row of unit-stride faces.
+    // in-plane face tasks of this thread
     int f_o[FPT], f_s[FPT], f_a[FPT], f_id[FPT];
     bool f_ok[FPT];
 #pragma unroll
-    for (int j = 0; j < FPT; ++j) {
-        int c, r, a;
-        bool ok = true;
-        if (j == 0) {
-            c = tx, r = ty, a = 0;
-        } else if (D >= 2 && j == 1) {
-            c = tx, r = ty, a = 1;
-        } else {
-            const int e = tid;
-            if (e < BY) {
-                c = BX, r = e, a = 0;
-            } else {
-                c = e - BY, r = BY, a = 1;
-                ok = (D >= 2) && e < BX + BY;
-            }
-        }
-        if (!ok) c = r = a = 0;
-        f_ok[j] = ok;
-        f_a[j] = a;
-        if (a == 0) {  // x-face between tile cells (c-1, r) and (c, r)
-            f_o[j] = ((D >= 2) ? (r + 2) * HX : 0) + c;
-            f_s[j] = 1;
-            f_id[j] = r * (BX + 1) + c;
-        } else {  // y-face between (c, r-1) and (c, r)
-            f_o[j] = r * HX + c + 2;
-            f_s[j] = HX;
-            f_id[j] = NFX + r * BX + c;
-        }
-    }
+    for (int j = 0; j < FPT; ++j) f_ok[j] = face_task<D, BX, BY>(tid, j, f_o[j], f_s[j], f_a[j], f_id[j]);
 
     const int zb = (D == 3) ? blockIdx.z * A.march : 0;
     const int ze = (D == 3) ? min(zb + A.march, nz) : 1;

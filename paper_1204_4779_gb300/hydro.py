@@ -29,6 +29,9 @@ EXPORTS = (
     "hydro_workspace_bytes", "hydro_create", "hydro_destroy", "hydro_set_stream", "hydro_step",
     "hydro_step_host", "hydro_cfl_dt", "hydro_totals", "hydro_status", "hydro_prim_to_cons",
     "hydro_cons_to_prim", "hydro_set_profiling", "hydro_kernel_times", "hydro_step_static",
+    "hydro_batch_workspace_bytes", "hydro_batch_create", "hydro_batch_destroy",
+    "hydro_batch_offsets", "hydro_batch_set_stream", "hydro_batch_step", "hydro_batch_totals",
+    "hydro_batch_set_profiling", "hydro_batch_kernel_times",
 )
 
 
@@ -96,6 +99,17 @@ def load_library(path: str = LIB_PATH, build_if_missing: bool = True):
             "hydro_kernel_times": ([vp, P(dbl), P(i64), i32, i32], ctypes.c_int),
             "hydro_step_static": ([P(Grid), dbl, P(i32), i32, dbl, P(State), i32, dbl, P(dbl), P(i32),
                                    vp], ctypes.c_int),
+            "hydro_batch_workspace_bytes": ([i32, P(i64), P(i64), i32, P(Variant), P(ctypes.c_size_t)],
+                                            ctypes.c_int),
+            "hydro_batch_create": ([i32, P(i64), P(i64), dbl, P(i32), i32, dbl, P(Variant), vp,
+                                    ctypes.c_size_t, vp, P(vp)], ctypes.c_int),
+            "hydro_batch_destroy": ([vp], ctypes.c_int),
+            "hydro_batch_offsets": ([vp, P(i64)], ctypes.c_int),
+            "hydro_batch_set_stream": ([vp, vp], ctypes.c_int),
+            "hydro_batch_step": ([vp, P(State), i32, dbl, P(dbl), P(i32)], ctypes.c_int),
+            "hydro_batch_totals": ([vp, P(State), P(dbl)], ctypes.c_int),
+            "hydro_batch_set_profiling": ([vp, i32], ctypes.c_int),
+            "hydro_batch_kernel_times": ([vp, P(dbl), P(i64), i32, i32], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -289,4 +303,100 @@ class Solver:
         n = (ctypes.c_int64 * 3)()
         _check(self.lib.hydro_kernel_times(self.ctx, ms, n, 3, 1 if reset else 0),
                "hydro_kernel_times")
+        return {k: (ms[i], n[i]) for i, k in enumerate(("cfl", "stage1", "stage2"))}
+
+
+class BatchSolver:
+    """Many independent 2D grids of uneven size advanced together (hydro_batch_* of the C ABI).
+
+    shapes: sequence of (nx, ny); every grid is its own unit square with its own CFL dt.
+    The packed state is a tensor of shape (4, total_cells): plane k holds grid g's cells at
+    [offsets[g], offsets[g+1]), x fastest.
+    """
+
+    def __init__(self, shapes, gamma: float, bc="periodic", dtype=torch.float32, cfl: float = 0.4,
+                 tile=None, device=None):
+        self.lib = load_library()
+        self.shapes = [(int(a), int(b)) for a, b in shapes]
+        self.n = len(self.shapes)
+        self.gamma, self.cfl, self.dtype = float(gamma), float(cfl), dtype
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        if isinstance(bc, (str, int)):
+            bc = [bc, bc]
+        bcs = (ctypes.c_int32 * 2)(*[HYDRO_BC_PERIODIC if b in ("periodic", 0) else HYDRO_BC_OUTFLOW
+                                     for b in bc])
+        nx = (ctypes.c_int64 * self.n)(*[s[0] for s in self.shapes])
+        ny = (ctypes.c_int64 * self.n)(*[s[1] for s in self.shapes])
+        var = Variant(int(tile[0]), int(tile[1]), 0, 0) if tile else None
+        nbytes = ctypes.c_size_t()
+        _check(self.lib.hydro_batch_workspace_bytes(self.n, nx, ny, _prec(dtype),
+                                                    ctypes.byref(var) if var else None,
+                                                    ctypes.byref(nbytes)), "hydro_batch_workspace_bytes")
+        self.workspace = torch.empty(int(nbytes.value), dtype=torch.uint8, device=self.device)
+        ctx = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(self.lib.hydro_batch_create(self.n, nx, ny, self.gamma, bcs, _prec(dtype), self.cfl,
+                                               ctypes.byref(var) if var else None,
+                                               self.workspace.data_ptr(), int(nbytes.value),
+                                               _stream_ptr(self.device), ctypes.byref(ctx)),
+                   "hydro_batch_create")
+        self.ctx = ctx
+        offs = (ctypes.c_int64 * (self.n + 1))()
+        _check(self.lib.hydro_batch_offsets(self.ctx, offs), "hydro_batch_offsets")
+        self.offsets = list(offs)
+        self.total = self.offsets[-1]
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.hydro_batch_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def empty_state(self) -> torch.Tensor:
+        return torch.empty((4, self.total), dtype=self.dtype, device=self.device)
+
+    def grid_view(self, packed: torch.Tensor, g: int) -> torch.Tensor:
+        """(4, ny, nx) view of grid g inside a packed tensor."""
+        nx, ny = self.shapes[g]
+        return packed[:, self.offsets[g]:self.offsets[g + 1]].view(4, ny, nx)
+
+    def _state(self, U: torch.Tensor) -> State:
+        if U.dtype != self.dtype or tuple(U.shape) != (4, self.total):
+            raise ValueError("packed state must be (4, total_cells) of the batch dtype")
+        return state_struct(U, 4)
+
+    def step(self, U: torch.Tensor, n_steps: int, t_end: float = 0.0, t=None, sync: bool = True):
+        """Advance every grid in place; returns (t per grid, steps per grid)."""
+        self.lib.hydro_batch_set_stream(self.ctx, _stream_ptr(self.device))
+        s = self._state(U)
+        if not sync:
+            _check(self.lib.hydro_batch_step(self.ctx, ctypes.byref(s), int(n_steps), float(t_end),
+                                             None, None), "hydro_batch_step")
+            return None, None
+        tt = (ctypes.c_double * self.n)(*(t if t is not None else [0.0] * self.n))
+        done = (ctypes.c_int32 * self.n)()
+        _check(self.lib.hydro_batch_step(self.ctx, ctypes.byref(s), int(n_steps), float(t_end), tt,
+                                         done), "hydro_batch_step")
+        return list(tt), list(done)
+
+    def totals(self, U: torch.Tensor):
+        self.lib.hydro_batch_set_stream(self.ctx, _stream_ptr(self.device))
+        s = self._state(U)
+        out = (ctypes.c_double * (5 * self.n))()
+        _check(self.lib.hydro_batch_totals(self.ctx, ctypes.byref(s), out), "hydro_batch_totals")
+        return [list(out[5 * g:5 * g + 5]) for g in range(self.n)]
+
+    def set_profiling(self, on: bool):
+        _check(self.lib.hydro_batch_set_profiling(self.ctx, 1 if on else 0), "hydro_batch_set_profiling")
+
+    def kernel_times(self, reset: bool = False):
+        ms = (ctypes.c_double * 3)()
+        n = (ctypes.c_int64 * 3)()
+        _check(self.lib.hydro_batch_kernel_times(self.ctx, ms, n, 3, 1 if reset else 0),
+               "hydro_batch_kernel_times")
         return {k: (ms[i], n[i]) for i, k in enumerate(("cfl", "stage1", "stage2"))}
