@@ -76,14 +76,21 @@ typedef struct {
 /* Kernel variant (the tuning space).  Zero-initialised = library default.
  *   tile_x, tile_y: in-plane CTA tile (cells); tile_y = 1 for dim 1.  The compiled shapes are
  *                   listed by hydro_variant_supported().
- *   march:          dim 3 only: z-planes one CTA marches through (>= 1).
- *   split:          0 = one kernel per RK stage (the only split built).
- */
+ *   march:          dim 3 only: z-planes one CTA marches through (>= 1), i.e. the cells each
+ *                   thread updates per stage.
+ *   split:          fusion split.  0 = the CFL signal and the next dt are reduced in the
+ *                   epilogue of RK stage 2 (default); 1 = a separate CFL pass after stage 2
+ *                   (one more launch and one more read of the state per step).
+ *   staging:        staging depth, dim 3 only.  0 = default (1); 1 = the next z-plane's loads
+ *                   are issued one plane ahead of their use; 2 = each plane is loaded when it
+ *                   is staged (no look-ahead, fewer registers).
+ * Every variant computes the same step; they differ in speed only. */
 typedef struct {
     int32_t tile_x;
     int32_t tile_y;
     int32_t march;
     int32_t split;
+    int32_t staging;
 } hydro_variant_t;
 
 typedef struct hydro_ctx hydro_ctx_t;
@@ -218,6 +225,32 @@ int hydro_batch_totals(hydro_batch_t *batch, const hydro_state_t *packed, double
 int hydro_batch_set_profiling(hydro_batch_t *batch, int32_t on);
 int hydro_batch_kernel_times(hydro_batch_t *batch, double *ms_out, int64_t *launches_out,
                              int32_t n, int32_t reset);
+
+/* ---- Cost model of the variant tuner: a 3-layer MLP trained on the GPU ---------------------
+ * y = W3 tanh(W2 tanh(W1 x + b1) + b2) + b3, input width d, hidden width H, FP32.  All arrays
+ * are device memory owned by the caller: params (hydro_mlp_sizes' param_count floats, layout
+ * W1 (H x d, row-major), b1, W2 (H x H), b2, W3 (1 x H), b3), Adam moments m and v (same
+ * size), inputs X (n x d, row-major), targets t (n), and a workspace of workspace_bytes for
+ * n samples.  Loss: mean squared error over the n samples.  Calls are ordered on `stream`
+ * and do not synchronise.  Deterministic (fixed reduction order, no atomics). */
+int hydro_mlp_sizes(int32_t d, int32_t hidden, int64_t n, int64_t *param_count,
+                    size_t *workspace_bytes);
+/* y_out[s] = network(X[s]) for s < n. */
+int hydro_mlp_forward(const float *params, int32_t d, int32_t hidden, const float *X, int64_t n,
+                      float *y_out, void *workspace, void *stream);
+/* Gradient of the loss w.r.t. params (back-propagation) into grad_out (param_count floats) and
+ * the loss into loss_out[0]; either may be NULL. */
+int hydro_mlp_gradient(const float *params, int32_t d, int32_t hidden, const float *X,
+                       const float *t, int64_t n, void *workspace, float *grad_out,
+                       float *loss_out, void *stream);
+/* One Adam step (step >= 1 is the 1-based update count for the bias corrections). */
+int hydro_mlp_adam(float *params, float *m, float *v, const float *grad, int64_t count,
+                   int32_t step, float lr, float beta1, float beta2, float eps, void *stream);
+/* `epochs` full-batch Adam steps (numbered step0+1 ...); loss_out[k] (device, may be NULL)
+ * receives the loss before step k. */
+int hydro_mlp_train(float *params, float *m, float *v, int32_t d, int32_t hidden, const float *X,
+                    const float *t, int64_t n, int32_t epochs, int32_t step0, float lr,
+                    void *workspace, float *loss_out, void *stream);
 
 /* Size of the device scratch array of hydro_step_static: 4 MiB, held by every GPU that loads
  * this library until the process exits. */

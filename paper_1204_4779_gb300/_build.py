@@ -33,6 +33,7 @@ UNITS = {
     "batch_f32.cu": ["-ftz=true"],
     "batch_f64.cu": ["--fmad=false"],
     "batch_abi.cu": [],
+    "mlp.cu": [],
 }
 HEADERS = ["hydro_device.cuh", "stage_kernel.cuh", "stage_launch.cuh", "hydro_internal.h",
            "batch_kernel.cuh"]

@@ -40,10 +40,13 @@ template <class T> AuxT<T> make_aux(const AuxArgs &A) {
 
 // Max over cells of sum_a (|v_a| + c_s) / dr_a, c_s = sqrt(gamma p / rho); flags rho <= 0 or
 // p <= 0; the last CTA turns the max into dt (cfl / max, clipped onto t_end).
-template <class T, int D>
+template <class T, int D, bool ADVANCE>
 __global__ void __launch_bounds__(kAuxThreads) cfl_kernel(const AuxT<T> A) {
     __shared__ T sred[2 * kAuxThreads / 32];
     constexpr int NV = D + 2;
+    // after a step that did not run (dt = 0: t reached t_end, or a failed state) there is
+    // nothing to reduce; the same for every CTA
+    if (ADVANCE && !(__ldcg(&A.ctrl->dt) > 0.0)) return;
     T smax = T(0);
     bool bad = false;
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -65,7 +68,7 @@ __global__ void __launch_bounds__(kAuxThreads) cfl_kernel(const AuxT<T> A) {
         smax = (s > smax || s != s) ? s : smax;
         bad |= !(v[0] > T(0)) || !(v[NV - 1] > T(0));
     }
-    reduce_signal_and_finalize<T, kAuxThreads>(A.ctrl, smax, bad, false, sred);
+    reduce_signal_and_finalize<T, kAuxThreads>(A.ctrl, smax, bad, ADVANCE, sred);
 }
 
 // Totals, level 1: CTA b sums the contiguous chunk [b*chunk, (b+1)*chunk) of each plane in
@@ -159,13 +162,13 @@ int grid_for(long long ncell) {
     return (int)(b < 1 ? 1 : b);
 }
 
-template <class T> cudaError_t cfl_t(const AuxArgs &A, cudaStream_t st) {
+template <class T, bool ADV> cudaError_t cfl_t(const AuxArgs &A, cudaStream_t st) {
     const AuxT<T> a = make_aux<T>(A);
     const int g = grid_for(A.ncell);
     switch (A.dim) {
-        case 1: cfl_kernel<T, 1><<<g, kAuxThreads, 0, st>>>(a); break;
-        case 2: cfl_kernel<T, 2><<<g, kAuxThreads, 0, st>>>(a); break;
-        case 3: cfl_kernel<T, 3><<<g, kAuxThreads, 0, st>>>(a); break;
+        case 1: cfl_kernel<T, 1, ADV><<<g, kAuxThreads, 0, st>>>(a); break;
+        case 2: cfl_kernel<T, 2, ADV><<<g, kAuxThreads, 0, st>>>(a); break;
+        case 3: cfl_kernel<T, 3, ADV><<<g, kAuxThreads, 0, st>>>(a); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -207,8 +210,9 @@ template <class T> cudaError_t convert_t(const AuxArgs &A, int to_cons, cudaStre
 
 }  // namespace
 
-cudaError_t launch_cfl(const AuxArgs &A, cudaStream_t st) {
-    return A.prec == 1 ? cfl_t<float>(A, st) : cfl_t<double>(A, st);
+cudaError_t launch_cfl(const AuxArgs &A, cudaStream_t st, bool advance) {
+    if (A.prec == 1) return advance ? cfl_t<float, true>(A, st) : cfl_t<float, false>(A, st);
+    return advance ? cfl_t<double, true>(A, st) : cfl_t<double, false>(A, st);
 }
 
 cudaError_t launch_totals(const AuxArgs &A, double *partials, int nparts, double vol,

@@ -24,7 +24,7 @@ constexpr int kGraphSlots = 8;
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct BatchLayout {
-    size_t ctrl_off, t0_off, grids_off, items_off, u1_off, plane_bytes, total;
+    size_t ctrl_off, t0_off, grids_off, items_off, sig_off, u1_off, plane_bytes, total;
     long long ncell, n_items;
 };
 
@@ -66,7 +66,8 @@ BatchLayout batch_layout(int32_t n_grids, const int64_t *nx, const int64_t *ny, 
     L.t0_off = align_up(sizeof(Ctrl) * (size_t)n_grids);
     L.grids_off = L.t0_off + align_up(sizeof(double) * (size_t)n_grids);
     L.items_off = L.grids_off + align_up(sizeof(BatchGrid) * (size_t)n_grids);
-    L.u1_off = L.items_off + align_up(sizeof(BatchItem) * (size_t)L.n_items);
+    L.sig_off = L.items_off + align_up(sizeof(BatchItem) * (size_t)L.n_items);
+    L.u1_off = L.sig_off + align_up(sizeof(double) * (size_t)L.n_items);
     L.plane_bytes = align_up((size_t)L.ncell * esz);
     L.total = L.u1_off + 4 * L.plane_bytes;
     return L;
@@ -93,6 +94,7 @@ struct hydro_batch {
     double *t0 = nullptr;
     BatchGrid *grids = nullptr;
     BatchItem *items = nullptr;
+    void *tile_sig = nullptr;
     void *u1[4] = {};
     double gamma = 1.4, cfl = 0.4;
     int periodic[2] = {1, 1};
@@ -130,6 +132,7 @@ BatchLaunch launch_args(const hydro_batch *b, const hydro_state_t *s, int kind, 
     L.grids = b->grids;
     L.n_grids = b->n_grids;
     L.ctrl = b->ctrl;
+    L.tile_sig = b->tile_sig;
     L.t0 = t0;
     L.t_end = t_end;
     L.cfl = b->cfl;
@@ -192,11 +195,13 @@ int get_graph(hydro_batch *b, const hydro_state_t *s, int chunk, cudaGraphExec_t
         slot->exec = nullptr;
     }
     const BatchLaunch L1 = launch_args(b, s, 2, nullptr, 0.0), L2 = launch_args(b, s, 3, nullptr, 0.0);
+    const BatchLaunch F = launch_args(b, s, 6, nullptr, 0.0);
     BCK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
     cudaError_t le = cudaSuccess;
     for (int i = 0; i < chunk && le == cudaSuccess; ++i) {
         le = launch(b, L1, b->cap, 2);
         if (le == cudaSuccess) le = launch(b, L2, b->cap, 3);
+        if (le == cudaSuccess) le = launch(b, F, b->cap, 6);
     }
     cudaGraph_t graph = nullptr;
     const cudaError_t ee = cudaStreamEndCapture(b->cap, &graph);
@@ -283,6 +288,7 @@ int hydro_batch_create(int32_t n_grids, const int64_t *nx, const int64_t *ny, do
     b->t0 = reinterpret_cast<double *>(b->ws + lay.t0_off);
     b->grids = reinterpret_cast<BatchGrid *>(b->ws + lay.grids_off);
     b->items = reinterpret_cast<BatchItem *>(b->ws + lay.items_off);
+    b->tile_sig = b->ws + lay.sig_off;
     for (int k = 0; k < 4; ++k) b->u1[k] = b->ws + lay.u1_off + lay.plane_bytes * (size_t)k;
 
     // host tables: grid geometry and the (grid, tile) work list, grid by grid, row-major
@@ -303,6 +309,7 @@ int hydro_batch_create(int32_t n_grids, const int64_t *nx, const int64_t *ny, do
         G.inv_dr[1] = (float)(1.0 / G.dr[1]);
         const int tx = (G.nx + bx - 1) / bx, ty = (G.ny + by - 1) / by;
         G.ntiles = tx * ty;
+        G.first_item = (int)hi.size();
         for (int j = 0; j < ty; ++j)
             for (int i = 0; i < tx; ++i) hi.push_back(BatchItem{g, i * bx, j * by, 0});
         b->offsets[(size_t)g] = off;
@@ -372,17 +379,22 @@ int hydro_batch_step(hydro_batch_t *b, const hydro_state_t *packed, int32_t n_st
     const BatchLaunch I = launch_args(b, packed, 0, t_inout ? b->t0 : nullptr, t_end);
     BCK(launch(b, I, b->stream, 0));
     const BatchLaunch C = launch_args(b, packed, 1, nullptr, t_end);
+    const BatchLaunch F0 = launch_args(b, packed, 5, nullptr, t_end);
     if (b->profiling) {
         int rc = timed(b, C, 1, 0);
         if (rc) return rc;
+        BCK(launch(b, F0, b->stream, 5));
         const BatchLaunch L1 = launch_args(b, packed, 2, nullptr, 0.0);
         const BatchLaunch L2 = launch_args(b, packed, 3, nullptr, 0.0);
+        const BatchLaunch F = launch_args(b, packed, 6, nullptr, 0.0);
         for (int i = 0; i < n_steps; ++i) {
             if ((rc = timed(b, L1, 2, 1))) return rc;
             if ((rc = timed(b, L2, 3, 2))) return rc;
+            if ((rc = timed(b, F, 6, 0))) return rc;
         }
     } else {
         BCK(launch(b, C, b->stream, 1));
+        BCK(launch(b, F0, b->stream, 5));
         int left = n_steps;
         while (left > 0) {
             int chunk = kMaxChunk;

@@ -7,10 +7,11 @@
 // ordered grid by grid; a persistent grid of CTAs walks it with a fixed stride, so CTAs that
 // run at the same time work on neighbouring tiles of the same grid (halo reuse in L2).
 //
-// Each grid has its own control block (dt, time, CFL signal, status): every grid is its own
-// unit square with its own CFL dt.  In stage 2 each tile reduces the CFL signal of its new
-// cells and adds one atomic to its grid's block; the last of the grid's tiles to finish
-// finalises that grid's dt for the next step (no grid-wide barrier, no wait).
+// Each grid has its own control block (dt, time, status): every grid is its own unit square
+// with its own CFL dt.  In stage 2 each tile reduces the CFL signal of its new cells and
+// stores the maximum in its own slot (a plain store: no atomic, no fence on the tile's path);
+// a small finaliser kernel, one warp per grid, reduces each grid's slots and sets its dt for
+// the next step.
 #pragma once
 
 #include "hydro_device.cuh"
@@ -27,11 +28,39 @@ template <class T> struct BatchArgs {
     int n_items;
     const BatchGrid *grids;
     Ctrl *ctrl;  // one per grid
+    T *tile_sig;       // CFL-signal maximum of each work item (NaN: a bad cell)
     const double *t0;  // per-grid start time (init kernel), may be null
     double t_end, cfl;
     int periodic[2];
     Gas<T> gas;
 };
+
+// Max over the CTA of a non-negative value or NaN (on the bit patterns: NaN > inf > finite),
+// returned to thread 0.  Call from all threads.
+template <class T, int NT> __device__ __forceinline__ T block_max(T v, T *sred) {
+    using U = typename std::conditional<sizeof(T) == 4, unsigned int, unsigned long long>::type;
+    U bits;
+    if constexpr (sizeof(T) == 4)
+        bits = __float_as_uint(v);
+    else
+        bits = (unsigned long long)__double_as_longlong(v);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const U other = __shfl_xor_sync(0xffffffffu, bits, o);
+        bits = other > bits ? other : bits;
+    }
+    U *sb = reinterpret_cast<U *>(sred);
+    __syncthreads();  // the previous use of sred is over
+    if ((threadIdx.x & 31) == 0) sb[threadIdx.x >> 5] = bits;
+    __syncthreads();
+    U m = 0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < NT / 32; ++w) m = sb[w] > m ? sb[w] : m;
+    if constexpr (sizeof(T) == 4)
+        return __uint_as_float((unsigned int)m);
+    else
+        return __longlong_as_double((long long)m);
+}
 
 template <class T, int BX, int BY, int STAGE>
 __global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY>::value))
@@ -138,8 +167,10 @@ __global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY>::value))
                 bad = !(v[0] > T(0)) || !(v[3] > T(0));
             }
         }
-        if constexpr (STAGE == 2)
-            reduce_signal_and_finalize<T, NT>(ctrl, smax, bad, true, sRed, (unsigned)R.ntiles);
+        if constexpr (STAGE == 2) {
+            const T m = block_max<T, NT>(bad ? T(NAN) : smax, sRed);
+            if (threadIdx.x == 0) A.tile_sig[it] = m;
+        }
     }
 }
 
@@ -189,7 +220,42 @@ __global__ void __launch_bounds__(BX * BY) batch_cfl_kernel(const BatchArgs<T> A
             smax = s;
             bad = !(v[0] > T(0)) || !(v[3] > T(0));
         }
-        reduce_signal_and_finalize<T, NT>(A.ctrl + W.g, smax, bad, false, sRed, (unsigned)R.ntiles);
+        const T m = block_max<T, NT>(bad ? T(NAN) : smax, sRed);
+        if (threadIdx.x == 0) A.tile_sig[it] = m;
+    }
+}
+
+// dt of every grid from its tiles' signal maxima: one warp per grid reduces the grid's slots
+// in a fixed pattern, lane 0 finalises (advance: a step has just completed).
+template <class T, bool ADVANCE>
+__global__ void __launch_bounds__(256) batch_finalize_kernel(const BatchArgs<T> A, int n_grids) {
+    using U = typename std::conditional<sizeof(T) == 4, unsigned int, unsigned long long>::type;
+    const int g = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (g >= n_grids) return;
+    const BatchGrid R = A.grids[g];
+    U m = 0;
+    for (int i = lane; i < R.ntiles; i += 32) {
+        const T v = A.tile_sig[R.first_item + i];
+        U b;
+        if constexpr (sizeof(T) == 4)
+            b = __float_as_uint(v);
+        else
+            b = (unsigned long long)__double_as_longlong(v);
+        m = b > m ? b : m;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const U other = __shfl_xor_sync(0xffffffffu, m, o);
+        m = other > m ? other : m;
+    }
+    if (lane == 0) {
+        Ctrl *c = A.ctrl + g;
+        if constexpr (sizeof(T) == 4)
+            c->sig32 = (unsigned int)m;
+        else
+            c->sig64 = (unsigned long long)m;
+        finalize_dt<T>(c, ADVANCE);
     }
 }
 
@@ -229,6 +295,7 @@ template <class T> BatchArgs<T> make_batch_args(const BatchLaunch &L) {
     A.n_items = L.n_items;
     A.grids = L.grids;
     A.ctrl = static_cast<Ctrl *>(L.ctrl);
+    A.tile_sig = static_cast<T *>(L.tile_sig);
     A.t0 = L.t0;
     A.t_end = L.t_end;
     A.cfl = L.cfl;
@@ -265,6 +332,8 @@ cudaError_t batch_dispatch_tile(const BatchLaunch &L, cudaStream_t st, int kind,
         case 2: batch_stage_kernel<T, BX, BY, 1><<<L.n_blocks, S::NT, smem, st>>>(A); break;
         case 3: batch_stage_kernel<T, BX, BY, 2><<<L.n_blocks, S::NT, smem, st>>>(A); break;
         case 4: batch_totals_kernel<T><<<L.n_grids, 256, 0, st>>>(A, L.n_grids); break;
+        case 5: batch_finalize_kernel<T, false><<<(L.n_grids * 32 + 255) / 256, 256, 0, st>>>(A, L.n_grids); break;
+        case 6: batch_finalize_kernel<T, true><<<(L.n_grids * 32 + 255) / 256, 256, 0, st>>>(A, L.n_grids); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

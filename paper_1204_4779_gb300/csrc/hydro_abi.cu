@@ -74,16 +74,18 @@ Layout layout_for(int dim, long long ncell, int prec) {
     return L;
 }
 
-bool tile_compiled(int prec, int dim, int bx, int by) {
+// 0: not compiled; 1: compiled with the default staging depth; 2: with both depths
+int tile_compiled(int prec, int dim, int bx, int by) {
     for (int i = 0; i < hydro::kNumTiles; ++i) {
         const hydro::TileShape &t = hydro::kTiles[i];
-        if (t.prec == prec && t.dim == dim && t.bx == bx && t.by == by) return true;
+        if (t.prec == prec && t.dim == dim && t.bx == bx && t.by == by) return t.both_pf ? 2 : 1;
     }
-    return false;
+    return 0;
 }
 
 void default_variant(int prec, int dim, hydro_variant_t *v) {
     v->split = 0;
+    v->staging = 1;
     v->march = 0;
     if (dim == 1) {
         v->tile_x = 128;
@@ -104,11 +106,17 @@ bool resolve_variant(int prec, int dim, const hydro_variant_t *in, hydro_variant
         if (in->tile_y) out->tile_y = in->tile_y;
         if (in->march) out->march = in->march;
         out->split = in->split;
+        if (in->staging) out->staging = in->staging;
     }
-    if (out->split != 0) return false;
+    if (out->split != 0 && out->split != 1) return false;
+    if (out->staging != 1 && out->staging != 2) return false;
     if (dim == 3 && out->march < 1) return false;
-    if (dim < 3) out->march = 1;
-    return tile_compiled(prec, dim, out->tile_x, out->tile_y);
+    if (dim < 3) {
+        out->march = 1;
+        out->staging = 1;  // one plane: nothing to look ahead to
+    }
+    const int comp = tile_compiled(prec, dim, out->tile_x, out->tile_y);
+    return comp == 2 || (comp == 1 && out->staging == 1);
 }
 
 }  // namespace
@@ -164,6 +172,8 @@ hydro::StageLaunch stage_args(const hydro_ctx *c, const hydro_state_t *s, int st
     L.march = c->var.march;
     L.tile_x = c->var.tile_x;
     L.tile_y = c->var.tile_y;
+    L.prefetch = c->var.staging == 2 ? 0 : 1;
+    L.split = c->var.split;
     L.gamma = c->gamma;
     L.ctrl = c->ctrl;
     return L;
@@ -242,11 +252,13 @@ int get_graph(hydro_ctx *c, const hydro_state_t *s, int chunk, cudaGraphExec_t *
         slot->exec = nullptr;
     }
     const hydro::StageLaunch L1 = stage_args(c, s, 1), L2 = stage_args(c, s, 2);
+    const hydro::AuxArgs C = aux_args(c, s);
     CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
     cudaError_t le = cudaSuccess;
     for (int i = 0; i < chunk && le == cudaSuccess; ++i) {
         le = launch_stage(c, L1, c->cap);
         if (le == cudaSuccess) le = launch_stage(c, L2, c->cap);
+        if (le == cudaSuccess && c->var.split) le = hydro::launch_cfl(C, c->cap, /*advance=*/true);
     }
     cudaGraph_t graph = nullptr;
     cudaError_t ee = cudaStreamEndCapture(c->cap, &graph);
@@ -269,7 +281,9 @@ int get_graph(hydro_ctx *c, const hydro_state_t *s, int chunk, cudaGraphExec_t *
 
 int run_steps_profiled(hydro_ctx *c, const hydro_state_t *s, int n) {
     const hydro::StageLaunch L1 = stage_args(c, s, 1), L2 = stage_args(c, s, 2);
-    const size_t need = (size_t)2 * n + 1;
+    const hydro::AuxArgs C = aux_args(c, s);
+    const int per = c->var.split ? 3 : 2;  // launches per step
+    const size_t need = (size_t)per * n + 1;
     while (c->events.size() < need) {
         cudaEvent_t e;
         CK(cudaEventCreate(&e));
@@ -277,20 +291,26 @@ int run_steps_profiled(hydro_ctx *c, const hydro_state_t *s, int n) {
     }
     CK(cudaEventRecord(c->events[0], c->stream));
     for (int i = 0; i < n; ++i) {
+        const int e0 = per * i;
         CK(launch_stage(c, L1, c->stream));
-        CK(cudaEventRecord(c->events[2 * i + 1], c->stream));
+        CK(cudaEventRecord(c->events[e0 + 1], c->stream));
         CK(launch_stage(c, L2, c->stream));
-        CK(cudaEventRecord(c->events[2 * i + 2], c->stream));
+        CK(cudaEventRecord(c->events[e0 + 2], c->stream));
+        if (c->var.split) {
+            CK(hydro::launch_cfl(C, c->stream, /*advance=*/true));
+            CK(cudaEventRecord(c->events[e0 + 3], c->stream));
+        }
     }
-    CK(cudaEventSynchronize(c->events[2 * n]));
+    CK(cudaEventSynchronize(c->events[(size_t)per * n]));
     for (int i = 0; i < n; ++i) {
-        float m1 = 0, m2 = 0;
-        CK(cudaEventElapsedTime(&m1, c->events[2 * i], c->events[2 * i + 1]));
-        CK(cudaEventElapsedTime(&m2, c->events[2 * i + 1], c->events[2 * i + 2]));
-        c->kms[1] += m1;
-        c->kms[2] += m2;
-        c->klaunch[1] += 1;
-        c->klaunch[2] += 1;
+        const int e0 = per * i;
+        for (int k = 0; k < per; ++k) {
+            float m = 0;
+            CK(cudaEventElapsedTime(&m, c->events[e0 + k], c->events[e0 + k + 1]));
+            const int kind = k < 2 ? k + 1 : 0;  // stage 1, stage 2, then the CFL pass
+            c->kms[kind] += m;
+            c->klaunch[kind] += 1;
+        }
     }
     return HYDRO_OK;
 }

@@ -246,10 +246,11 @@ template <> __device__ __forceinline__ void push_signal<double>(Ctrl *c, double 
 }
 
 // Run by one thread of the last CTA of a reduction launch.  `advance`: a step with dt = c->dt
-// has just completed.  Then dt of the next step = cfl / max signal, clipped onto t_end.
+// has just completed (no step ran if that dt is 0, e.g. once t reached t_end).  Then dt of the
+// next step = cfl / max signal, clipped onto t_end.
 template <class T> __device__ void finalize_dt(Ctrl *c, bool advance) {
     volatile Ctrl *vc = c;
-    if (advance) {
+    if (advance && vc->dt > 0.0) {
         const double dt = vc->dt;
         vc->t = vc->clipped ? vc->t_end : vc->t + dt;
         vc->dt_last = dt;

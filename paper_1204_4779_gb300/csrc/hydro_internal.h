@@ -20,6 +20,8 @@ struct StageLaunch {
     int periodic[3];
     int march;
     int tile_x, tile_y;
+    int prefetch;       // dim 3: 1 = next plane's loads one plane ahead, 0 = at staging
+    int split;          // stage 2: 0 = dt reduction fused, 1 = left to a separate CFL pass
     double dr[3];
     double gamma;
     void *ctrl;
@@ -32,9 +34,9 @@ cudaError_t stage_f32_d2(const StageLaunch &L, cudaStream_t st, bool prepare_onl
 cudaError_t stage_f32_d3(const StageLaunch &L, cudaStream_t st, bool prepare_only);
 cudaError_t stage_f64(int dim, const StageLaunch &L, cudaStream_t st, bool prepare_only);
 
-// Compiled tile shapes.
+// Compiled tile shapes (both_pf: both staging depths compiled).
 struct TileShape {
-    int prec, dim, bx, by;
+    int prec, dim, bx, by, both_pf;
 };
 extern const TileShape kTiles[];
 extern const int kNumTiles;
@@ -50,8 +52,10 @@ struct AuxArgs {
     double gamma;
     void *ctrl;
 };
-// CFL pass: max signal of u -> dt of the first step in ctrl (ctrl must be initialised).
-cudaError_t launch_cfl(const AuxArgs &A, cudaStream_t st);
+// CFL pass: max signal of u -> dt of the next step in ctrl.  advance = false: the first dt of
+// a call (ctrl freshly initialised); true: after an RK step whose stage 2 left the reduction
+// to this pass (t advances by the step's dt first).
+cudaError_t launch_cfl(const AuxArgs &A, cudaStream_t st, bool advance = false);
 // Totals: per-CTA partials into `partials` (dim+2 x nparts doubles), then the fixed-order
 // final sum times the cell volume into ctrl->totals.
 cudaError_t launch_totals(const AuxArgs &A, double *partials, int nparts, double vol,
@@ -68,7 +72,7 @@ struct BatchGrid {  // geometry of one grid of the batch
     long long off;    // first cell of the grid in every packed plane
     int nx, ny;
     int ntiles;       // work items of this grid
-    int pad;
+    int first_item;   // index of its first work item
     double dr[2];
     float inv_dr[2];
 };
@@ -81,13 +85,16 @@ struct BatchLaunch {
     const BatchGrid *grids;
     int n_grids;
     void *ctrl;          // n_grids control blocks
+    void *tile_sig;      // n_items CFL-signal maxima, one per work item (element type)
     const double *t0;    // per-grid start times (init), may be null
     double t_end, cfl, gamma;
     int periodic[2];
     int n_blocks;        // persistent grid size
     int tile_x, tile_y;
 };
-// kind: 0 init, 1 CFL pass, 2 RK stage 1, 3 RK stage 2 (+ per-grid dt), 4 per-grid totals.
+// kind: 0 init, 1 CFL pass (tile maxima), 2 RK stage 1, 3 RK stage 2 (+ tile maxima),
+// 4 per-grid totals, 5 per-grid dt from the tile maxima (first dt of a call), 6 the same after
+// a step (time advances first).
 // prepare_only: set kernel attributes and report resident CTAs per SM of the stage kernel.
 cudaError_t batch_f32(const BatchLaunch &L, cudaStream_t st, int kind, bool prepare_only,
                       int *blocks_per_sm);

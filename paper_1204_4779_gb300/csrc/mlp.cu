@@ -1,0 +1,224 @@
+// Cost model of the variant tuner: a 3-layer MLP (tanh, tanh, linear) with its forward pass,
+// back-propagation and Adam update as hand-written FP32 CUDA kernels.
+//
+// The network is small (input ~30 features, width 64, a few thousand samples), so each
+// kernel gives one thread one output element and loops over the reduction index in a fixed
+// order: deterministic results, no atomics.
+//
+// Flat parameter layout: W1 (H x d, row-major), b1 (H), W2 (H x H), b2 (H), W3 (1 x H), b3 (1).
+// Workspace for n samples (floats): h1 (n H), h2 (n H), y (n), dy (n), dz2 (n H), dz1 (n H),
+// grad (P), loss (1).
+#include <math.h>
+#include <string.h>
+
+#include "../../include/hydro.h"
+#include "hydro_internal.h"
+
+namespace {
+
+constexpr int kThreads = 256;
+
+struct Sizes {
+    long long P, h1, h2, y, dy, dz2, dz1, grad, loss, total;  // float offsets / count
+};
+
+Sizes sizes(int d, int H, long long n) {
+    Sizes S;
+    S.P = (long long)H * d + H + (long long)H * H + H + H + 1;
+    long long o = 0;
+    S.h1 = o; o += n * H;
+    S.h2 = o; o += n * H;
+    S.y = o; o += n;
+    S.dy = o; o += n;
+    S.dz2 = o; o += n * H;
+    S.dz1 = o; o += n * H;
+    S.grad = o; o += S.P;
+    S.loss = o; o += 1;
+    S.total = o;
+    return S;
+}
+
+// out[s][j] = act(b[j] + sum_i in[s][i] W[j][i])
+template <bool TANH>
+__global__ void __launch_bounds__(kThreads) dense_forward(const float *in, int din, const float *W,
+                                                          const float *b, int dout, long long n,
+                                                          float *out) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * dout) return;
+    const long long s = idx / dout;
+    const int j = (int)(idx % dout);
+    float acc = b[j];
+    for (int i = 0; i < din; ++i) acc = fmaf(in[s * din + i], W[(long long)j * din + i], acc);
+    out[idx] = TANH ? tanhf(acc) : acc;
+}
+
+// dy[s] = 2 (y[s] - t[s]) / n; loss = (1/n) sum_s (y[s] - t[s])^2 (one CTA, fixed order)
+__global__ void __launch_bounds__(kThreads) mse_kernel(const float *y, const float *t, long long n,
+                                                       float *dy, float *loss) {
+    __shared__ float s[kThreads];
+    float acc = 0.0f;
+    for (long long i = threadIdx.x; i < n; i += kThreads) {
+        const float e = y[i] - t[i];
+        dy[i] = 2.0f * e / (float)n;
+        acc = fmaf(e, e, acc);
+    }
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = kThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *loss = s[0] / (float)n;
+}
+
+// dz[s][i] = (sum_j delta[s][j] W[j][i]) (1 - h[s][i]^2): back through a dense layer and tanh
+__global__ void __launch_bounds__(kThreads) dense_backward(const float *delta, int dout,
+                                                           const float *W, const float *h, int din,
+                                                           long long n, float *dz) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * din) return;
+    const long long s = idx / din;
+    const int i = (int)(idx % din);
+    float acc = 0.0f;
+    for (int j = 0; j < dout; ++j) acc = fmaf(delta[s * dout + j], W[(long long)j * din + i], acc);
+    const float hv = h[idx];
+    dz[idx] = acc * (1.0f - hv * hv);
+}
+
+// gW[j][i] = sum_s delta[s][j] in[s][i]; gb[j] = sum_s delta[s][j]  (thread (j, i), i = din: gb)
+__global__ void __launch_bounds__(kThreads) dense_wgrad(const float *delta, int dout,
+                                                        const float *in, int din, long long n,
+                                                        float *gW, float *gb) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)dout * (din + 1)) return;
+    const int j = (int)(idx / (din + 1));
+    const int i = (int)(idx % (din + 1));
+    float acc = 0.0f;
+    if (i < din) {
+        for (long long s = 0; s < n; ++s) acc = fmaf(delta[s * dout + j], in[s * din + i], acc);
+        gW[(long long)j * din + i] = acc;
+    } else {
+        for (long long s = 0; s < n; ++s) acc += delta[s * dout + j];
+        gb[j] = acc;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) adam_kernel(float *p, float *m, float *v, const float *g,
+                                                        long long count, float lr, float b1,
+                                                        float b2, float eps, float c1, float c2) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+unsigned blocks(long long work) { return (unsigned)((work + kThreads - 1) / kThreads); }
+
+cudaError_t forward_all(const float *p, int d, int H, const float *X, long long n, float *ws,
+                        const Sizes &S, cudaStream_t st) {
+    const float *W1 = p, *b1 = W1 + (long long)H * d, *W2 = b1 + H, *b2 = W2 + (long long)H * H;
+    const float *W3 = b2 + H, *b3 = W3 + H;
+    dense_forward<true><<<blocks(n * H), kThreads, 0, st>>>(X, d, W1, b1, H, n, ws + S.h1);
+    dense_forward<true><<<blocks(n * H), kThreads, 0, st>>>(ws + S.h1, H, W2, b2, H, n, ws + S.h2);
+    dense_forward<false><<<blocks(n), kThreads, 0, st>>>(ws + S.h2, H, W3, b3, 1, n, ws + S.y);
+    return cudaGetLastError();
+}
+
+cudaError_t gradient_all(const float *p, int d, int H, const float *X, const float *t, long long n,
+                         float *ws, const Sizes &S, cudaStream_t st) {
+    cudaError_t e = forward_all(p, d, H, X, n, ws, S, st);
+    if (e != cudaSuccess) return e;
+    const float *W2 = p + (long long)H * d + H, *W3 = W2 + (long long)H * H + H;
+    float *g = ws + S.grad;
+    float *gW1 = g, *gb1 = gW1 + (long long)H * d, *gW2 = gb1 + H, *gb2 = gW2 + (long long)H * H;
+    float *gW3 = gb2 + H, *gb3 = gW3 + H;
+    mse_kernel<<<1, kThreads, 0, st>>>(ws + S.y, t, n, ws + S.dy, ws + S.loss);
+    // output layer (linear): delta = dy
+    dense_wgrad<<<blocks((long long)1 * (H + 1)), kThreads, 0, st>>>(ws + S.dy, 1, ws + S.h2, H, n, gW3, gb3);
+    dense_backward<<<blocks(n * H), kThreads, 0, st>>>(ws + S.dy, 1, W3, ws + S.h2, H, n, ws + S.dz2);
+    dense_wgrad<<<blocks((long long)H * (H + 1)), kThreads, 0, st>>>(ws + S.dz2, H, ws + S.h1, H, n, gW2, gb2);
+    dense_backward<<<blocks(n * H), kThreads, 0, st>>>(ws + S.dz2, H, W2, ws + S.h1, H, n, ws + S.dz1);
+    dense_wgrad<<<blocks((long long)H * (d + 1)), kThreads, 0, st>>>(ws + S.dz1, H, X, d, n, gW1, gb1);
+    return cudaGetLastError();
+}
+
+bool dims_ok(int d, int H, long long n) { return d >= 1 && d <= 4096 && H >= 1 && H <= 4096 && n >= 1; }
+
+}  // namespace
+
+extern "C" {
+
+int hydro_mlp_sizes(int32_t d, int32_t hidden, int64_t n, int64_t *param_count,
+                    size_t *workspace_bytes) {
+    if (!dims_ok(d, hidden, n)) return HYDRO_EINVAL;
+    const Sizes S = sizes(d, hidden, n);
+    if (param_count) *param_count = S.P;
+    if (workspace_bytes) *workspace_bytes = sizeof(float) * (size_t)S.total;
+    return HYDRO_OK;
+}
+
+int hydro_mlp_forward(const float *params, int32_t d, int32_t hidden, const float *X, int64_t n,
+                      float *y_out, void *workspace, void *stream) {
+    if (!params || !X || !y_out || !workspace || !dims_ok(d, hidden, n)) return HYDRO_EINVAL;
+    const Sizes S = sizes(d, hidden, n);
+    float *ws = static_cast<float *>(workspace);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = forward_all(params, d, hidden, X, n, ws, S, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(y_out, ws + S.y, sizeof(float) * (size_t)n, cudaMemcpyDeviceToDevice, st);
+    return e == cudaSuccess ? HYDRO_OK : hydro::record_cuda_error(e, "hydro_mlp_forward");
+}
+
+int hydro_mlp_gradient(const float *params, int32_t d, int32_t hidden, const float *X,
+                       const float *t, int64_t n, void *workspace, float *grad_out,
+                       float *loss_out, void *stream) {
+    if (!params || !X || !t || !workspace || !dims_ok(d, hidden, n)) return HYDRO_EINVAL;
+    const Sizes S = sizes(d, hidden, n);
+    float *ws = static_cast<float *>(workspace);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = gradient_all(params, d, hidden, X, t, n, ws, S, st);
+    if (e == cudaSuccess && grad_out)
+        e = cudaMemcpyAsync(grad_out, ws + S.grad, sizeof(float) * (size_t)S.P,
+                            cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && loss_out)
+        e = cudaMemcpyAsync(loss_out, ws + S.loss, sizeof(float), cudaMemcpyDeviceToDevice, st);
+    return e == cudaSuccess ? HYDRO_OK : hydro::record_cuda_error(e, "hydro_mlp_gradient");
+}
+
+int hydro_mlp_adam(float *params, float *m, float *v, const float *grad, int64_t count,
+                   int32_t step, float lr, float beta1, float beta2, float eps, void *stream) {
+    if (!params || !m || !v || !grad || count < 1 || step < 1) return HYDRO_EINVAL;
+    const float c1 = 1.0f - powf(beta1, (float)step);
+    const float c2 = 1.0f - powf(beta2, (float)step);
+    adam_kernel<<<blocks(count), kThreads, 0, static_cast<cudaStream_t>(stream)>>>(
+        params, m, v, grad, count, lr, beta1, beta2, eps, c1, c2);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? HYDRO_OK : hydro::record_cuda_error(e, "hydro_mlp_adam");
+}
+
+int hydro_mlp_train(float *params, float *m, float *v, int32_t d, int32_t hidden, const float *X,
+                    const float *t, int64_t n, int32_t epochs, int32_t step0, float lr,
+                    void *workspace, float *loss_out, void *stream) {
+    if (!params || !m || !v || !X || !t || !workspace || epochs < 0 || step0 < 0 ||
+        !dims_ok(d, hidden, n))
+        return HYDRO_EINVAL;
+    const Sizes S = sizes(d, hidden, n);
+    float *ws = static_cast<float *>(workspace);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    for (int k = 0; k < epochs; ++k) {
+        cudaError_t e = gradient_all(params, d, hidden, X, t, n, ws, S, st);
+        if (e == cudaSuccess && loss_out)
+            e = cudaMemcpyAsync(loss_out + k, ws + S.loss, sizeof(float), cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return hydro::record_cuda_error(e, "hydro_mlp_train");
+        const int rc = hydro_mlp_adam(params, m, v, ws + S.grad, S.P, step0 + k + 1, lr, 0.9f,
+                                      0.999f, 1e-8f, stream);
+        if (rc) return rc;
+    }
+    return HYDRO_OK;
+}
+
+}  // extern "C"

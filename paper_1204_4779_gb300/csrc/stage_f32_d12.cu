@@ -4,16 +4,16 @@
 namespace hydro {
 
 cudaError_t stage_f32_d1(const StageLaunch &L, cudaStream_t st, bool prepare_only) {
-    HYDRO_STAGE_CASE(float, 1, 128, 1)
-    HYDRO_STAGE_CASE(float, 1, 256, 1)
+    HYDRO_STAGE_CASE(float, 1, 128, 1, false)
+    HYDRO_STAGE_CASE(float, 1, 256, 1, false)
     return cudaErrorInvalidValue;
 }
 
 cudaError_t stage_f32_d2(const StageLaunch &L, cudaStream_t st, bool prepare_only) {
-    HYDRO_STAGE_CASE(float, 2, 32, 8)
-    HYDRO_STAGE_CASE(float, 2, 64, 4)
-    HYDRO_STAGE_CASE(float, 2, 16, 16)
-    HYDRO_STAGE_CASE(float, 2, 32, 16)
+    HYDRO_STAGE_CASE(float, 2, 32, 8, false)
+    HYDRO_STAGE_CASE(float, 2, 64, 4, false)
+    HYDRO_STAGE_CASE(float, 2, 16, 16, false)
+    HYDRO_STAGE_CASE(float, 2, 32, 16, false)
     return cudaErrorInvalidValue;
 }
 

@@ -6,20 +6,21 @@ namespace hydro {
 
 cudaError_t stage_f64(int dim, const StageLaunch &L, cudaStream_t st, bool prepare_only) {
     if (dim == 1) {
-        HYDRO_STAGE_CASE(double, 1, 128, 1)
+        HYDRO_STAGE_CASE(double, 1, 128, 1, false)
     } else if (dim == 2) {
-        HYDRO_STAGE_CASE(double, 2, 32, 8)
+        HYDRO_STAGE_CASE(double, 2, 32, 8, false)
     } else if (dim == 3) {
-        HYDRO_STAGE_CASE(double, 3, 32, 8)
+        HYDRO_STAGE_CASE(double, 3, 32, 8, false)
     }
     return cudaErrorInvalidValue;
 }
 
 const TileShape kTiles[] = {
-    {1, 1, 128, 1}, {1, 1, 256, 1},
-    {1, 2, 32, 8},  {1, 2, 64, 4},  {1, 2, 16, 16}, {1, 2, 32, 16},
-    {1, 3, 32, 8},  {1, 3, 32, 4},  {1, 3, 64, 4},  {1, 3, 16, 16}, {1, 3, 32, 16},
-    {0, 1, 128, 1}, {0, 2, 32, 8},  {0, 3, 32, 8},
+    {1, 1, 128, 1, 0}, {1, 1, 256, 1, 0},
+    {1, 2, 32, 8, 0},  {1, 2, 64, 4, 0},  {1, 2, 16, 16, 0}, {1, 2, 32, 16, 0},
+    {1, 3, 32, 8, 1},  {1, 3, 32, 4, 1},  {1, 3, 64, 4, 1},  {1, 3, 16, 16, 1},
+    {1, 3, 32, 16, 1}, {1, 3, 16, 8, 1},
+    {0, 1, 128, 1, 0}, {0, 2, 32, 8, 0},  {0, 3, 32, 8, 0},
 };
 const int kNumTiles = sizeof(kTiles) / sizeof(kTiles[0]);
 

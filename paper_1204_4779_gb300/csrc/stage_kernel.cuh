@@ -181,7 +181,11 @@ template <class T, int NT> struct MinBlocks {
     static constexpr int value = (sizeof(T) == 4 && NT <= 256) ? 2 : 1;
 };
 
-template <class T, int D, int BX, int BY, int STAGE>
+// STAGE: RK stage (1 or 2).  PF (staging depth, dim 3): 1 = the next z-plane's loads are
+// issued one plane ahead of their use, 0 = each plane is loaded when it is staged.  FUSED
+// (stage 2): 1 = the CFL signal and the next dt are reduced in this kernel's epilogue, 0 = left
+// to a separate CFL pass.
+template <class T, int D, int BX, int BY, int STAGE, int PF = 1, bool FUSED = true>
 __global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY>::value))
     stage_kernel(const StageArgs<T> A) {
     using S = StageShape<T, D, BX, BY>;
@@ -282,7 +286,7 @@ __global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY>::value))
             dzc[k] = minbee(Vc[k] - Vm1[k], Vn[k] - Vc[k]);
         }
         fz_face(Vm1, dzm, Vc, dzc, G, Fzm);
-        load_u(pown, remap(zb + 2, nz, pz), own_off);
+        if constexpr (PF == 1) load_u(pown, remap(zb + 2, nz, pz), own_off);
     } else {
         T u[NV];
         load_u(u, 0, own_off);
@@ -292,7 +296,7 @@ __global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY>::value))
     for (int j = 0; j < HPT; ++j)
         if (h_ok[j]) load_u(phalo[j], (D == 3) ? remap(zb, nz, pz) : 0, h_off[j]);
     stage_plane(sV0, Vc, phalo);
-    if constexpr (D == 3) {
+    if constexpr (D == 3 && PF == 1) {
         if (zb + 1 < ze) {
 #pragma unroll
             for (int j = 0; j < HPT; ++j)
@@ -318,8 +322,11 @@ __global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY>::value))
         }
         T Vnn[NV];
         if constexpr (D == 3) {
+            if constexpr (PF == 0) load_u(pown, remap(z + 2, nz, pz), own_off);
             prim_of_cons<T, D>(pown, Vnn, G);  // V(z+2)
-            if (z + 1 < ze) load_u(pown, remap(z + 3, nz, pz), own_off);
+            if constexpr (PF == 1) {
+                if (z + 1 < ze) load_u(pown, remap(z + 3, nz, pz), own_off);
+            }
         }
 
         // in-plane faces of plane z, each once
@@ -334,8 +341,13 @@ __global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY>::value))
             fz_face(Vc, dzc, Vn, dzn, G, Fzp);
             // stage plane z+1 into the other buffer, prefetch the halo of plane z+2
             if (z + 1 < ze) {
+                if constexpr (PF == 0) {
+#pragma unroll
+                    for (int j = 0; j < HPT; ++j)
+                        if (h_ok[j]) load_u(phalo[j], remap(z + 1, nz, pz), h_off[j]);
+                }
                 stage_plane(sVn, Vn, phalo);
-                if (z + 2 < ze) {
+                if (PF == 1 && z + 2 < ze) {
 #pragma unroll
                     for (int j = 0; j < HPT; ++j)
                         if (h_ok[j]) load_u(phalo[j], remap(z + 2, nz, pz), h_off[j]);
@@ -362,7 +374,7 @@ __global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY>::value))
             const int i = ((D == 3) ? z * nxy : 0) + y * nx + x;
 #pragma unroll
             for (int k = 0; k < NV; ++k) A.uout[k][i] = un[k];
-            if constexpr (STAGE == 2) {
+            if constexpr (STAGE == 2 && FUSED) {
                 // CFL signal of the new state: sum_a (|v_a| + c_s) / dr_a
                 T v[NV];
                 prim_of_cons<T, D>(un, v, G);
@@ -391,7 +403,7 @@ __global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY>::value))
         }
     }
 
-    if constexpr (STAGE == 2) reduce_signal_and_finalize<T, NT>(ctrl, smax, bad, true, sRed);
+    if constexpr (STAGE == 2 && FUSED) reduce_signal_and_finalize<T, NT>(ctrl, smax, bad, true, sRed);
 }
 
 }  // namespace hydro

@@ -7,31 +7,6 @@
 
 namespace hydro {
 
-template <class T, int D, int BX, int BY>
-static cudaError_t launch_stage_inst(int stage, const StageArgs<T> &A, cudaStream_t st) {
-    using S = StageShape<T, D, BX, BY>;
-    const dim3 grid((unsigned)((A.n[0] + BX - 1) / BX),
-                    (unsigned)((D >= 2) ? (A.n[1] + BY - 1) / BY : 1),
-                    (unsigned)((D == 3) ? (A.n[2] + A.march - 1) / A.march : 1));
-    const size_t smem = S::smem_bytes;
-    if (stage == 1)
-        stage_kernel<T, D, BX, BY, 1><<<grid, S::NT, smem, st>>>(A);
-    else
-        stage_kernel<T, D, BX, BY, 2><<<grid, S::NT, smem, st>>>(A);
-    return cudaGetLastError();
-}
-
-template <class T, int D, int BX, int BY>
-static cudaError_t prepare_stage_inst() {
-    using S = StageShape<T, D, BX, BY>;
-    const int smem = (int)S::smem_bytes;
-    cudaError_t e = cudaFuncSetAttribute(stage_kernel<T, D, BX, BY, 1>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(stage_kernel<T, D, BX, BY, 2>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-}
-
 template <class T> static StageArgs<T> make_stage_args(const StageLaunch &L) {
     StageArgs<T> A;
     for (int k = 0; k < 5; ++k) {
@@ -51,11 +26,59 @@ template <class T> static StageArgs<T> make_stage_args(const StageLaunch &L) {
     return A;
 }
 
+// The kernels of one (T, D, tile) for one staging depth PF: stage 1, stage 2 with the fused dt
+// reduction, stage 2 without it.
+template <class T, int D, int BX, int BY, int PF> struct StageKernels {
+    static constexpr auto s1 = stage_kernel<T, D, BX, BY, 1, PF, true>;
+    static constexpr auto s2 = stage_kernel<T, D, BX, BY, 2, PF, true>;
+    static constexpr auto s2_split = stage_kernel<T, D, BX, BY, 2, PF, false>;
+};
+
+template <class T, int D, int BX, int BY, int PF>
+static cudaError_t launch_stage_pf(const StageLaunch &L, const StageArgs<T> &A, cudaStream_t st) {
+    using S = StageShape<T, D, BX, BY>;
+    using K = StageKernels<T, D, BX, BY, PF>;
+    const dim3 grid((unsigned)((A.n[0] + BX - 1) / BX),
+                    (unsigned)((D >= 2) ? (A.n[1] + BY - 1) / BY : 1),
+                    (unsigned)((D == 3) ? (A.n[2] + A.march - 1) / A.march : 1));
+    const size_t smem = S::smem_bytes;
+    if (L.stage == 1)
+        K::s1<<<grid, S::NT, smem, st>>>(A);
+    else if (L.split)
+        K::s2_split<<<grid, S::NT, smem, st>>>(A);
+    else
+        K::s2<<<grid, S::NT, smem, st>>>(A);
+    return cudaGetLastError();
+}
+
+template <class T, int D, int BX, int BY, int PF>
+static cudaError_t prepare_stage_pf() {
+    using K = StageKernels<T, D, BX, BY, PF>;
+    const int smem = (int)StageShape<T, D, BX, BY>::smem_bytes;
+    cudaError_t e = cudaFuncSetAttribute(K::s1, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(K::s2, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(K::s2_split, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    return e;
+}
+
+// Both staging depths exist only in dim 3 (the z-march); dims 1 and 2 have one plane.
+template <class T, int D, int BX, int BY, bool BOTH_PF>
+static cudaError_t dispatch_tile(const StageLaunch &L, cudaStream_t st, bool prepare_only) {
+    if constexpr (BOTH_PF && D == 3) {
+        if (L.prefetch == 0) {
+            if (prepare_only) return prepare_stage_pf<T, D, BX, BY, 0>();
+            return launch_stage_pf<T, D, BX, BY, 0>(L, make_stage_args<T>(L), st);
+        }
+    }
+    if (prepare_only) return prepare_stage_pf<T, D, BX, BY, 1>();
+    return launch_stage_pf<T, D, BX, BY, 1>(L, make_stage_args<T>(L), st);
+}
+
 }  // namespace hydro
 
-// One dispatch case: (BX, BY) compiled for (T, D).
-#define HYDRO_STAGE_CASE(T, D, BX, BY)                                                     \
-    if (L.tile_x == BX && L.tile_y == BY) {                                                \
-        if (prepare_only) return prepare_stage_inst<T, D, BX, BY>();                       \
-        return launch_stage_inst<T, D, BX, BY>(L.stage, make_stage_args<T>(L), st);        \
-    }
+// One dispatch case: (BX, BY) compiled for (T, D), with both staging depths (PF2 = true) or
+// only the default one.
+#define HYDRO_STAGE_CASE(T, D, BX, BY, PF2) \
+    if (L.tile_x == BX && L.tile_y == BY) return dispatch_tile<T, D, BX, BY, PF2>(L, st, prepare_only);

@@ -100,6 +100,8 @@ extern "C" int hydro_step_static(const hydro_grid_t *grid, double gamma, const i
     L.march = dim == 3 ? (n[2] < 64 ? n[2] : 64) : 1;
     L.tile_x = dim == 1 ? 128 : 32;
     L.tile_y = dim == 1 ? 1 : 8;
+    L.prefetch = 1;
+    L.split = 0;
     L.gamma = gamma;
     for (int a = 0; a < 3; ++a) {
         L.n[a] = n[a];

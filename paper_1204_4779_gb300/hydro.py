@@ -32,6 +32,7 @@ EXPORTS = (
     "hydro_batch_workspace_bytes", "hydro_batch_create", "hydro_batch_destroy",
     "hydro_batch_offsets", "hydro_batch_set_stream", "hydro_batch_step", "hydro_batch_totals",
     "hydro_batch_set_profiling", "hydro_batch_kernel_times",
+    "hydro_mlp_sizes", "hydro_mlp_forward", "hydro_mlp_gradient", "hydro_mlp_adam", "hydro_mlp_train",
 )
 
 
@@ -56,7 +57,7 @@ class State(ctypes.Structure):
 
 class Variant(ctypes.Structure):
     _fields_ = [("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32),
-                ("march", ctypes.c_int32), ("split", ctypes.c_int32)]
+                ("march", ctypes.c_int32), ("split", ctypes.c_int32), ("staging", ctypes.c_int32)]
 
 
 _lib = None
@@ -110,6 +111,13 @@ def load_library(path: str = LIB_PATH, build_if_missing: bool = True):
             "hydro_batch_totals": ([vp, P(State), P(dbl)], ctypes.c_int),
             "hydro_batch_set_profiling": ([vp, i32], ctypes.c_int),
             "hydro_batch_kernel_times": ([vp, P(dbl), P(i64), i32, i32], ctypes.c_int),
+            "hydro_mlp_sizes": ([i32, i32, i64, P(i64), P(ctypes.c_size_t)], ctypes.c_int),
+            "hydro_mlp_forward": ([vp, i32, i32, vp, i64, vp, vp, vp], ctypes.c_int),
+            "hydro_mlp_gradient": ([vp, i32, i32, vp, vp, i64, vp, vp, vp, vp], ctypes.c_int),
+            "hydro_mlp_adam": ([vp, vp, vp, vp, i64, i32, ctypes.c_float, ctypes.c_float,
+                                ctypes.c_float, ctypes.c_float, vp], ctypes.c_int),
+            "hydro_mlp_train": ([vp, vp, vp, i32, i32, vp, vp, i64, i32, i32, ctypes.c_float, vp, vp,
+                                 vp], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -148,9 +156,10 @@ def state_struct(t: torch.Tensor, nv: int) -> State:
     return s
 
 
-def variant_supported(dtype, dim: int, tile=(0, 0), march: int = 0) -> bool:
+def variant_supported(dtype, dim: int, tile=(0, 0), march: int = 0, split: int = 0,
+                      staging: int = 0) -> bool:
     lib = load_library()
-    v = Variant(int(tile[0]), int(tile[1]), int(march), 0)
+    v = Variant(int(tile[0]), int(tile[1]), int(march), int(split), int(staging))
     return bool(lib.hydro_variant_supported(_prec(dtype), dim, ctypes.byref(v)))
 
 
@@ -178,7 +187,7 @@ class Solver:
     """One context of libhydro.so on the current CUDA device.
 
     shape: cells per axis (nx, [ny, [nz]]); bc: per-axis "periodic"/"outflow" (or 0/1);
-    variant: dict(tile=(bx, by), march=m) or None for the default.
+    variant: dict(tile=(bx, by), march=m, split=0|1, staging=0|1|2) or None for the default.
     """
 
     def __init__(self, shape, gamma: float, bc="periodic", dtype=torch.float32, cfl: float = 0.4,
@@ -208,7 +217,8 @@ class Solver:
         var = None
         if variant:
             tile = variant.get("tile", (0, 0))
-            var = Variant(int(tile[0]), int(tile[1]), int(variant.get("march", 0)), 0)
+            var = Variant(int(tile[0]), int(tile[1]), int(variant.get("march", 0)),
+                          int(variant.get("split", 0)), int(variant.get("staging", 0)))
         bcs = (ctypes.c_int32 * 3)(*(self.bc + [0] * (3 - self.dim)))
         ctx = ctypes.c_void_p()
         with torch.cuda.device(self.device):
@@ -327,7 +337,7 @@ class BatchSolver:
                                      for b in bc])
         nx = (ctypes.c_int64 * self.n)(*[s[0] for s in self.shapes])
         ny = (ctypes.c_int64 * self.n)(*[s[1] for s in self.shapes])
-        var = Variant(int(tile[0]), int(tile[1]), 0, 0) if tile else None
+        var = Variant(int(tile[0]), int(tile[1]), 0, 0, 0) if tile else None
         nbytes = ctypes.c_size_t()
         _check(self.lib.hydro_batch_workspace_bytes(self.n, nx, ny, _prec(dtype),
                                                     ctypes.byref(var) if var else None,

@@ -114,7 +114,8 @@ def test_graph_and_direct_launches_agree():
     P.step(UP, 70)
     assert torch.equal(UA, UP)
     kt = P.kernel_times()
-    assert kt["stage1"][1] == 70 and kt["stage2"][1] == 70 and kt["cfl"][1] == 1
+    # the "cfl" slot holds the first CFL pass and the per-step dt finaliser
+    assert kt["stage1"][1] == 70 and kt["stage2"][1] == 70 and kt["cfl"][1] == 71
 
 
 @pytest.mark.slow

@@ -100,11 +100,27 @@ def test_sod_fp32_l1():
     assert e <= 1e-4
 
 
-@pytest.mark.parametrize("tile", [(32, 8), (32, 4), (64, 4), (16, 16), (32, 16)])
-def test_every_fp32_3d_tile(tile):
+@pytest.mark.parametrize("tile", [(32, 8), (32, 4), (64, 4), (16, 16), (32, 16), (16, 8)])
+@pytest.mark.parametrize("split,staging", [(0, 1), (1, 1), (0, 2), (1, 2)])
+def test_every_fp32_3d_variant(tile, split, staging):
+    """Every compiled tile with both fusion splits and both staging depths."""
     V = inputs.smooth((45, 38, 21), seed=11)
-    e, _, _ = _l1_32(V, 1.4, (0, 1, 0), 10, variant=dict(tile=tile, march=6))
+    e, _, _ = _l1_32(V, 1.4, (0, 1, 0), 10,
+                     variant=dict(tile=tile, march=6, split=split, staging=staging))
     assert e <= 2e-6
+
+
+@pytest.mark.parametrize("dim_shape", [(1, (300,)), (2, (70, 45)), (3, (37, 29, 23))])
+def test_fp64_split_variant_matches_oracle(dim_shape):
+    """The separate-CFL-pass variant computes the same step to 1e-10 in FP64."""
+    dim, shape = dim_shape
+    V = inputs.smooth(shape, seed=14)
+    _compare64(V, 1.4, (0,) * dim, 0.4, 15, variant=dict(split=1, march=8))
+
+
+def test_split_variant_time_clipping():
+    V = inputs.sod_1d(256)
+    _compare64(V, 1.4, (1,), 0.4, 100000, t_end=0.1, variant=dict(split=1))
 
 
 @pytest.mark.parametrize("tile", [(32, 8), (64, 4), (16, 16), (32, 16)])

@@ -1,0 +1,64 @@
+"""The variant tuner on the GPU: real benchmarks of stage-kernel variants, the cost model
+trained on them by the library's CUDA kernels, and what the trained model gains: ranked by
+the trained network, a held-out grid's variants are found faster than by the same network
+untrained and than by the plain evolutionary search with the same number of benchmarks."""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def test_benchmark_records():
+    from paper_1204_4779_gb300 import tuner as T
+    b = T.Benchmark((40, 36, 33), reps=3, steps=2)
+    r = b(b.space.default_genome())
+    assert r.ok and r.mu > 0 and r.sigma >= 0
+    r2 = b((1, 2, 1, 1))
+    assert r2.ok and r2.genome == (1, 2, 1, 1)
+
+
+@pytest.mark.slow
+def test_trained_cost_model_ranks_and_guides_the_search():
+    from paper_1204_4779_gb300 import tuner as T
+    rng = np.random.default_rng(5)
+    db = T.DB(None)
+    space = T.Space(3)
+    genomes = space.all_genomes()
+    for sh in [(64, 64, 64), (96, 96, 96), (128, 128, 128), (96, 64, 160)]:
+        bench = T.Benchmark(sh, reps=3, steps=2)
+        for i in rng.permutation(len(genomes))[:70]:
+            db.add(bench(genomes[i]))
+    target = (160, 160, 160)
+    bench = T.Benchmark(target, reps=3, steps=2)
+    truth = [bench(g) for g in genomes]          # every variant of the held-out grid
+    best = max(r.mu for r in truth)
+    X, y = T.training_set(db.records)
+    Xt = np.array([T.features(space, g, target) for g in genomes])
+    meas = np.array([-math.log(r.mu) for r in truth])
+    trained = T.CostModel(T.gpu_mlp_factory(64, seed=1), epochs=1500)
+    losses = trained.fit(X, y)
+    assert losses[-1] < 0.5 * losses[0]
+    untrained = T.CostModel(T.gpu_mlp_factory(64, seed=1), epochs=0)
+    untrained.fit(X, y, epochs=0)
+    rho_t = T.spearman(trained.predict(Xt), meas)
+    rho_u = T.spearman(untrained.predict(Xt), meas)
+    print(f"spearman trained {rho_t:.2f} untrained {rho_u:.2f}")
+    assert rho_t > 0.5 and rho_t > rho_u + 0.2
+    # the best measured variant among the model's top 8 is within 5 % of the true best
+    top = np.argsort(trained.predict(Xt))[:8]
+    assert max(truth[i].mu for i in top) >= 0.95 * best
+    # same budget of benchmarks: model-guided search vs plain evolutionary search
+    lookup = {tuple(g): r for g, r in zip(genomes, truth)}
+    ev = lambda g: lookup[tuple(g)]
+    mg, _, _ = T.model_guided(space, target, ev, T.CostModel(T.gpu_mlp_factory(64, seed=2)),
+                              db.records, np.random.default_rng(3), budget_evals=8,
+                              retrain_every=100)
+    plain = [T.evolve(space, ev, np.random.default_rng(s), budget_evals=8)[0].mu
+             for s in range(5)]
+    print(f"model-guided {mg.mu / best:.3f} plain mean {np.mean(plain) / best:.3f}")
+    assert mg.mu >= 0.95 * best
+    assert mg.mu >= np.mean(plain)
