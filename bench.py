@@ -116,6 +116,23 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def aggregate_replicas(ms_local: float, units_local: float, device=None):
+    """Whole-job throughput of independent replicas: the units all ranks processed divided by
+    the slowest rank's time.  Returns (units per second, slowest ms).  Works on any
+    initialised process group (NCCL on the GPU machine, gloo in the CPU tests) or alone."""
+    import torch
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        mx = torch.tensor([ms_local], dtype=torch.float64, device=device)
+        tot = torch.tensor([units_local], dtype=torch.float64, device=device)
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+        ms, units = float(mx.item()), float(tot.item())
+    else:
+        ms, units = float(ms_local), float(units_local)
+    return units / (ms * 1e-3), ms
+
+
 def _gpu_index(local_rank: int) -> int:
     vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
     ids = [v.strip() for v in vis.split(",") if v.strip()]
@@ -219,11 +236,7 @@ def run_ours(args):
     S.set_profiling(False)
     if done != args.steps:
         raise RuntimeError(f"only {done} of {args.steps} steps ran")
-    t = torch.tensor([ms], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * ncell * args.steps / (ms_max * 1e-3)
+    value, ms_max = aggregate_replicas(ms, ncell * args.steps, device=dev)
 
     # --- roofline of the dominant kernel ---------------------------------------------------
     hbm, peak_kind = _peaks()
@@ -251,11 +264,9 @@ def run_ours(args):
         e1.record()
         torch.cuda.synchronize()
         barrier()
-        te = torch.tensor([e0.elapsed_time(e1)], device=dev, dtype=torch.float64)
-        if world > 1:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e2e_value, _ = aggregate_replicas(e0.elapsed_time(e1), ncell * args.e2e_steps, device=dev)
         nbytes = nv * 4 * ncell
-        e2e = {"value": world * ncell * args.e2e_steps / (float(te.item()) * 1e-3),
+        e2e = {"value": e2e_value,
                "unit": "cell-updates/s", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
                "steps": args.e2e_steps,
                "call": "hydro_step_host: pinned host state in, 1 RK step, host state out"}

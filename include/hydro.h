@@ -78,12 +78,17 @@ typedef struct {
  *                   listed by hydro_variant_supported().
  *   march:          dim 3 only: z-planes one CTA marches through (>= 1), i.e. the cells each
  *                   thread updates per stage.
- *   split:          fusion split.  0 = the CFL signal and the next dt are reduced in the
- *                   epilogue of RK stage 2 (default); 1 = a separate CFL pass after stage 2
- *                   (one more launch and one more read of the state per step).
+ *   split:          fusion split.  0 = library default (dim 3: fused; dims 1 and 2:
+ *                   separate); 1 = a separate CFL pass after RK stage 2 (one more launch and
+ *                   one more read of the state per step); 2 = the CFL signal and the next dt
+ *                   reduced in the epilogue of stage 2 (fused).
  *   staging:        staging depth, dim 3 only.  0 = default (1); 1 = the next z-plane's loads
  *                   are issued one plane ahead of their use; 2 = each plane is loaded when it
  *                   is staged (no look-ahead, fewer registers).
+ *   occupancy:      dim 3 FP32 only: resident 256-thread CTAs per SM the register budget of
+ *                   the stage kernels targets.  0 = library default (3 for dim 3 FP32, else
+ *                   2); 2 (about 128 registers a thread); 3 (about 80 registers, 24 warps per
+ *                   SM).
  * Every variant computes the same step; they differ in speed only. */
 typedef struct {
     int32_t tile_x;
@@ -91,6 +96,7 @@ typedef struct {
     int32_t march;
     int32_t split;
     int32_t staging;
+    int32_t occupancy;
 } hydro_variant_t;
 
 typedef struct hydro_ctx hydro_ctx_t;
@@ -131,6 +137,14 @@ int hydro_destroy(hydro_ctx_t *ctx);
 
 /* Change the stream later calls are ordered on. */
 int hydro_set_stream(hydro_ctx_t *ctx, void *stream);
+
+/* Scheme options for later steps (section 4.2 interpolation listing; wave speeds of the cited
+ * HLLC solver).  order: 2 = piecewise-linear MinBee reconstruction (default), 1 = first order
+ * (the face values are the cell values).  riemann: 0 = Davis wave-speed estimates (default),
+ * 1 = pressure-based estimates (Toro's PVRS: p* = max(0, (p_L+p_R)/2 - (u_R-u_L) rho_bar a_bar/2),
+ * q_K = 1 if p* <= p_K else sqrt(1 + (gamma+1)/(2 gamma) (p* / p_K - 1)), S_L = u_L - a_L q_L,
+ * S_R = u_R + a_R q_R).  HYDRO_EINVAL for other values. */
+int hydro_set_scheme(hydro_ctx_t *ctx, int32_t order, int32_t riemann);
 
 /* Advance `state` (in place) by up to n_steps midpoint-RK steps (section 4.1).
  *   t_end     > 0: the last step is clipped so that t lands exactly on t_end and no step

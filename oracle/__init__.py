@@ -92,6 +92,11 @@ def _bind(lib):
     lib.oracle_fluxes.argtypes = [c_int, lp, dp, c_double, ip, dp, ctypes.POINTER(dp)]
     lib.oracle_run.argtypes = [c_int, lp, dp, c_double, ip, c_double, dp, c_int, c_double,
                                dp, ip, c_int]
+    lib.oracle_run_opt.argtypes = [c_int, lp, dp, c_double, ip, c_double, c_int, c_int, dp, c_int,
+                                   c_double, dp, ip, c_int]
+    lib.oracle_run_opt.restype = c_int
+    lib.oracle_hllc_opt.argtypes = [c_int, c_int, c_double, c_int, dp, dp, dp]
+    lib.oracle_hllc_opt.restype = None
     lib.oracle_totals.argtypes = [c_int, lp, dp, dp, dp]
     for f in ("oracle_prim_to_cons", "oracle_cons_to_prim", "oracle_cfl_dt", "oracle_fluxes",
               "oracle_run", "oracle_totals", "oracle_has_openmp", "oracle_max_threads"):
@@ -131,11 +136,15 @@ def interpolate(y0: float, y1: float, y2: float):
     return lo.value, hi.value
 
 
-def hllc(dim: int, axis: int, gamma: float, VL, VR) -> np.ndarray:
-    """HLLC flux through a face with normal `axis` from primitive states VL (lower) and VR (upper)."""
+def hllc(dim: int, axis: int, gamma: float, VL, VR, riemann: int = 0) -> np.ndarray:
+    """HLLC flux through a face with normal `axis` from primitive states VL (lower) and VR
+    (upper); riemann: wave-speed estimate, 0 Davis (default), 1 pressure-based."""
     vl, vr = _c64(VL), _c64(VR)
     out = np.zeros(dim + 2)
-    _load().oracle_hllc(dim, axis, gamma, _dp(vl), _dp(vr), _dp(out))
+    if riemann == 0:
+        _load().oracle_hllc(dim, axis, gamma, _dp(vl), _dp(vr), _dp(out))
+    else:
+        _load().oracle_hllc_opt(dim, axis, gamma, riemann, _dp(vl), _dp(vr), _dp(out))
     return out
 
 
@@ -197,8 +206,10 @@ def fluxes(U, gamma: float, bc=(0, 0, 0), dr=None):
 
 
 def run(U, gamma: float, cfl: float, n_steps: int, bc=(0, 0, 0), t_end: float = 0.0,
-        t0: float = 0.0, dr=None, threads: int = 1, check: bool = True):
-    """Advance a copy of U by up to n_steps midpoint-RK steps.
+        t0: float = 0.0, dr=None, threads: int = 1, check: bool = True, order: int = 2,
+        riemann: int = 0):
+    """Advance a copy of U by up to n_steps midpoint-RK steps (order: reconstruction order 1
+    or 2; riemann: HLLC wave speeds, 0 Davis, 1 pressure-based).
 
     Returns (U_new, t, steps_done, rc).  With t_end > 0 the last step is clipped onto t_end.
     """
@@ -207,8 +218,13 @@ def run(U, gamma: float, cfl: float, n_steps: int, bc=(0, 0, 0), t_end: float = 
     bcs = (ctypes.c_int * 3)(*(list(bc) + [0] * (3 - len(bc))))
     t = ctypes.c_double(t0)
     done = ctypes.c_int()
-    rc = _load().oracle_run(dim, n, _dr(dim, n, dr), gamma, bcs, cfl, _dp(u), int(n_steps),
-                            float(t_end), ctypes.byref(t), ctypes.byref(done), int(threads))
+    if order == 2 and riemann == 0:
+        rc = _load().oracle_run(dim, n, _dr(dim, n, dr), gamma, bcs, cfl, _dp(u), int(n_steps),
+                                float(t_end), ctypes.byref(t), ctypes.byref(done), int(threads))
+    else:
+        rc = _load().oracle_run_opt(dim, n, _dr(dim, n, dr), gamma, bcs, cfl, int(order),
+                                    int(riemann), _dp(u), int(n_steps), float(t_end),
+                                    ctypes.byref(t), ctypes.byref(done), int(threads))
     if check and rc not in (ORC_OK,):
         raise OracleError(f"oracle_run rc={rc}")
     return u, t.value, done.value, rc

@@ -35,6 +35,13 @@
  *  - Time: the last step is clipped so that t lands on t_end; a clipped step
  *    sets t = t_end exactly.
  *  - No positivity floors.
+ *  Scheme options (defaults: order 2, Davis speeds):
+ *  - order 1: the first-order branch of the paper's interpolation (section 4.2 listing): the
+ *    face values are the cell values, no slopes.
+ *  - pressure-based HLLC wave speeds (Toro's PVRS estimate): p_pv = (p_L + p_R)/2 -
+ *    (u_R - u_L) rho_bar a_bar / 2 with rho_bar, a_bar the arithmetic means,
+ *    p_star = max(0, p_pv), q_K = 1 if p_star <= p_K else
+ *    sqrt(1 + (gamma+1)/(2 gamma) (p_star / p_K - 1)), S_L = u_L - a_L q_L, S_R = u_R + a_R q_R.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -173,12 +180,24 @@ void oracle_interpolate(double y0, double y1, double y2, double *left, double *r
     *right = y1 + 0.5 * dy; /* value at the cell's upper face */
 }
 
+/* Interpolate of the given order: order 1 leaves the cell value on both faces. */
+static void interpolate_order(int order, double y0, double y1, double y2, double *left,
+                              double *right) {
+    if (order == 1) {
+        *left = y1;
+        *right = y1;
+        return;
+    }
+    oracle_interpolate(y0, y1, y2, left, right);
+}
+
 /* ------------------------------------------------- HLLC (section 4.1) ----- */
 
 /* HLLC_a(VL, VR): flux through a face whose normal is axis a, from the
- * primitive states on its lower (L) and upper (R) side. */
-void oracle_hllc(int dim, int a, double gamma, const double *VL, const double *VR,
-                 double *F) {
+ * primitive states on its lower (L) and upper (R) side; riemann selects the wave-speed
+ * estimate (0 Davis, 1 pressure-based). */
+void oracle_hllc_opt(int dim, int a, double gamma, int riemann, const double *VL,
+                     const double *VR, double *F) {
     double rl = VL[0], ul = VL[1 + a], pl = VL[dim + 1];
     double rr = VR[0], ur = VR[1 + a], pr = VR[dim + 1];
     double UL[5], UR[5], FL[5], FR[5];
@@ -189,8 +208,20 @@ void oracle_hllc(int dim, int a, double gamma, const double *VL, const double *V
 
     double al = sqrt(gamma * pl / rl);
     double ar = sqrt(gamma * pr / rr);
-    double SL = fmin(ul - al, ur - ar);
-    double SR = fmax(ul + al, ur + ar);
+    double SL, SR;
+    if (riemann == 0) { /* Davis */
+        SL = fmin(ul - al, ur - ar);
+        SR = fmax(ul + al, ur + ar);
+    } else { /* pressure-based (PVRS) */
+        double rbar = 0.5 * (rl + rr);
+        double abar = 0.5 * (al + ar);
+        double ppv = 0.5 * (pl + pr) - 0.5 * (ur - ul) * rbar * abar;
+        double ps = fmax(0.0, ppv);
+        double ql = ps <= pl ? 1.0 : sqrt(1.0 + (gamma + 1.0) / (2.0 * gamma) * (ps / pl - 1.0));
+        double qr = ps <= pr ? 1.0 : sqrt(1.0 + (gamma + 1.0) / (2.0 * gamma) * (ps / pr - 1.0));
+        SL = ul - al * ql;
+        SR = ur + ar * qr;
+    }
     double Ss = (pr - pl + rl * ul * (SL - ul) - rr * ur * (SR - ur)) /
                 (rl * (SL - ul) - rr * (SR - ur));
 
@@ -220,6 +251,11 @@ void oracle_hllc(int dim, int a, double gamma, const double *VL, const double *V
     for (int k = 0; k < nv; ++k) F[k] = FK[k] + S * (Us[k] - U[k]);
 }
 
+void oracle_hllc(int dim, int a, double gamma, const double *VL, const double *VR,
+                 double *F) {
+    oracle_hllc_opt(dim, a, gamma, 0, VL, VR, F);
+}
+
 /* Euler flux, exported for the special-case pins (HLLC(V,V) = F(V)). */
 void oracle_euler_flux(int dim, int a, double gamma, const double *V, double *F) {
     euler_flux(dim, a, gamma, V, F);
@@ -230,6 +266,8 @@ void oracle_euler_flux(int dim, int a, double gamma, const double *V, double *F)
 typedef struct {
     grid_t G;
     int nv;
+    int order;         /* reconstruction order, 1 or 2 */
+    int riemann;       /* HLLC wave speeds: 0 Davis, 1 pressure-based */
     double *U[5];      /* padded conserved planes (scratch copy of a stage input) */
     double *V[5];      /* padded primitive planes */
     double *VL[3][5];  /* face values, lower side, per axis */
@@ -254,6 +292,7 @@ static int alloc_work(work_t *W, const grid_t *G) {
     memset(W, 0, sizeof *W);
     W->G = *G;
     W->nv = G->dim + 2;
+    W->order = 2;
     for (int k = 0; k < W->nv; ++k) {
         W->U[k] = calloc((size_t)G->npad, sizeof(double));
         W->V[k] = calloc((size_t)G->npad, sizeof(double));
@@ -319,8 +358,8 @@ static void flux_all_axes(work_t *W, double *const *U_int) {
                     long ci = pidx(G, i0, i1, i2);
                     for (int k = 0; k < nv; ++k) {
                         double lft, rgt;
-                        oracle_interpolate(W->V[k][ci - stride], W->V[k][ci],
-                                           W->V[k][ci + stride], &lft, &rgt);
+                        interpolate_order(W->order, W->V[k][ci - stride], W->V[k][ci],
+                                          W->V[k][ci + stride], &lft, &rgt);
                         if (c[a] >= 0) { /* face c - 1/2 exists: VR there */
                             W->VR[a][k][fidx(G, a, c)] = lft;
                         }
@@ -339,7 +378,7 @@ static void flux_all_axes(work_t *W, double *const *U_int) {
                 vl[k] = W->VL[a][k][f];
                 vr[k] = W->VR[a][k][f];
             }
-            oracle_hllc(dim, a, G->gamma, vl, vr, fl);
+            oracle_hllc_opt(dim, a, G->gamma, W->riemann, vl, vr, fl);
             for (int k = 0; k < nv; ++k) W->F[a][k][f] = fl[k];
         }
     }
@@ -510,15 +549,18 @@ int oracle_fluxes(int dim, const long n[3], const double dr[3], double gamma,
  * dt = min(dt, t_end - t) and a clipped step sets t = t_end; stop once
  * t >= t_end.  Returns ORC_ENONFINITE if a step leaves a non-finite value,
  * rho <= 0 or p <= 0 (the state then holds that step's output). */
-int oracle_run(int dim, const long n[3], const double dr[3], double gamma,
-               const int bc[3], double cfl, double *U, int n_steps, double t_end,
-               double *t_inout, int *steps_done, int nthreads) {
+int oracle_run_opt(int dim, const long n[3], const double dr[3], double gamma,
+                   const int bc[3], double cfl, int order, int riemann, double *U, int n_steps,
+                   double t_end, double *t_inout, int *steps_done, int nthreads) {
     grid_t G;
     int rc = make_grid(&G, dim, n, dr, gamma, bc);
     if (rc) return rc;
+    if ((order != 1 && order != 2) || (riemann != 0 && riemann != 1)) return ORC_EINVAL;
     set_threads(nthreads);
     work_t W;
     rc = alloc_work(&W, &G);
+    W.order = order;
+    W.riemann = riemann;
     double *u1 = rc ? NULL : calloc((size_t)(dim + 2) * (size_t)G.ncell, sizeof(double));
     if (rc || !u1) {
         free_work(&W);
@@ -552,6 +594,13 @@ int oracle_run(int dim, const long n[3], const double dr[3], double gamma,
     free(u1);
     free_work(&W);
     return rc;
+}
+
+int oracle_run(int dim, const long n[3], const double dr[3], double gamma,
+               const int bc[3], double cfl, double *U, int n_steps, double t_end,
+               double *t_inout, int *steps_done, int nthreads) {
+    return oracle_run_opt(dim, n, dr, gamma, bc, cfl, 2, 0, U, n_steps, t_end, t_inout,
+                          steps_done, nthreads);
 }
 
 /* fixed-order pairwise sum of x[0..n) */

@@ -25,6 +25,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # translation unit -> extra flags
 UNITS = {
     "stage_f32_d3.cu": ["-ftz=true"],
+    "stage_f32_d3b.cu": ["-ftz=true"],
     "stage_f32_d12.cu": ["-ftz=true"],
     "stage_f64.cu": ["--fmad=false"],
     "aux_kernels.cu": ["--fmad=false"],

@@ -83,9 +83,13 @@ int tile_compiled(int prec, int dim, int bx, int by) {
     return 0;
 }
 
+// Defaults chosen by the variant tuner's measurements on GB300: in 3D the FP32 kernels with the
+// three-CTA register budget; in 1D and 2D, where a CTA updates one tile, the separate CFL pass
+// (a fused per-CTA reduction costs more there than one extra read of the state).
 void default_variant(int prec, int dim, hydro_variant_t *v) {
-    v->split = 0;
+    v->split = dim < 3 ? 1 : 0;
     v->staging = 1;
+    v->occupancy = (dim == 3 && prec == HYDRO_F32) ? 3 : 2;
     v->march = 0;
     if (dim == 1) {
         v->tile_x = 128;
@@ -95,7 +99,6 @@ void default_variant(int prec, int dim, hydro_variant_t *v) {
         v->tile_y = 8;
     }
     if (dim == 3) v->march = 64;
-    (void)prec;
 }
 
 // Resolve a (possibly partial) variant against the defaults; false if not compiled.
@@ -105,11 +108,14 @@ bool resolve_variant(int prec, int dim, const hydro_variant_t *in, hydro_variant
         if (in->tile_x) out->tile_x = in->tile_x;
         if (in->tile_y) out->tile_y = in->tile_y;
         if (in->march) out->march = in->march;
-        out->split = in->split;
+        if (in->split) out->split = in->split == 2 ? 0 : in->split;
         if (in->staging) out->staging = in->staging;
+        if (in->occupancy) out->occupancy = in->occupancy;
     }
-    if (out->split != 0 && out->split != 1) return false;
+    if (in && (in->split < 0 || in->split > 2)) return false;
     if (out->staging != 1 && out->staging != 2) return false;
+    if (out->occupancy != 2 && out->occupancy != 3) return false;
+    if (out->occupancy == 3 && (dim != 3 || prec != HYDRO_F32)) return false;
     if (dim == 3 && out->march < 1) return false;
     if (dim < 3) {
         out->march = 1;
@@ -130,6 +136,7 @@ struct hydro_ctx {
     int periodic[3] = {1, 1, 1};
     double dr[3] = {1, 1, 1};
     double gamma = 1.4, cfl = 0.4;
+    int order = 2, riemann = 0;
     hydro_variant_t var = {};
     Layout lay = {};
     unsigned char *ws = nullptr;
@@ -174,6 +181,9 @@ hydro::StageLaunch stage_args(const hydro_ctx *c, const hydro_state_t *s, int st
     L.tile_y = c->var.tile_y;
     L.prefetch = c->var.staging == 2 ? 0 : 1;
     L.split = c->var.split;
+    L.occupancy = c->var.occupancy;
+    L.order = c->order;
+    L.riemann = c->riemann;
     L.gamma = c->gamma;
     L.ctrl = c->ctrl;
     return L;
@@ -458,6 +468,22 @@ int hydro_destroy(hydro_ctx_t *c) {
     for (auto e : c->events) cudaEventDestroy(e);
     if (c->cap) cudaStreamDestroy(c->cap);
     delete c;
+    return HYDRO_OK;
+}
+
+int hydro_set_scheme(hydro_ctx_t *c, int32_t order, int32_t riemann) {
+    if (!c || (order != 1 && order != 2) || (riemann != 0 && riemann != 1)) return HYDRO_EINVAL;
+    if (order == c->order && riemann == c->riemann) return HYDRO_OK;
+    DeviceGuard dg(c->device);
+    // captured graphs hold the old kernel arguments
+    for (auto &g : c->graphs)
+        if (g.exec) {
+            cudaGraphExecDestroy(g.exec);
+            g.exec = nullptr;
+            g.chunk = 0;
+        }
+    c->order = order;
+    c->riemann = riemann;
     return HYDRO_OK;
 }
 

@@ -127,9 +127,12 @@ __device__ __forceinline__ float minbee(float d01, float d12) {
 // increasing axis order).  Flux components: (mass, normal momentum, tangential momenta,
 // energy).  NLAST: the normal axis is the last axis (only the kinetic-energy summation order
 // of the exact mode depends on it: v^2 is summed in axis order).
+// riemann: wave-speed estimate, 0 = Davis, 1 = pressure-based (Toro's PVRS: p_pv from the
+// arithmetic means, p* = max(0, p_pv), q_K = 1 or sqrt(1 + (g+1)/(2g) (p*/p_K - 1)) behind a
+// shock, S_L = u_L - a_L q_L, S_R = u_R + a_R q_R).
 template <class T, int D, bool NLAST>
 __device__ __forceinline__ void hllc(T rl, const T (&vl)[D], T pl, T rr, const T (&vr)[D], T pr,
-                                     const Gas<T> &G, T (&F)[D + 2]) {
+                                     const Gas<T> &G, T (&F)[D + 2], int riemann = 0) {
     using A = Arith<T>;
     const T ul = vl[0], ur = vr[0];
     T al, ar, irl = T(0), irr = T(0);
@@ -142,8 +145,28 @@ __device__ __forceinline__ void hllc(T rl, const T (&vl)[D], T pl, T rr, const T
         al = A::sqrt_(G.g * pl * irl);
         ar = A::sqrt_(G.g * pr * irr);
     }
-    const T SL = fmin(ul - al, ur - ar);
-    const T SR = fmax(ul + al, ur + ar);
+    T SL, SR;
+    if (riemann == 0) {
+        SL = fmin(ul - al, ur - ar);
+        SR = fmax(ul + al, ur + ar);
+    } else {
+        const T rbar = T(0.5) * (rl + rr);
+        const T abar = T(0.5) * (al + ar);
+        const T ppv = T(0.5) * (pl + pr) - T(0.5) * (ur - ul) * rbar * abar;
+        const T ps = fmax(T(0), ppv);
+        T ql = T(1), qr = T(1);
+        if constexpr (A::exact) {
+            const T c = (G.g + T(1)) / (T(2) * G.g);
+            if (!(ps <= pl)) ql = sqrt(T(1) + c * (ps / pl - T(1)));
+            if (!(ps <= pr)) qr = sqrt(T(1) + c * (ps / pr - T(1)));
+        } else {
+            const T c = (G.g + 1.0f) * (0.5f * Arith<float>::rcp(G.g));
+            if (!(ps <= pl)) ql = A::sqrt_(fmaf(c, ps * Arith<float>::rcp(pl) - 1.0f, 1.0f));
+            if (!(ps <= pr)) qr = A::sqrt_(fmaf(c, ps * Arith<float>::rcp(pr) - 1.0f, 1.0f));
+        }
+        SL = ul - al * ql;
+        SR = ur + ar * qr;
+    }
     const T ml = rl * (SL - ul);
     const T mr = rr * (SR - ur);
     T Ss;

@@ -22,6 +22,9 @@ struct StageLaunch {
     int tile_x, tile_y;
     int prefetch;       // dim 3: 1 = next plane's loads one plane ahead, 0 = at staging
     int split;          // stage 2: 0 = dt reduction fused, 1 = left to a separate CFL pass
+    int occupancy;      // dim 3 FP32: resident CTAs per SM the register budget targets (2 or 3)
+    int order;          // reconstruction order (2 MinBee, 1 first order); 0 = 2
+    int riemann;        // HLLC wave speeds: 0 Davis, 1 pressure-based
     double dr[3];
     double gamma;
     void *ctrl;

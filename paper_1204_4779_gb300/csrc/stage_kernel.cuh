@@ -38,6 +38,8 @@ template <class T> struct StageArgs {
     int n[3];
     int periodic[3];
     int march;          // z-planes per CTA (dim 3)
+    int order;          // reconstruction order: 2 = MinBee slopes, 1 = face values = cell values
+    int riemann;        // HLLC wave speeds: 0 = Davis, 1 = pressure-based
     double dr[3];       // cell sizes (the FP64 CFL signal divides by them)
     T inv_dr[3];        // 1 / dr in the element type (the FP32 CFL signal multiplies)
     Gas<T> gas;
@@ -65,7 +67,8 @@ template <class T, int D, int BX, int BY> struct StageShape {
 // (0 or 1).  Face between q1 and q2.  Writes the flux in axis order to sF (field stride NF).
 template <class T, int D, int PL, int NF>
 __device__ __forceinline__ void inplane_face(const T *__restrict__ sV, T *__restrict__ sF, int o,
-                                             int s, int a, int f, const Gas<T> &G) {
+                                             int s, int a, int f, const Gas<T> &G,
+                                             int order = 2, int riemann = 0) {
     constexpr int NV = D + 2;
     // field of the normal velocity, then tangential ones in increasing axis order
     int fld[D];
@@ -77,10 +80,16 @@ __device__ __forceinline__ void inplane_face(const T *__restrict__ sV, T *__rest
     for (int k = 0; k < NV; ++k) {
         const int field = (k == 0) ? 0 : (k == NV - 1 ? NV - 1 : fld[k - 1]);
         const T *q = sV + field * PL + o;
-        const T q0 = q[0], q1 = q[s], q2 = q[2 * s], q3 = q[3 * s];
-        const T d01 = q1 - q0, d12 = q2 - q1, d23 = q3 - q2;
-        L[k] = q1 + T(0.5) * minbee(d01, d12);
-        R[k] = q2 - T(0.5) * minbee(d12, d23);
+        const T q1 = q[s], q2 = q[2 * s];
+        if (order == 2) {
+            const T q0 = q[0], q3 = q[3 * s];
+            const T d01 = q1 - q0, d12 = q2 - q1, d23 = q3 - q2;
+            L[k] = q1 + T(0.5) * minbee(d01, d12);
+            R[k] = q2 - T(0.5) * minbee(d12, d23);
+        } else {
+            L[k] = q1;
+            R[k] = q2;
+        }
     }
     T vl[D], vr[D], F[NV];
 #pragma unroll
@@ -88,7 +97,7 @@ __device__ __forceinline__ void inplane_face(const T *__restrict__ sV, T *__rest
         vl[b] = L[1 + b];
         vr[b] = R[1 + b];
     }
-    hllc<T, D, false>(L[0], vl, L[NV - 1], R[0], vr, R[NV - 1], G, F);
+    hllc<T, D, false>(L[0], vl, L[NV - 1], R[0], vr, R[NV - 1], G, F, riemann);
     sF[f] = F[0];
 #pragma unroll
     for (int b = 0; b < D; ++b) sF[fld[b] * NF + f] = F[1 + b];
@@ -99,7 +108,8 @@ __device__ __forceinline__ void inplane_face(const T *__restrict__ sV, T *__rest
 // states and MinBee slopes.  Returned normal-first: (mass, m_z, m_x, m_y, E).
 template <class T>
 __device__ __forceinline__ void fz_face(const T (&Vlo)[5], const T (&dlo)[5], const T (&Vhi)[5],
-                                        const T (&dhi)[5], const Gas<T> &G, T (&F)[5]) {
+                                        const T (&dhi)[5], const Gas<T> &G, T (&F)[5],
+                                        int riemann = 0) {
     T L[5], R[5];
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
@@ -108,7 +118,7 @@ __device__ __forceinline__ void fz_face(const T (&Vlo)[5], const T (&dlo)[5], co
     }
     const T vl[3] = {L[3], L[1], L[2]};
     const T vr[3] = {R[3], R[1], R[2]};
-    hllc<T, 3, true>(L[0], vl, L[4], R[0], vr, R[4], G, F);
+    hllc<T, 3, true>(L[0], vl, L[4], R[0], vr, R[4], G, F, riemann);
 }
 
 // Shared-memory position (lx, ly) of halo task h of a BX x BY tile (the cross-shaped two-cell
@@ -177,16 +187,19 @@ __device__ __forceinline__ bool face_task(int tid, int j, int &o, int &s, int &a
     return ok;
 }
 
-template <class T, int NT> struct MinBlocks {
-    static constexpr int value = (sizeof(T) == 4 && NT <= 256) ? 2 : 1;
+// Resident CTAs per SM the register budget targets: OCC 256-thread CTAs' worth of warps in
+// FP32 (OCC = 2: ~128 registers per thread, 3: ~80); FP64 keeps one CTA's budget.
+template <class T, int NT, int OCC = 2> struct MinBlocks {
+    static constexpr int v = OCC * 256 / NT;
+    static constexpr int value = (sizeof(T) == 4) ? (v > 1 ? v : 1) : 1;
 };
 
 // STAGE: RK stage (1 or 2).  PF (staging depth, dim 3): 1 = the next z-plane's loads are
 // issued one plane ahead of their use, 0 = each plane is loaded when it is staged.  FUSED
 // (stage 2): 1 = the CFL signal and the next dt are reduced in this kernel's epilogue, 0 = left
-// to a separate CFL pass.
-template <class T, int D, int BX, int BY, int STAGE, int PF = 1, bool FUSED = true>
-__global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY>::value))
+// to a separate CFL pass.  OCC: resident CTAs per SM the register budget targets.
+template <class T, int D, int BX, int BY, int STAGE, int PF = 1, bool FUSED = true, int OCC = 2>
+__global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY, OCC>::value))
     stage_kernel(const StageArgs<T> A) {
     using S = StageShape<T, D, BX, BY>;
     constexpr int NV = S::NV, NT = S::NT, HX = S::HX, PL = S::PL;
@@ -208,6 +221,7 @@ __global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY>::value))
     const T cy = (D >= 2) ? T(__ldcg(&ctrl->coef[STAGE - 1][1])) : T(0);
     const T cz = (D == 3) ? T(__ldcg(&ctrl->coef[STAGE - 1][2])) : T(0);
     const Gas<T> G = A.gas;
+    const bool order2 = A.order == 2;
 
     const int tid = threadIdx.x;
     const int tx = tid % BX, ty = tid / BX;
@@ -282,10 +296,10 @@ __global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY>::value))
         prim_of_cons<T, D>(u, Vn, G);
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
-            dzm[k] = minbee(Vm1[k] - Vm2[k], Vc[k] - Vm1[k]);
-            dzc[k] = minbee(Vc[k] - Vm1[k], Vn[k] - Vc[k]);
+            dzm[k] = order2 ? minbee(Vm1[k] - Vm2[k], Vc[k] - Vm1[k]) : T(0);
+            dzc[k] = order2 ? minbee(Vc[k] - Vm1[k], Vn[k] - Vc[k]) : T(0);
         }
-        fz_face(Vm1, dzm, Vc, dzc, G, Fzm);
+        fz_face(Vm1, dzm, Vc, dzc, G, Fzm, A.riemann);
         if constexpr (PF == 1) load_u(pown, remap(zb + 2, nz, pz), own_off);
     } else {
         T u[NV];
@@ -332,13 +346,15 @@ __global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY>::value))
         // in-plane faces of plane z, each once
 #pragma unroll
         for (int j = 0; j < FPT; ++j)
-            if (f_ok[j]) inplane_face<T, D, PL, NF>(sVc, sF, f_o[j], f_s[j], f_a[j], f_id[j], G);
+            if (f_ok[j])
+                inplane_face<T, D, PL, NF>(sVc, sF, f_o[j], f_s[j], f_a[j], f_id[j], G, A.order,
+                                           A.riemann);
         // z-face above this column
         T Fzp[NV], dzn[NV];
         if constexpr (D == 3) {
 #pragma unroll
-            for (int k = 0; k < NV; ++k) dzn[k] = minbee(Vn[k] - Vc[k], Vnn[k] - Vn[k]);
-            fz_face(Vc, dzc, Vn, dzn, G, Fzp);
+            for (int k = 0; k < NV; ++k) dzn[k] = order2 ? minbee(Vn[k] - Vc[k], Vnn[k] - Vn[k]) : T(0);
+            fz_face(Vc, dzc, Vn, dzn, G, Fzp, A.riemann);
             // stage plane z+1 into the other buffer, prefetch the halo of plane z+2
             if (z + 1 < ze) {
                 if constexpr (PF == 0) {

@@ -21,23 +21,25 @@ template <class T> static StageArgs<T> make_stage_args(const StageLaunch &L) {
         A.inv_dr[a] = T(1.0 / L.dr[a]);
     }
     A.march = L.march;
+    A.order = L.order == 1 ? 1 : 2;
+    A.riemann = L.riemann;
     A.gas = make_gas<T>(L.gamma);
     A.ctrl = static_cast<Ctrl *>(L.ctrl);
     return A;
 }
 
-// The kernels of one (T, D, tile) for one staging depth PF: stage 1, stage 2 with the fused dt
-// reduction, stage 2 without it.
-template <class T, int D, int BX, int BY, int PF> struct StageKernels {
-    static constexpr auto s1 = stage_kernel<T, D, BX, BY, 1, PF, true>;
-    static constexpr auto s2 = stage_kernel<T, D, BX, BY, 2, PF, true>;
-    static constexpr auto s2_split = stage_kernel<T, D, BX, BY, 2, PF, false>;
+// The kernels of one (T, D, tile) for one staging depth PF and occupancy target OCC: stage 1,
+// stage 2 with the fused dt reduction, stage 2 without it.
+template <class T, int D, int BX, int BY, int PF, int OCC> struct StageKernels {
+    static constexpr auto s1 = stage_kernel<T, D, BX, BY, 1, PF, true, OCC>;
+    static constexpr auto s2 = stage_kernel<T, D, BX, BY, 2, PF, true, OCC>;
+    static constexpr auto s2_split = stage_kernel<T, D, BX, BY, 2, PF, false, OCC>;
 };
 
-template <class T, int D, int BX, int BY, int PF>
+template <class T, int D, int BX, int BY, int PF, int OCC = 2>
 static cudaError_t launch_stage_pf(const StageLaunch &L, const StageArgs<T> &A, cudaStream_t st) {
     using S = StageShape<T, D, BX, BY>;
-    using K = StageKernels<T, D, BX, BY, PF>;
+    using K = StageKernels<T, D, BX, BY, PF, OCC>;
     const dim3 grid((unsigned)((A.n[0] + BX - 1) / BX),
                     (unsigned)((D >= 2) ? (A.n[1] + BY - 1) / BY : 1),
                     (unsigned)((D == 3) ? (A.n[2] + A.march - 1) / A.march : 1));
@@ -51,9 +53,9 @@ static cudaError_t launch_stage_pf(const StageLaunch &L, const StageArgs<T> &A, 
     return cudaGetLastError();
 }
 
-template <class T, int D, int BX, int BY, int PF>
+template <class T, int D, int BX, int BY, int PF, int OCC = 2>
 static cudaError_t prepare_stage_pf() {
-    using K = StageKernels<T, D, BX, BY, PF>;
+    using K = StageKernels<T, D, BX, BY, PF, OCC>;
     const int smem = (int)StageShape<T, D, BX, BY>::smem_bytes;
     cudaError_t e = cudaFuncSetAttribute(K::s1, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess)
@@ -63,17 +65,24 @@ static cudaError_t prepare_stage_pf() {
     return e;
 }
 
-// Both staging depths exist only in dim 3 (the z-march); dims 1 and 2 have one plane.
+template <class T, int D, int BX, int BY, int PF, int OCC>
+static cudaError_t run_or_prepare(const StageLaunch &L, cudaStream_t st, bool prepare_only) {
+    if (prepare_only) return prepare_stage_pf<T, D, BX, BY, PF, OCC>();
+    return launch_stage_pf<T, D, BX, BY, PF, OCC>(L, make_stage_args<T>(L), st);
+}
+
+// Both staging depths and both occupancy targets exist only in dim 3 (the z-march; dims 1 and
+// 2 have one plane and small register needs).
 template <class T, int D, int BX, int BY, bool BOTH_PF>
 static cudaError_t dispatch_tile(const StageLaunch &L, cudaStream_t st, bool prepare_only) {
     if constexpr (BOTH_PF && D == 3) {
-        if (L.prefetch == 0) {
-            if (prepare_only) return prepare_stage_pf<T, D, BX, BY, 0>();
-            return launch_stage_pf<T, D, BX, BY, 0>(L, make_stage_args<T>(L), st);
-        }
+        const bool occ3 = L.occupancy == 3;
+        if (L.prefetch == 0)
+            return occ3 ? run_or_prepare<T, D, BX, BY, 0, 3>(L, st, prepare_only)
+                        : run_or_prepare<T, D, BX, BY, 0, 2>(L, st, prepare_only);
+        if (occ3) return run_or_prepare<T, D, BX, BY, 1, 3>(L, st, prepare_only);
     }
-    if (prepare_only) return prepare_stage_pf<T, D, BX, BY, 1>();
-    return launch_stage_pf<T, D, BX, BY, 1>(L, make_stage_args<T>(L), st);
+    return run_or_prepare<T, D, BX, BY, 1, 2>(L, st, prepare_only);
 }
 
 }  // namespace hydro

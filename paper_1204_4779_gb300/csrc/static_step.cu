@@ -102,6 +102,7 @@ extern "C" int hydro_step_static(const hydro_grid_t *grid, double gamma, const i
     L.tile_y = dim == 1 ? 1 : 8;
     L.prefetch = 1;
     L.split = 0;
+    L.occupancy = 2;
     L.gamma = gamma;
     for (int a = 0; a < 3; ++a) {
         L.n[a] = n[a];

@@ -27,7 +27,7 @@ HYDRO_F64, HYDRO_F32 = 0, 1
 EXPORTS = (
     "hydro_version", "hydro_strerror", "hydro_last_cuda_error", "hydro_variant_supported",
     "hydro_workspace_bytes", "hydro_create", "hydro_destroy", "hydro_set_stream", "hydro_step",
-    "hydro_step_host", "hydro_cfl_dt", "hydro_totals", "hydro_status", "hydro_prim_to_cons",
+    "hydro_step_host", "hydro_set_scheme", "hydro_cfl_dt", "hydro_totals", "hydro_status", "hydro_prim_to_cons",
     "hydro_cons_to_prim", "hydro_set_profiling", "hydro_kernel_times", "hydro_step_static",
     "hydro_batch_workspace_bytes", "hydro_batch_create", "hydro_batch_destroy",
     "hydro_batch_offsets", "hydro_batch_set_stream", "hydro_batch_step", "hydro_batch_totals",
@@ -57,7 +57,8 @@ class State(ctypes.Structure):
 
 class Variant(ctypes.Structure):
     _fields_ = [("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32),
-                ("march", ctypes.c_int32), ("split", ctypes.c_int32), ("staging", ctypes.c_int32)]
+                ("march", ctypes.c_int32), ("split", ctypes.c_int32), ("staging", ctypes.c_int32),
+                ("occupancy", ctypes.c_int32)]
 
 
 _lib = None
@@ -89,6 +90,7 @@ def load_library(path: str = LIB_PATH, build_if_missing: bool = True):
                               P(vp)], ctypes.c_int),
             "hydro_destroy": ([vp], ctypes.c_int),
             "hydro_set_stream": ([vp, vp], ctypes.c_int),
+            "hydro_set_scheme": ([vp, i32, i32], ctypes.c_int),
             "hydro_step": ([vp, P(State), i32, dbl, P(dbl), P(i32)], ctypes.c_int),
             "hydro_step_host": ([vp, P(State), P(vp), P(vp), i32, dbl, P(dbl), P(i32)], ctypes.c_int),
             "hydro_cfl_dt": ([vp, P(State), P(dbl)], ctypes.c_int),
@@ -157,9 +159,9 @@ def state_struct(t: torch.Tensor, nv: int) -> State:
 
 
 def variant_supported(dtype, dim: int, tile=(0, 0), march: int = 0, split: int = 0,
-                      staging: int = 0) -> bool:
+                      staging: int = 0, occupancy: int = 0) -> bool:
     lib = load_library()
-    v = Variant(int(tile[0]), int(tile[1]), int(march), int(split), int(staging))
+    v = Variant(int(tile[0]), int(tile[1]), int(march), int(split), int(staging), int(occupancy))
     return bool(lib.hydro_variant_supported(_prec(dtype), dim, ctypes.byref(v)))
 
 
@@ -187,7 +189,8 @@ class Solver:
     """One context of libhydro.so on the current CUDA device.
 
     shape: cells per axis (nx, [ny, [nz]]); bc: per-axis "periodic"/"outflow" (or 0/1);
-    variant: dict(tile=(bx, by), march=m, split=0|1, staging=0|1|2) or None for the default.
+    variant: dict(tile=(bx, by), march=m, split=0|1, staging=0|1|2, occupancy=0|2|3) or None for
+    the default.
     """
 
     def __init__(self, shape, gamma: float, bc="periodic", dtype=torch.float32, cfl: float = 0.4,
@@ -218,7 +221,8 @@ class Solver:
         if variant:
             tile = variant.get("tile", (0, 0))
             var = Variant(int(tile[0]), int(tile[1]), int(variant.get("march", 0)),
-                          int(variant.get("split", 0)), int(variant.get("staging", 0)))
+                          int(variant.get("split", 0)), int(variant.get("staging", 0)),
+                          int(variant.get("occupancy", 0)))
         bcs = (ctypes.c_int32 * 3)(*(self.bc + [0] * (3 - self.dim)))
         ctx = ctypes.c_void_p()
         with torch.cuda.device(self.device):
@@ -307,6 +311,11 @@ class Solver:
     def set_profiling(self, on: bool):
         _check(self.lib.hydro_set_profiling(self.ctx, 1 if on else 0), "hydro_set_profiling")
 
+    def set_scheme(self, order: int = 2, riemann: int = 0):
+        """Reconstruction order (2 MinBee, 1 first order) and HLLC wave speeds (0 Davis, 1
+        pressure-based) of later steps."""
+        _check(self.lib.hydro_set_scheme(self.ctx, int(order), int(riemann)), "hydro_set_scheme")
+
     def kernel_times(self, reset: bool = False):
         """{kind: (total_ms, launches)} for kinds 'cfl', 'stage1', 'stage2'."""
         ms = (ctypes.c_double * 3)()
@@ -337,7 +346,7 @@ class BatchSolver:
                                      for b in bc])
         nx = (ctypes.c_int64 * self.n)(*[s[0] for s in self.shapes])
         ny = (ctypes.c_int64 * self.n)(*[s[1] for s in self.shapes])
-        var = Variant(int(tile[0]), int(tile[1]), 0, 0, 0) if tile else None
+        var = Variant(int(tile[0]), int(tile[1]), 0, 0, 0, 0) if tile else None
         nbytes = ctypes.c_size_t()
         _check(self.lib.hydro_batch_workspace_bytes(self.n, nx, ny, _prec(dtype),
                                                     ctypes.byref(var) if var else None,

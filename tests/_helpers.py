@@ -9,10 +9,11 @@ def shape_of(V):
     return tuple(reversed(V.shape[1:]))
 
 
-def oracle_run(V, gamma, bc, cfl, n_steps, t_end=0.0, threads=None):
+def oracle_run(V, gamma, bc, cfl, n_steps, t_end=0.0, threads=None, order=2, riemann=0):
     U = oracle.prim_to_cons(V, gamma)
     th = oracle.max_threads() if threads is None else threads
-    return oracle.run(U, gamma, cfl, n_steps, bc=bc, t_end=t_end, threads=th)
+    return oracle.run(U, gamma, cfl, n_steps, bc=bc, t_end=t_end, threads=th, order=order,
+                      riemann=riemann)
 
 
 def gpu_state(V, gamma, dtype):
@@ -24,13 +25,16 @@ def gpu_state(V, gamma, dtype):
     return U64.to(dtype).contiguous()
 
 
-def gpu_run(V, gamma, bc, dtype, cfl, n_steps, t_end=0.0, variant=None, profiling=False):
+def gpu_run(V, gamma, bc, dtype, cfl, n_steps, t_end=0.0, variant=None, profiling=False,
+            scheme=None):
     import torch
     from paper_1204_4779_gb300 import hydro
     U = gpu_state(V, gamma, dtype)
     S = hydro.Solver(shape_of(V), gamma, bc=list(bc), dtype=dtype, cfl=cfl, variant=variant)
     if profiling:
         S.set_profiling(True)
+    if scheme is not None:
+        S.set_scheme(*scheme)
     t, steps = S.step(U, n_steps, t_end=t_end)
     out = U.to(torch.float64).cpu().numpy()
     S.close()

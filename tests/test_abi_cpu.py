@@ -73,7 +73,7 @@ def test_create_rejects_bad_arguments_before_touching_the_device():
     assert lib.hydro_create(ctypes.byref(g), 1.4, bc, 1, 0.4, None, None, 1 << 30, None, ctypes.byref(ctx)) == E
     bad_bc = (ctypes.c_int32 * 3)(0, 5, 0)
     assert lib.hydro_create(ctypes.byref(g), 1.4, bad_bc, 1, 0.4, None, ws, 1 << 30, None, ctypes.byref(ctx)) == E
-    v = hydro.Variant(7, 7, 0, 0, 0)
+    v = hydro.Variant(7, 7, 0, 0, 0, 0)
     assert lib.hydro_create(ctypes.byref(g), 1.4, bc, 1, 0.4, ctypes.byref(v), ws, 1 << 30, None,
                             ctypes.byref(ctx)) == hydro.HYDRO_EUNSUPPORTED
     assert lib.hydro_create(ctypes.byref(g), 1.4, bc, 1, 0.4, None, ws, 1 << 30, None, None) == E
@@ -102,5 +102,9 @@ def test_variant_table():
     assert hydro.variant_supported(torch.float32, 3, (16, 8), 32, split=1, staging=2)
     assert hydro.variant_supported(torch.float64, 3, (32, 8), 32, split=1)
     assert not hydro.variant_supported(torch.float64, 3, (32, 8), 32, staging=2)
-    assert not hydro.variant_supported(torch.float32, 3, (32, 8), 32, split=2)
+    assert hydro.variant_supported(torch.float32, 3, (32, 8), 32, split=2)
+    assert not hydro.variant_supported(torch.float32, 3, (32, 8), 32, split=3)
     assert hydro.variant_supported(torch.float32, 2, (32, 8), staging=2)  # one plane: ignored
+    assert hydro.variant_supported(torch.float32, 3, (32, 8), 64, occupancy=3)
+    assert not hydro.variant_supported(torch.float64, 3, (32, 8), 64, occupancy=3)
+    assert not hydro.variant_supported(torch.float32, 2, (32, 8), occupancy=3)

@@ -101,26 +101,60 @@ def test_sod_fp32_l1():
 
 
 @pytest.mark.parametrize("tile", [(32, 8), (32, 4), (64, 4), (16, 16), (32, 16), (16, 8)])
-@pytest.mark.parametrize("split,staging", [(0, 1), (1, 1), (0, 2), (1, 2)])
+@pytest.mark.parametrize("split,staging", [(2, 1), (1, 1), (2, 2), (1, 2)])
 def test_every_fp32_3d_variant(tile, split, staging):
-    """Every compiled tile with both fusion splits and both staging depths."""
+    """Every compiled tile with both fusion splits (2 fused, 1 separate CFL pass) and both
+    staging depths, on the two-CTA register budget."""
     V = inputs.smooth((45, 38, 21), seed=11)
     e, _, _ = _l1_32(V, 1.4, (0, 1, 0), 10,
-                     variant=dict(tile=tile, march=6, split=split, staging=staging))
+                     variant=dict(tile=tile, march=6, split=split, staging=staging, occupancy=2))
     assert e <= 2e-6
 
 
+@pytest.mark.parametrize("tile", [(32, 8), (32, 4), (64, 4), (16, 16), (32, 16), (16, 8)])
+@pytest.mark.parametrize("split,staging", [(2, 1), (1, 2)])
+def test_fp32_3d_occupancy3_variant(tile, split, staging):
+    """The kernels compiled for three resident CTAs per SM (about 80 registers a thread)."""
+    V = inputs.smooth((45, 38, 21), seed=11)
+    e, _, _ = _l1_32(V, 1.4, (0, 1, 0), 10,
+                     variant=dict(tile=tile, march=6, split=split, staging=staging, occupancy=3))
+    assert e <= 2e-6
+
+
+@pytest.mark.parametrize("split", [1, 2])
 @pytest.mark.parametrize("dim_shape", [(1, (300,)), (2, (70, 45)), (3, (37, 29, 23))])
-def test_fp64_split_variant_matches_oracle(dim_shape):
-    """The separate-CFL-pass variant computes the same step to 1e-10 in FP64."""
+def test_fp64_both_splits_match_oracle(dim_shape, split):
+    """Fused and separate dt reductions compute the same step to 1e-10 in FP64."""
     dim, shape = dim_shape
     V = inputs.smooth(shape, seed=14)
-    _compare64(V, 1.4, (0,) * dim, 0.4, 15, variant=dict(split=1, march=8))
+    _compare64(V, 1.4, (0,) * dim, 0.4, 15, variant=dict(split=split, march=8))
 
 
-def test_split_variant_time_clipping():
+@pytest.mark.parametrize("split", [1, 2])
+def test_both_splits_time_clipping(split):
     V = inputs.sod_1d(256)
-    _compare64(V, 1.4, (1,), 0.4, 100000, t_end=0.1, variant=dict(split=1))
+    _compare64(V, 1.4, (1,), 0.4, 100000, t_end=0.1, variant=dict(split=split))
+
+
+@pytest.mark.parametrize("order,riemann", [(1, 0), (2, 1), (1, 1)])
+@pytest.mark.parametrize("dim_shape", [(1, (300,)), (2, (70, 45)), (3, (37, 29, 23))])
+def test_scheme_options_fp64_match_oracle(dim_shape, order, riemann):
+    """First-order reconstruction and pressure-based wave speeds, FP64 <= 1e-10."""
+    dim, shape = dim_shape
+    V = inputs.smooth(shape, seed=15) if dim != 1 else inputs.sod_1d(300)
+    bc = (1,) if dim == 1 else (0,) * dim
+    G, tg, sg = gpu_run(V, 1.4, bc, F64, 0.4, 20, scheme=(order, riemann))
+    O, to, so, _ = oracle_run(V, 1.4, bc, 0.4, 20, order=order, riemann=riemann)
+    assert sg == so and tg == to
+    assert max_rel_err(G, O) <= 1e-10
+
+
+@pytest.mark.parametrize("order,riemann", [(1, 0), (2, 1)])
+def test_scheme_options_fp32_blast(order, riemann):
+    V = inputs.blast_3d(48, radius_cells=6.0)
+    G, tg, sg = gpu_run(V, 1.4, (0, 0, 0), F32, 0.4, 30, scheme=(order, riemann))
+    O, to, so, _ = oracle_run(V, 1.4, (0, 0, 0), 0.4, 30, order=order, riemann=riemann)
+    assert l1_rel(G[0], O[0]) <= 1e-5
 
 
 @pytest.mark.parametrize("tile", [(32, 8), (64, 4), (16, 16), (32, 16)])

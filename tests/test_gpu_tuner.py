@@ -1,7 +1,8 @@
 """The variant tuner on the GPU: real benchmarks of stage-kernel variants, the cost model
-trained on them by the library's CUDA kernels, and what the trained model gains: ranked by
-the trained network, a held-out grid's variants are found faster than by the same network
-untrained and than by the plain evolutionary search with the same number of benchmarks."""
+trained on them by the library's CUDA kernels, and what the trained model gains: it ranks a
+held-out grid's variants (unlike the same network trained on shuffled times), and a search
+guided by it finds the best variant with fewer benchmarks than the plain evolutionary search
+with the same number of benchmarks."""
 import math
 
 import numpy as np
@@ -17,8 +18,8 @@ def test_benchmark_records():
     b = T.Benchmark((40, 36, 33), reps=3, steps=2)
     r = b(b.space.default_genome())
     assert r.ok and r.mu > 0 and r.sigma >= 0
-    r2 = b((1, 2, 1, 1))
-    assert r2.ok and r2.genome == (1, 2, 1, 1)
+    r2 = b((1, 2, 1, 1, 1))
+    assert r2.ok and r2.genome == (1, 2, 1, 1, 1)
 
 
 @pytest.mark.slow
@@ -42,12 +43,13 @@ def test_trained_cost_model_ranks_and_guides_the_search():
     trained = T.CostModel(T.gpu_mlp_factory(64, seed=1), epochs=1500)
     losses = trained.fit(X, y)
     assert losses[-1] < 0.5 * losses[0]
-    untrained = T.CostModel(T.gpu_mlp_factory(64, seed=1), epochs=0)
-    untrained.fit(X, y, epochs=0)
+    # control: the same network trained on the same inputs with the measured times shuffled
+    control = T.CostModel(T.gpu_mlp_factory(64, seed=1), epochs=1500)
+    control.fit(X, rng.permutation(y))
     rho_t = T.spearman(trained.predict(Xt), meas)
-    rho_u = T.spearman(untrained.predict(Xt), meas)
-    print(f"spearman trained {rho_t:.2f} untrained {rho_u:.2f}")
-    assert rho_t > 0.5 and rho_t > rho_u + 0.2
+    rho_c = T.spearman(control.predict(Xt), meas)
+    print(f"spearman trained {rho_t:.2f} shuffled-target control {rho_c:.2f}")
+    assert rho_t > 0.5 and rho_t > rho_c + 0.3
     # the best measured variant among the model's top 8 is within 5 % of the true best
     top = np.argsort(trained.predict(Xt))[:8]
     assert max(truth[i].mu for i in top) >= 0.95 * best

@@ -21,7 +21,7 @@ G = 1.4
 MUTANTS = [
     ("addflux_sign", "sum += coef[a] * (fm - fp);", "sum += coef[a] * (fp - fm);"),
     ("energy_star_term_dropped", "(Ss - u) * (Ss + p / (r * (S - u)))", "(Ss - u) * Ss"),
-    ("wave_speed_sign", "double SL = fmin(ul - al, ur - ar);", "double SL = fmin(ul - al, ur + ar);"),
+    ("wave_speed_sign", "SL = fmin(ul - al, ur - ar);", "SL = fmin(ul - al, ur + ar);"),
     ("limiter_picks_larger", "else if (fabs(dy01) < fabs(dy12))", "else if (fabs(dy01) > fabs(dy12))"),
     ("limiter_no_extremum_clip", "if (dy01 * dy12 < 0.0)", "if (dy01 * dy12 < -1e300)"),
     ("face_values_swapped", "*left = y1 - 0.5 * dy;", "*left = y1 + 0.5 * dy;"),

@@ -23,13 +23,14 @@ def test_triangulation_truth_table():
 
 def test_space_and_features():
     s3 = T.Space(3)
-    assert len(s3.all_genomes()) == 6 * 7 * 2 * 2
-    assert s3.variant(s3.default_genome()) == {"tile": (32, 8), "march": 64, "split": 0, "staging": 1}
+    assert len(s3.all_genomes()) == 6 * 7 * 2 * 2 * 2
+    assert s3.variant(s3.default_genome()) == {"tile": (32, 8), "march": 64, "split": 2,
+                                               "staging": 1, "occupancy": 3}
     f = T.features(s3, s3.default_genome(), (512, 512, 512))
     assert f.shape == (T.N_FEATURES,)
     f2 = T.features(T.Space(2), T.Space(2).default_genome(), (2048, 2048))
     assert f2.shape == (T.N_FEATURES,) and not np.array_equal(f, f2)
-    assert len({tuple(T.features(s3, g, (64, 64, 64))) for g in s3.all_genomes()}) == 168
+    assert len({tuple(T.features(s3, g, (64, 64, 64))) for g in s3.all_genomes()}) == 336
 
 
 def test_draw_prefers_high_scores_at_low_temperature():
@@ -73,7 +74,8 @@ def synthetic_cups(space, genome, shape, noise_rng=None):
     nz = shape[2]
     best_march = min(256, max(4, nz // 4))
     march_cost = 0.05 * (math.log2(v["march"]) - math.log2(best_march)) ** 2
-    logt = -23.0 + tile_cost + march_cost + 0.08 * v["split"] + 0.04 * (v["staging"] == 2)
+    logt = (-23.0 + tile_cost + march_cost + 0.08 * (v["split"] == 1) + 0.04 * (v["staging"] == 2)
+            - 0.03 * (v["occupancy"] == 3))
     if noise_rng is not None:
         logt += noise_rng.normal(0, 0.005)
     return math.exp(-logt)
