@@ -48,15 +48,16 @@ def _kernel_digest() -> str:
     return h.hexdigest()[:16]
 
 
-def _traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was taken on
-    the current kernel source; else None."""
+def _ncu_record(field: str, kernel: str):
+    """Per-launch figure (`per_launch_bytes` or `per_launch_warp_instructions`) of `kernel` at
+    512^3 from the committed ncu summary, if it was taken on the current kernel source; else
+    None."""
     try:
-        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+        with open(os.path.join(ROOT, "profiles", "ncu_counters.json")) as f:
             rec = json.load(f)
         if rec.get("kernel_digest") != _kernel_digest():
             return None
-        return rec["per_launch_bytes"].get(kernel)
+        return rec[field].get(kernel)
     except Exception:
         return None
 
@@ -245,7 +246,8 @@ def run_ours(args):
     dom = max(("stage1", "stage2"), key=lambda k: kt[k][0])
     avg_ms = kt[dom][0] / max(kt[dom][1], 1)
     achieved = alg[dom] / (avg_ms * 1e-3) / 1e9
-    traffic = _traffic(dom)
+    traffic = _ncu_record("per_launch_bytes", dom)
+    winst = _ncu_record("per_launch_warp_instructions", dom)
     kernels = {k: {"avg_ms": v[0] / max(v[1], 1), "launches": v[1],
                    "alg_bytes_per_launch": alg.get(k, nv * 4 * ncell)} for k, v in kt.items()}
 
@@ -271,6 +273,19 @@ def run_ours(args):
                "steps": args.e2e_steps,
                "call": "hydro_step_host: pinned host state in, 1 RK step, host state out"}
 
+    # the kernel's real limit: instruction issue (4 warp-instructions per clock per SM)
+    clocks = clk.summary()
+    issue = None
+    if winst is not None:
+        props = torch.cuda.get_device_properties(dev)
+        mhz = clocks.get("sm_mhz") or 2070.0
+        peak = 4.0 * props.multi_processor_count * mhz * 1e6
+        ach = winst / (avg_ms * 1e-3)
+        issue = {"kernel": dom, "achieved": ach, "peak": peak, "unit": "warp-instructions/s",
+                 "frac": ach / peak, "warp_instructions_per_launch": winst,
+                 "source": "ncu smsp__inst_executed.sum (profiles/ncu_counters.json) / live "
+                           "CUDA-event launch time; peak = 4 x SMs x sampled SM clock"}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_cups()
@@ -285,13 +300,15 @@ def run_ours(args):
                        "grid": [n, n, n], "gamma": GAMMA, "cfl": CFL,
                        "blast_radius_cells": RADIUS, "parallelism": f"replicas x{world}",
                        "l2": f"inputs larger than L2 ({5 * 4 * ncell / 2**30:.2f} GiB state vs 129 MB L2); no flush",
-                       "variant": {"tile": [32, 8], "march": 64, "split": "per-stage"}},
+                       "variant": {"tile": [32, 8], "march": 64, "split": "fused dt reduction",
+                                   "staging": "look-ahead", "occupancy": 3}},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": traffic, "kernel": dom,
                          "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"},
             "kernels": kernels,
             "gpu_launches": int(sum(v[1] for v in kt.values())),
-            "clocks": clk.summary(),
+            "clocks": clocks,
+            "issue_roofline": issue,
             "e2e": e2e,
             "cpu_baseline": cpu,
             "sim_time": t_sim,

@@ -240,6 +240,21 @@ int hydro_batch_set_profiling(hydro_batch_t *batch, int32_t on);
 int hydro_batch_kernel_times(hydro_batch_t *batch, double *ms_out, int64_t *launches_out,
                              int32_t n, int32_t reset);
 
+/* ---- The linear-wave example (section 2.3) ---------------------------------------------
+ * f_t = g, g_t = c^2 f_xx on n >= 3 cells of the periodic interval [0, length), dx = length/n,
+ * advanced n_steps times by Eqs. eqLWDiscF and eqLWDiscG:
+ *     f1[i] = f[i] + dt g[i];  g1[i] = g[i] + (c^2 dt/dx^2)(f1[i+1] + f1[i-1] - 2 f1[i]),
+ * with the discrete energy E = sum_i (c^2 ((f1[i+1]-f1[i-1])/(2 dx))^2 + ((g[i]+g1[i])/2)^2)/2 dx
+ * computed in FP64 after every step into energy_out[step] (host, n_steps doubles; may be NULL).
+ * (The paper prints this energy with c^2 inside the square and no 1/2; the form above is the
+ * one its listing computes and the scheme conserves.)  f and g: device arrays of n elements
+ * of precision prec, updated in place.  Workspace: hydro_wave_workspace_bytes() bytes,
+ * 256-byte aligned, caller-owned.  Synchronises `stream`. */
+int hydro_wave_workspace_bytes(int64_t n, int32_t prec, int32_t n_steps, size_t *bytes_out);
+int hydro_wave_run(int32_t prec, int64_t n, double c, double length, double dt, void *f, void *g,
+                   int32_t n_steps, double *energy_out, void *workspace, size_t workspace_bytes,
+                   void *stream);
+
 /* ---- Cost model of the variant tuner: a 3-layer MLP trained on the GPU ---------------------
  * y = W3 tanh(W2 tanh(W1 x + b1) + b2) + b3, input width d, hidden width H, FP32.  All arrays
  * are device memory owned by the caller: params (hydro_mlp_sizes' param_count floats, layout

@@ -35,6 +35,7 @@ UNITS = {
     "batch_f64.cu": ["--fmad=false"],
     "batch_abi.cu": [],
     "mlp.cu": [],
+    "wave.cu": ["--fmad=false"],
 }
 HEADERS = ["hydro_device.cuh", "stage_kernel.cuh", "stage_launch.cuh", "hydro_internal.h",
            "batch_kernel.cuh"]

@@ -1,0 +1,160 @@
+// The paper's linear-wave example (arXiv:1204.4779, section 2.3): f_t = g, g_t = c^2 f_xx on a
+// periodic 1D grid, advanced by Eqs. eqLWDiscF and eqLWDiscG,
+//     f1[i] = f[i] + dt g[i]
+//     g1[i] = g[i] + (c^2 dt / dx^2) (f1[i+1] + f1[i-1] - 2 f1[i]),
+// with the discrete energy
+//     E = sum_i (1/2) (c^2 ((f1[i+1] - f1[i-1]) / (2 dx))^2 + ((g[i] + g1[i]) / 2)^2) dx
+// audited in FP64 after every step (the form of the paper's listing, which the scheme conserves
+// to round-off).
+//
+// One launch per step: a CTA owns a tile of cells, recomputes f1 on its tile plus one halo cell
+// each side from f and g (no second pass over f1), updates g, and reduces its energy terms
+// into one FP64 partial with a fixed tree; a one-CTA kernel sums the partials in fixed order.
+// State ping-pongs between the caller's arrays and two workspace arrays.  FP64 is compiled with
+// --fmad=false (plain IEEE operations in the order of the formulas); FP32 runs the stencil in
+// FP32 and the energy in FP64.
+#include <string.h>
+
+#include "../../include/hydro.h"
+#include "hydro_internal.h"
+
+namespace {
+
+constexpr int kWaveThreads = 256;
+
+template <class T>
+__global__ void __launch_bounds__(kWaveThreads)
+    wave_step_kernel(const T *__restrict__ f, const T *__restrict__ g, T *__restrict__ fo,
+                     T *__restrict__ go, long long n, T dt, T k, double c2, double dx,
+                     double *partial) {
+    __shared__ T s_f1[kWaveThreads + 2];
+    __shared__ double s_e[kWaveThreads];
+    const long long base = (long long)blockIdx.x * kWaveThreads;
+    const long long i = base + threadIdx.x;
+    const bool active = i < n;
+    // f1 on the tile and its two halo cells (periodic)
+    if (active) s_f1[threadIdx.x + 1] = f[i] + dt * g[i];
+    if (threadIdx.x == 0) {
+        const long long l = base == 0 ? n - 1 : base - 1;
+        s_f1[0] = f[l] + dt * g[l];
+    }
+    if (threadIdx.x == kWaveThreads - 1 || i == n - 1) {
+        const long long r = i + 1 >= n ? 0 : i + 1;
+        s_f1[threadIdx.x + 2] = f[r] + dt * g[r];
+    }
+    __syncthreads();
+    double e = 0.0;
+    if (active) {
+        const T fm = s_f1[threadIdx.x], f1 = s_f1[threadIdx.x + 1], fp = s_f1[threadIdx.x + 2];
+        const T g1 = g[i] + k * (fp + fm - T(2) * f1);
+        fo[i] = f1;
+        go[i] = g1;
+        const double dfdx = ((double)fp - (double)fm) / (2.0 * dx);
+        const double gm = ((double)g[i] + (double)g1) / 2.0;
+        e = 0.5 * (c2 * dfdx * dfdx + gm * gm) * dx;
+    }
+    s_e[threadIdx.x] = e;
+    __syncthreads();
+    for (int w = kWaveThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) s_e[threadIdx.x] += s_e[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = s_e[0];
+}
+
+__global__ void __launch_bounds__(kWaveThreads)
+    wave_energy_kernel(const double *partial, int nparts, double *out) {
+    __shared__ double s[kWaveThreads];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += kWaveThreads) acc += partial[i];
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = kWaveThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = s[0];
+}
+
+size_t align_up(size_t x) { return (x + 255) / 256 * 256; }
+
+struct WaveLayout {
+    size_t f_off, g_off, part_off, e_off, total;
+    long long nblocks;
+};
+
+WaveLayout wave_layout(long long n, int prec, int n_steps) {
+    WaveLayout L;
+    const size_t esz = prec == HYDRO_F32 ? 4 : 8;
+    L.nblocks = (n + kWaveThreads - 1) / kWaveThreads;
+    L.f_off = 0;
+    L.g_off = align_up((size_t)n * esz);
+    L.part_off = L.g_off + align_up((size_t)n * esz);
+    L.e_off = L.part_off + align_up(sizeof(double) * (size_t)L.nblocks);
+    L.total = L.e_off + align_up(sizeof(double) * (size_t)(n_steps > 0 ? n_steps : 1));
+    return L;
+}
+
+template <class T>
+int wave_run_t(long long n, double c, double length, double dt, T *f, T *g, int n_steps,
+               double *energy_out, unsigned char *ws, const WaveLayout &L, cudaStream_t st) {
+    T *fa = f, *ga = g;
+    T *fb = reinterpret_cast<T *>(ws + L.f_off), *gb = reinterpret_cast<T *>(ws + L.g_off);
+    double *part = reinterpret_cast<double *>(ws + L.part_off);
+    double *energy = reinterpret_cast<double *>(ws + L.e_off);
+    const double dx = length / (double)n;
+    const T k = T(c * c * dt / (dx * dx));
+    for (int s = 0; s < n_steps; ++s) {
+        wave_step_kernel<T><<<(unsigned)L.nblocks, kWaveThreads, 0, st>>>(fa, ga, fb, gb, n, T(dt), k,
+                                                                          c * c, dx, part);
+        wave_energy_kernel<<<1, kWaveThreads, 0, st>>>(part, (int)L.nblocks, energy + s);
+        T *t = fa;
+        fa = fb;
+        fb = t;
+        t = ga;
+        ga = gb;
+        gb = t;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && fa != f) {  // odd step count: the result is in the workspace
+        e = cudaMemcpyAsync(f, fa, sizeof(T) * (size_t)n, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(g, ga, sizeof(T) * (size_t)n, cudaMemcpyDeviceToDevice, st);
+    }
+    if (e == cudaSuccess && energy_out && n_steps > 0)
+        e = cudaMemcpyAsync(energy_out, energy, sizeof(double) * (size_t)n_steps,
+                            cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? HYDRO_OK : hydro::record_cuda_error(e, "hydro_wave_run");
+}
+
+}  // namespace
+
+extern "C" {
+
+int hydro_wave_workspace_bytes(int64_t n, int32_t prec, int32_t n_steps, size_t *bytes_out) {
+    if (!bytes_out || n < 3 || n >= (1LL << 40) || n_steps < 0) return HYDRO_EINVAL;
+    if (prec != HYDRO_F32 && prec != HYDRO_F64) return HYDRO_EINVAL;
+    *bytes_out = wave_layout(n, prec, n_steps).total;
+    return HYDRO_OK;
+}
+
+int hydro_wave_run(int32_t prec, int64_t n, double c, double length, double dt, void *f, void *g,
+                   int32_t n_steps, double *energy_out, void *workspace, size_t workspace_bytes,
+                   void *stream) {
+    if (!f || !g || !workspace || n < 3 || n_steps < 0) return HYDRO_EINVAL;
+    if (prec != HYDRO_F32 && prec != HYDRO_F64) return HYDRO_EINVAL;
+    if (!(c > 0.0) || !(length > 0.0) || !(dt > 0.0) || ((uintptr_t)workspace) % 256)
+        return HYDRO_EINVAL;
+    const WaveLayout L = wave_layout(n, prec, n_steps);
+    if (workspace_bytes < L.total || L.nblocks >= (1LL << 31)) return HYDRO_EINVAL;
+    unsigned char *ws = static_cast<unsigned char *>(workspace);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (prec == HYDRO_F32)
+        return wave_run_t<float>(n, c, length, dt, static_cast<float *>(f), static_cast<float *>(g),
+                                 n_steps, energy_out, ws, L, st);
+    return wave_run_t<double>(n, c, length, dt, static_cast<double *>(f), static_cast<double *>(g),
+                              n_steps, energy_out, ws, L, st);
+}
+
+}  // extern "C"

@@ -33,6 +33,7 @@ EXPORTS = (
     "hydro_batch_offsets", "hydro_batch_set_stream", "hydro_batch_step", "hydro_batch_totals",
     "hydro_batch_set_profiling", "hydro_batch_kernel_times",
     "hydro_mlp_sizes", "hydro_mlp_forward", "hydro_mlp_gradient", "hydro_mlp_adam", "hydro_mlp_train",
+    "hydro_wave_workspace_bytes", "hydro_wave_run",
 )
 
 
@@ -114,6 +115,9 @@ def load_library(path: str = LIB_PATH, build_if_missing: bool = True):
             "hydro_batch_set_profiling": ([vp, i32], ctypes.c_int),
             "hydro_batch_kernel_times": ([vp, P(dbl), P(i64), i32, i32], ctypes.c_int),
             "hydro_mlp_sizes": ([i32, i32, i64, P(i64), P(ctypes.c_size_t)], ctypes.c_int),
+            "hydro_wave_workspace_bytes": ([i64, i32, i32, P(ctypes.c_size_t)], ctypes.c_int),
+            "hydro_wave_run": ([i32, i64, dbl, dbl, dbl, vp, vp, i32, P(dbl), vp, ctypes.c_size_t, vp],
+                               ctypes.c_int),
             "hydro_mlp_forward": ([vp, i32, i32, vp, i64, vp, vp, vp], ctypes.c_int),
             "hydro_mlp_gradient": ([vp, i32, i32, vp, vp, i64, vp, vp, vp, vp], ctypes.c_int),
             "hydro_mlp_adam": ([vp, vp, vp, vp, i64, i32, ctypes.c_float, ctypes.c_float,
@@ -419,3 +423,21 @@ class BatchSolver:
         _check(self.lib.hydro_batch_kernel_times(self.ctx, ms, n, 3, 1 if reset else 0),
                "hydro_batch_kernel_times")
         return {k: (ms[i], n[i]) for i, k in enumerate(("cfl", "stage1", "stage2"))}
+
+
+def wave_run(f: torch.Tensor, g: torch.Tensor, c: float, length: float, dt: float, n_steps: int):
+    """The paper's linear-wave example (hydro_wave_run): advance f, g (1D device tensors, float32
+    or float64) in place by n_steps steps; returns the FP64 energy after each step."""
+    lib = load_library()
+    if f.shape != g.shape or f.dim() != 1 or f.dtype != g.dtype:
+        raise ValueError("f and g must be 1D tensors of one shape and dtype")
+    n = f.numel()
+    nbytes = ctypes.c_size_t()
+    _check(lib.hydro_wave_workspace_bytes(n, _prec(f.dtype), int(n_steps), ctypes.byref(nbytes)),
+           "hydro_wave_workspace_bytes")
+    ws = torch.empty(int(nbytes.value), dtype=torch.uint8, device=f.device)
+    energy = (ctypes.c_double * max(int(n_steps), 1))()
+    _check(lib.hydro_wave_run(_prec(f.dtype), n, float(c), float(length), float(dt), f.data_ptr(),
+                              g.data_ptr(), int(n_steps), energy, ws.data_ptr(), int(nbytes.value),
+                              _stream_ptr(f.device)), "hydro_wave_run")
+    return list(energy)[:int(n_steps)]
