@@ -32,23 +32,59 @@ def test_fp64_matches_oracle(n):
 
 
 def test_energy_conserved_at_large_size():
+    """At N = 2^22 the centred difference in the energy, (f1[i+1] - f1[i-1]) / (2 dx), cancels
+    values of order one that differ by O(dx), so each step's FP64 rounding is amplified by
+    about 1/(N dx) and the energy wanders at the 1e-12 level even in the oracle.  The GPU's
+    wander must stay within a small factor of the oracle's own on the same data."""
     from paper_1204_4779_gb300 import hydro
     n = 1 << 22
-    x = torch.arange(n, dtype=torch.float64, device="cuda") * (2 * math.pi / n)
-    f, g = torch.sin(x), torch.cos(3 * x)
+    x = np.arange(n) * (2 * math.pi / n)
+    f0, g0 = np.sin(x), np.cos(3 * x)
     dt = (2 * math.pi / n) / C
+    _, _, Eo = W.run(f0, g0, C, 2 * math.pi, dt, 200)
+    f, g = torch.from_numpy(f0).cuda(), torch.from_numpy(g0).cuda()
     E = np.array(hydro.wave_run(f, g, C, 2 * math.pi, dt, 200))
-    assert (E.max() - E.min()) / E.mean() < 1e-12
+    drift_o = (Eo.max() - Eo.min()) / Eo.mean()
+    drift = (E.max() - E.min()) / E.mean()
+    assert drift_o < 1e-11
+    assert drift <= 10 * drift_o, (drift, drift_o)
+    assert np.max(np.abs(E - Eo)) <= 1e-11 * Eo.mean()
+
+
+def _fp32_steps(f, g, dt, k, c2, dx, steps):
+    """The FP32 form of the two update formulas in single precision, evaluated in the kernel's
+    order (no fused multiply-add), with the energy of each step in FP64."""
+    f, g = f.astype(np.float32), g.astype(np.float32)
+    dt32, k32, two = np.float32(dt), np.float32(k), np.float32(2)
+    E = []
+    for _ in range(steps):
+        f1 = f + dt32 * g
+        fp, fm = np.roll(f1, -1), np.roll(f1, 1)
+        g1 = g + k32 * (fp + fm - two * f1)
+        dfdx = (fp.astype(np.float64) - fm.astype(np.float64)) / (2.0 * dx)
+        gm = (g.astype(np.float64) + g1.astype(np.float64)) / 2.0
+        E.append(float(np.sum(0.5 * (c2 * dfdx * dfdx + gm * gm) * dx)))
+        f, g = f1, g1
+    return f, g, np.array(E)
 
 
 def test_fp32_energy_and_state():
+    """FP32 against the FP64 oracle: storing f (of order one) in FP32 rounds each step's
+    increment dt g (of order 2 pi / N) with relative error about eps32 N / (2 pi), 1e-5 at
+    N = 1024, and the energy error is of that order (a float32 evaluation of the same steps
+    gives 3.6e-5).  The kernel's own rounding is checked exactly against that evaluation."""
     from paper_1204_4779_gb300 import hydro
     n = 1024
     f0, g0 = W.initial(n)
-    dt = (2 * math.pi / n) / C
+    dx = 2 * math.pi / n
+    dt = dx / C
     fo, go, Eo = W.run(f0, g0, C, 2 * math.pi, dt, 200)
     f = torch.from_numpy(f0).float().cuda()
     g = torch.from_numpy(g0).float().cuda()
     E = np.array(hydro.wave_run(f, g, C, 2 * math.pi, dt, 200))
     assert np.max(np.abs(f.double().cpu().numpy() - fo)) <= 1e-4
-    assert np.max(np.abs(E - Eo)) / Eo.mean() <= 1e-5
+    assert np.max(np.abs(E - Eo)) / Eo.mean() <= 1e-4
+    fe, ge, Ee = _fp32_steps(f0, g0, dt, C * C * dt / (dx * dx), C * C, dx, 200)
+    assert np.array_equal(f.cpu().numpy(), fe)
+    assert np.array_equal(g.cpu().numpy(), ge)
+    assert np.max(np.abs(E - Ee)) <= 1e-13 * Ee.mean()
