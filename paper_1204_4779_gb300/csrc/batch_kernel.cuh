@@ -106,8 +106,7 @@ __global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY>::value))
 #pragma unroll
             for (int k = 0; k < NV; ++k) u[k] = __ldg(A.uin[k] + i);
             prim_of_cons<T, 2>(u, v, G);
-#pragma unroll
-            for (int k = 0; k < NV; ++k) sV[k * PL + own_s] = v[k];
+            Cells<T, NV>::put(sV, PL, own_s, v);
         }
 #pragma unroll
         for (int j = 0; j < HPT; ++j) {
@@ -119,8 +118,7 @@ __global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY>::value))
 #pragma unroll
                 for (int k = 0; k < NV; ++k) u[k] = __ldg(A.uin[k] + i);
                 prim_of_cons<T, 2>(u, v, G);
-#pragma unroll
-                for (int k = 0; k < NV; ++k) sV[k * PL + h_ly[j] * HX + h_lx[j]] = v[k];
+                Cells<T, NV>::put(sV, PL, h_ly[j] * HX + h_lx[j], v);
             }
         }
         T base[NV];
@@ -140,11 +138,15 @@ __global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY>::value))
         if (active) {
             const int fxl = ty * (BX + 1) + tx;
             const int fyb = NFX + ty * BX + tx;
-            T un[NV];
+            T un[NV], fw[NV], fe[NV], fs[NV], fn[NV];
+            Cells<T, NV>::get(sF, NF, fxl, fw);
+            Cells<T, NV>::get(sF, NF, fxl + 1, fe);
+            Cells<T, NV>::get(sF, NF, fyb, fs);
+            Cells<T, NV>::get(sF, NF, fyb + BX, fn);
 #pragma unroll
             for (int k = 0; k < NV; ++k) {
-                T sum = cx * (sF[k * NF + fxl] - sF[k * NF + fxl + 1]);
-                sum = sum + cy * (sF[k * NF + fyb] - sF[k * NF + fyb + BX]);
+                T sum = cx * (fw[k] - fe[k]);
+                sum = sum + cy * (fs[k] - fn[k]);
                 un[k] = base[k] + sum;
             }
             const long long i = off + (long long)y * nx + x;

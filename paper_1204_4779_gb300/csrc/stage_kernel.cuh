@@ -51,10 +51,12 @@ template <class T, int D, int BX, int BY> struct StageShape {
     static constexpr int NT = BX * BY;
     static constexpr int HX = BX + 4;
     static constexpr int HY = (D >= 2) ? BY + 4 : 1;
-    static constexpr int PL = HY * HX;  // shared plane of one field
+    // shared plane of one field, and the flux plane, in cells; multiples of four so that the
+    // 16-byte records of Cells stay aligned from plane to plane
+    static constexpr int PL = (HY * HX + 3) / 4 * 4;
     static constexpr int NFX = (BX + 1) * BY;
     static constexpr int NFY = (D >= 2) ? BX * (BY + 1) : 0;
-    static constexpr int NF = NFX + NFY;
+    static constexpr int NF = (NFX + NFY + 3) / 4 * 4;
     static constexpr int NH = (D >= 2) ? 4 * BY + 4 * BX : 4;
     static constexpr int HPT = (NH + NT - 1) / NT;  // halo cells per thread
     static constexpr int FPT = (D >= 2) ? 3 : 2;  // in-plane face rounds per thread
@@ -62,46 +64,95 @@ template <class T, int D, int BX, int BY> struct StageShape {
     static constexpr size_t smem_bytes = sizeof(T) * (size_t)(2 * NV * PL + 2 * NV * NF + 2 * (NT / 32));
 };
 
+// Shared-memory records of NV values per cell (primitive states, face fluxes) in arrays of
+// `stride` cells.  Generic form: one array per value.  FP32 with four or five values: the
+// first four are one float4 per cell and the fifth an array after them; FP64: pairs of
+// doubles as double2 plus the odd fifth.  One 128-bit access then moves four (two) values.
+// The base must be 16-byte aligned and `stride` a multiple of four.
+template <class T, int NV> struct Cells {
+    __device__ static __forceinline__ void put(T *b, int stride, int i, const T (&v)[NV]) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) b[k * stride + i] = v[k];
+    }
+    __device__ static __forceinline__ void get(const T *b, int stride, int i, T (&v)[NV]) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) v[k] = b[k * stride + i];
+    }
+};
+template <int NV> struct Cells4f {
+    static_assert(NV == 4 || NV == 5, "float4 records hold four or five values");
+    __device__ static __forceinline__ void put(float *b, int stride, int i, const float (&v)[NV]) {
+        reinterpret_cast<float4 *>(b)[i] = make_float4(v[0], v[1], v[2], v[3]);
+        if constexpr (NV == 5) b[4 * stride + i] = v[4];
+    }
+    __device__ static __forceinline__ void get(const float *b, int stride, int i, float (&v)[NV]) {
+        const float4 q = reinterpret_cast<const float4 *>(b)[i];
+        v[0] = q.x, v[1] = q.y, v[2] = q.z, v[3] = q.w;
+        if constexpr (NV == 5) v[4] = b[4 * stride + i];
+    }
+};
+template <> struct Cells<float, 4> : Cells4f<4> {};
+template <> struct Cells<float, 5> : Cells4f<5> {};
+template <int NV> struct Cells2d {
+    static_assert(NV == 4 || NV == 5, "double2 records hold four or five values");
+    __device__ static __forceinline__ void put(double *b, int stride, int i, const double (&v)[NV]) {
+        reinterpret_cast<double2 *>(b)[i] = make_double2(v[0], v[1]);
+        reinterpret_cast<double2 *>(b + 2 * stride)[i] = make_double2(v[2], v[3]);
+        if constexpr (NV == 5) b[4 * stride + i] = v[4];
+    }
+    __device__ static __forceinline__ void get(const double *b, int stride, int i, double (&v)[NV]) {
+        const double2 p = reinterpret_cast<const double2 *>(b)[i];
+        const double2 q = reinterpret_cast<const double2 *>(b + 2 * stride)[i];
+        v[0] = p.x, v[1] = p.y, v[2] = q.x, v[3] = q.y;
+        if constexpr (NV == 5) v[4] = b[4 * stride + i];
+    }
+};
+template <> struct Cells<double, 4> : Cells2d<4> {};
+template <> struct Cells<double, 5> : Cells2d<5> {};
+
 // Flux of one in-plane face from the staged primitive plane.  `o`: shared index of the
 // first of the four cells q0..q3 along the normal, `s`: their stride, `a`: the normal axis
-// (0 or 1).  Face between q1 and q2.  Writes the flux in axis order to sF (field stride NF).
+// (0 or 1).  Face between q1 and q2.  Writes the flux in axis order to record f of sF.
 template <class T, int D, int PL, int NF>
 __device__ __forceinline__ void inplane_face(const T *__restrict__ sV, T *__restrict__ sF, int o,
                                              int s, int a, int f, const Gas<T> &G,
                                              int order = 2, int riemann = 0) {
     constexpr int NV = D + 2;
-    // field of the normal velocity, then tangential ones in increasing axis order
-    int fld[D];
-    fld[0] = 1 + a;
-    if constexpr (D >= 2) fld[1] = 2 - a;
-    if constexpr (D == 3) fld[2] = 3;
-    T L[NV], R[NV];  // (rho, normal-first velocities, p)
+    using C = Cells<T, NV>;
+    T q1[NV], q2[NV], L[NV], R[NV];  // axis order (rho, v_x, [v_y, [v_z]], p)
+    C::get(sV, PL, o + s, q1);
+    C::get(sV, PL, o + 2 * s, q2);
+    if (order == 2) {
+        T q0[NV], q3[NV];
+        C::get(sV, PL, o, q0);
+        C::get(sV, PL, o + 3 * s, q3);
 #pragma unroll
-    for (int k = 0; k < NV; ++k) {
-        const int field = (k == 0) ? 0 : (k == NV - 1 ? NV - 1 : fld[k - 1]);
-        const T *q = sV + field * PL + o;
-        const T q1 = q[s], q2 = q[2 * s];
-        if (order == 2) {
-            const T q0 = q[0], q3 = q[3 * s];
-            const T d01 = q1 - q0, d12 = q2 - q1, d23 = q3 - q2;
-            L[k] = q1 + T(0.5) * minbee(d01, d12);
-            R[k] = q2 - T(0.5) * minbee(d12, d23);
-        } else {
-            L[k] = q1;
-            R[k] = q2;
+        for (int k = 0; k < NV; ++k) {
+            const T d01 = q1[k] - q0[k], d12 = q2[k] - q1[k], d23 = q3[k] - q2[k];
+            L[k] = q1[k] + T(0.5) * minbee(d01, d12);
+            R[k] = q2[k] - T(0.5) * minbee(d12, d23);
         }
+    } else {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) L[k] = q1[k], R[k] = q2[k];
     }
+    // velocities normal first, then the tangential ones in increasing axis order
     T vl[D], vr[D], F[NV];
-#pragma unroll
-    for (int b = 0; b < D; ++b) {
-        vl[b] = L[1 + b];
-        vr[b] = R[1 + b];
+    vl[0] = (D >= 2 && a) ? L[2] : L[1];
+    vr[0] = (D >= 2 && a) ? R[2] : R[1];
+    if constexpr (D >= 2) {
+        vl[1] = a ? L[1] : L[2];
+        vr[1] = a ? R[1] : R[2];
     }
+    if constexpr (D == 3) vl[2] = L[3], vr[2] = R[3];
     hllc<T, D, false>(L[0], vl, L[NV - 1], R[0], vr, R[NV - 1], G, F, riemann);
-    sF[f] = F[0];
-#pragma unroll
-    for (int b = 0; b < D; ++b) sF[fld[b] * NF + f] = F[1 + b];
-    sF[(NV - 1) * NF + f] = F[NV - 1];
+    T Fa[NV];  // back to axis order
+    Fa[0] = F[0];
+    Fa[1] = (D >= 2 && a) ? F[2] : F[1];
+    if constexpr (D >= 2) Fa[2] = a ? F[1] : F[2];
+    if constexpr (D == 3) Fa[3] = F[3];
+    Fa[NV - 1] = F[NV - 1];
+    C::put(sF, NF, f, Fa);
 }
 
 // Flux of the z-face between a column's cells z (lower) and z+1 (upper) from their primitive
@@ -265,15 +316,13 @@ __global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY, OCC>::value))
     // V of one plane into shared memory: the own cell from registers, the halo recovered
     // from its prefetched conserved values
     auto stage_plane = [&](T *sV, const T (&Vown)[NV], T (&ph)[HPT][NV]) {
-#pragma unroll
-        for (int k = 0; k < NV; ++k) sV[k * PL + own_s] = Vown[k];
+        Cells<T, NV>::put(sV, PL, own_s, Vown);
 #pragma unroll
         for (int j = 0; j < HPT; ++j) {
             if (h_ok[j]) {
                 T vh[NV];
                 prim_of_cons<T, D>(ph[j], vh, G);
-#pragma unroll
-                for (int k = 0; k < NV; ++k) sV[k * PL + h_s[j]] = vh[k];
+                Cells<T, NV>::put(sV, PL, h_s[j], vh);
             }
         }
     };
@@ -375,11 +424,17 @@ __global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY, OCC>::value))
         if (active) {
             const int fxl = ty * (BX + 1) + tx;
             const int fyb = NFX + ty * BX + tx;
-            T un[NV];
+            T un[NV], fw[NV], fe[NV], fs[NV], fn[NV];
+            Cells<T, NV>::get(sF, NF, fxl, fw);
+            Cells<T, NV>::get(sF, NF, fxl + 1, fe);
+            if constexpr (D >= 2) {
+                Cells<T, NV>::get(sF, NF, fyb, fs);
+                Cells<T, NV>::get(sF, NF, fyb + BX, fn);
+            }
 #pragma unroll
             for (int k = 0; k < NV; ++k) {
-                T sum = cx * (sF[k * NF + fxl] - sF[k * NF + fxl + 1]);
-                if constexpr (D >= 2) sum = sum + cy * (sF[k * NF + fyb] - sF[k * NF + fyb + BX]);
+                T sum = cx * (fw[k] - fe[k]);
+                if constexpr (D >= 2) sum = sum + cy * (fs[k] - fn[k]);
                 if constexpr (D == 3) {
                     // z fluxes are normal-first: (mass, m_z, m_x, m_y, E)
                     const int kk = (k == 0 || k == NV - 1) ? k : (k == 3 ? 1 : k + 1);
