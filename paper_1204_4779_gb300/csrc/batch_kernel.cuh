@@ -143,12 +143,7 @@ __global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY>::value))
             Cells<T, NV>::get(sF, NF, fxl + 1, fe);
             Cells<T, NV>::get(sF, NF, fyb, fs);
             Cells<T, NV>::get(sF, NF, fyb + BX, fn);
-#pragma unroll
-            for (int k = 0; k < NV; ++k) {
-                T sum = cx * (fw[k] - fe[k]);
-                sum = sum + cy * (fs[k] - fn[k]);
-                un[k] = base[k] + sum;
-            }
+            add_fluxes<T, 2>(base, cx, fw, fe, cy, fs, fn, T(0), fw, fw, un);  // no z term in 2D
             const long long i = off + (long long)y * nx + x;
 #pragma unroll
             for (int k = 0; k < NV; ++k) A.uout[k][i] = un[k];

@@ -66,6 +66,42 @@ template <> struct Arith<float> {
     }
 };
 
+// Packed FP32 pairs: Blackwell's f32x2 add/sub/mul/fma apply one operation to two FP32 values
+// held in a 64-bit register pair, so one issued instruction does the work of two.  Each lane
+// rounds as the scalar instruction would (round to nearest, flush-to-zero like the FP32 units).
+struct F2 {
+    unsigned long long r;
+};
+__device__ __forceinline__ F2 f2_pack(float a, float b) {
+    F2 v;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(v.r) : "f"(a), "f"(b));
+    return v;
+}
+__device__ __forceinline__ void f2_unpack(F2 v, float &a, float &b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v.r));
+}
+__device__ __forceinline__ F2 f2_add(F2 a, F2 b) {
+    F2 d;
+    asm("add.rn.ftz.f32x2 %0, %1, %2;" : "=l"(d.r) : "l"(a.r), "l"(b.r));
+    return d;
+}
+__device__ __forceinline__ F2 f2_sub(F2 a, F2 b) {
+    F2 d;
+    asm("sub.rn.ftz.f32x2 %0, %1, %2;" : "=l"(d.r) : "l"(a.r), "l"(b.r));
+    return d;
+}
+__device__ __forceinline__ F2 f2_mul(F2 a, F2 b) {
+    F2 d;
+    asm("mul.rn.ftz.f32x2 %0, %1, %2;" : "=l"(d.r) : "l"(a.r), "l"(b.r));
+    return d;
+}
+// a * b + c, one rounding per lane
+__device__ __forceinline__ F2 f2_fma(F2 a, F2 b, F2 c) {
+    F2 d;
+    asm("fma.rn.ftz.f32x2 %0, %1, %2, %3;" : "=l"(d.r) : "l"(a.r), "l"(b.r), "l"(c.r));
+    return d;
+}
+
 template <class T> struct Gas {
     T g;        // gamma
     T gm1;      // gamma - 1

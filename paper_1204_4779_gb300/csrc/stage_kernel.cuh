@@ -110,6 +110,118 @@ template <int NV> struct Cells2d {
 template <> struct Cells<double, 4> : Cells2d<4> {};
 template <> struct Cells<double, 5> : Cells2d<5> {};
 
+// FP32 values are processed in pairs (k, k+1) with f32x2 instructions, the last value alone
+// when NV is odd; FP64 (and anything else) value by value.  Either way each value sees the
+// same operations in the same order.
+template <class T, int NV> struct Pairs {
+    static constexpr int n = std::is_same<T, float>::value ? NV / 2 : 0;  // packed pairs
+    static constexpr int first_scalar = 2 * n;
+};
+
+// MinBee slopes d = minbee(c - m, p - c) of three consecutive cells, value by value (all zero
+// for first-order reconstruction).
+template <class T, int NV>
+__device__ __forceinline__ void minbee_slopes(const T (&m)[NV], const T (&c)[NV], const T (&p)[NV],
+                                              bool order2, T (&d)[NV]) {
+    using P = Pairs<T, NV>;
+    if (!order2) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) d[k] = T(0);
+        return;
+    }
+    if constexpr (P::n > 0) {
+#pragma unroll
+        for (int j = 0; j < P::n; ++j) {
+            const int k = 2 * j;
+            const F2 C = f2_pack(c[k], c[k + 1]);
+            float a0, a1, b0, b1;
+            f2_unpack(f2_sub(C, f2_pack(m[k], m[k + 1])), a0, a1);
+            f2_unpack(f2_sub(f2_pack(p[k], p[k + 1]), C), b0, b1);
+            d[k] = minbee(a0, b0);
+            d[k + 1] = minbee(a1, b1);
+        }
+    }
+#pragma unroll
+    for (int k = P::first_scalar; k < NV; ++k) d[k] = minbee(c[k] - m[k], p[k] - c[k]);
+}
+
+// Face states from cell values and slopes: out = v + s * d / 2 (s = +1: the cell's upper face,
+// -1: its lower face).
+template <class T, int NV>
+__device__ __forceinline__ void half_step(const T (&v)[NV], const T (&d)[NV], T s, T (&out)[NV]) {
+    using P = Pairs<T, NV>;
+    if constexpr (P::n > 0) {
+        const F2 h = f2_pack(0.5f * s, 0.5f * s);
+#pragma unroll
+        for (int j = 0; j < P::n; ++j) {
+            const int k = 2 * j;
+            f2_unpack(f2_fma(h, f2_pack(d[k], d[k + 1]), f2_pack(v[k], v[k + 1])), out[k], out[k + 1]);
+        }
+    }
+#pragma unroll
+    for (int k = P::first_scalar; k < NV; ++k)
+        out[k] = (s > T(0)) ? v[k] + T(0.5) * d[k] : v[k] - T(0.5) * d[k];
+}
+
+// MinBee faces of four consecutive cells q0..q3 along a normal: L = upper face of q1,
+// R = lower face of q2 (the two sides of the face between q1 and q2).
+template <class T, int NV>
+__device__ __forceinline__ void minbee_face_pair(const T (&q0)[NV], const T (&q1)[NV],
+                                                 const T (&q2)[NV], const T (&q3)[NV], T (&L)[NV],
+                                                 T (&R)[NV]) {
+    using P = Pairs<T, NV>;
+    if constexpr (P::n > 0) {
+        const F2 h = f2_pack(0.5f, 0.5f), mh = f2_pack(-0.5f, -0.5f);
+#pragma unroll
+        for (int j = 0; j < P::n; ++j) {
+            const int k = 2 * j;
+            const F2 Q1 = f2_pack(q1[k], q1[k + 1]), Q2 = f2_pack(q2[k], q2[k + 1]);
+            float a0, a1, b0, b1, c0, c1;
+            f2_unpack(f2_sub(Q1, f2_pack(q0[k], q0[k + 1])), a0, a1);
+            f2_unpack(f2_sub(Q2, Q1), b0, b1);
+            f2_unpack(f2_sub(f2_pack(q3[k], q3[k + 1]), Q2), c0, c1);
+            f2_unpack(f2_fma(h, f2_pack(minbee(a0, b0), minbee(a1, b1)), Q1), L[k], L[k + 1]);
+            f2_unpack(f2_fma(mh, f2_pack(minbee(b0, c0), minbee(b1, c1)), Q2), R[k], R[k + 1]);
+        }
+    }
+#pragma unroll
+    for (int k = P::first_scalar; k < NV; ++k) {
+        const T d01 = q1[k] - q0[k], d12 = q2[k] - q1[k], d23 = q3[k] - q2[k];
+        L[k] = q1[k] + T(0.5) * minbee(d01, d12);
+        R[k] = q2[k] - T(0.5) * minbee(d12, d23);
+    }
+}
+
+// AddFlux of one cell (Eq. eqAddFlux): un = base + cx (fw - fe) [+ cy (fs - fn) [+ cz (zm - zp)]],
+// the fluxes of its low and high faces per axis, all in axis order.
+template <class T, int D>
+__device__ __forceinline__ void add_fluxes(const T (&base)[D + 2], T cx, const T (&fw)[D + 2],
+                                           const T (&fe)[D + 2], T cy, const T (&fs)[D + 2],
+                                           const T (&fn)[D + 2], T cz, const T (&zm)[D + 2],
+                                           const T (&zp)[D + 2], T (&un)[D + 2]) {
+    constexpr int NV = D + 2;
+    using P = Pairs<T, NV>;
+    if constexpr (P::n > 0) {
+        const F2 CX = f2_pack(cx, cx), CY = f2_pack(cy, cy), CZ = f2_pack(cz, cz);
+#pragma unroll
+        for (int j = 0; j < P::n; ++j) {
+            const int k = 2 * j;
+            auto pk = [k](const float (&a)[NV]) { return f2_pack(a[k], a[k + 1]); };
+            F2 sum = f2_mul(CX, f2_sub(pk(fw), pk(fe)));
+            if constexpr (D >= 2) sum = f2_fma(CY, f2_sub(pk(fs), pk(fn)), sum);
+            if constexpr (D == 3) sum = f2_fma(CZ, f2_sub(pk(zm), pk(zp)), sum);
+            f2_unpack(f2_add(pk(base), sum), un[k], un[k + 1]);
+        }
+    }
+#pragma unroll
+    for (int k = P::first_scalar; k < NV; ++k) {
+        T sum = cx * (fw[k] - fe[k]);
+        if constexpr (D >= 2) sum = sum + cy * (fs[k] - fn[k]);
+        if constexpr (D == 3) sum = sum + cz * (zm[k] - zp[k]);
+        un[k] = base[k] + sum;
+    }
+}
+
 // Flux of one in-plane face from the staged primitive plane.  `o`: shared index of the
 // first of the four cells q0..q3 along the normal, `s`: their stride, `a`: the normal axis
 // (0 or 1).  Face between q1 and q2.  Writes the flux in axis order to record f of sF.
@@ -126,12 +238,7 @@ __device__ __forceinline__ void inplane_face(const T *__restrict__ sV, T *__rest
         T q0[NV], q3[NV];
         C::get(sV, PL, o, q0);
         C::get(sV, PL, o + 3 * s, q3);
-#pragma unroll
-        for (int k = 0; k < NV; ++k) {
-            const T d01 = q1[k] - q0[k], d12 = q2[k] - q1[k], d23 = q3[k] - q2[k];
-            L[k] = q1[k] + T(0.5) * minbee(d01, d12);
-            R[k] = q2[k] - T(0.5) * minbee(d12, d23);
-        }
+        minbee_face_pair<T, NV>(q0, q1, q2, q3, L, R);
     } else {
 #pragma unroll
         for (int k = 0; k < NV; ++k) L[k] = q1[k], R[k] = q2[k];
@@ -162,11 +269,8 @@ __device__ __forceinline__ void fz_face(const T (&Vlo)[5], const T (&dlo)[5], co
                                         const T (&dhi)[5], const Gas<T> &G, T (&F)[5],
                                         int riemann = 0) {
     T L[5], R[5];
-#pragma unroll
-    for (int k = 0; k < 5; ++k) {
-        L[k] = Vlo[k] + T(0.5) * dlo[k];
-        R[k] = Vhi[k] - T(0.5) * dhi[k];
-    }
+    half_step<T, 5>(Vlo, dlo, T(1), L);
+    half_step<T, 5>(Vhi, dhi, T(-1), R);
     const T vl[3] = {L[3], L[1], L[2]};
     const T vr[3] = {R[3], R[1], R[2]};
     hllc<T, 3, true>(L[0], vl, L[4], R[0], vr, R[4], G, F, riemann);
@@ -343,11 +447,8 @@ __global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY, OCC>::value))
         prim_of_cons<T, D>(u, Vc, G);
         load_u(u, remap(zb + 1, nz, pz), own_off);
         prim_of_cons<T, D>(u, Vn, G);
-#pragma unroll
-        for (int k = 0; k < NV; ++k) {
-            dzm[k] = order2 ? minbee(Vm1[k] - Vm2[k], Vc[k] - Vm1[k]) : T(0);
-            dzc[k] = order2 ? minbee(Vc[k] - Vm1[k], Vn[k] - Vc[k]) : T(0);
-        }
+        minbee_slopes<T, NV>(Vm2, Vm1, Vc, order2, dzm);
+        minbee_slopes<T, NV>(Vm1, Vc, Vn, order2, dzc);
         fz_face(Vm1, dzm, Vc, dzc, G, Fzm, A.riemann);
         if constexpr (PF == 1) load_u(pown, remap(zb + 2, nz, pz), own_off);
     } else {
@@ -401,8 +502,7 @@ __global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY, OCC>::value))
         // z-face above this column
         T Fzp[NV], dzn[NV];
         if constexpr (D == 3) {
-#pragma unroll
-            for (int k = 0; k < NV; ++k) dzn[k] = order2 ? minbee(Vn[k] - Vc[k], Vnn[k] - Vn[k]) : T(0);
+            minbee_slopes<T, NV>(Vc, Vn, Vnn, order2, dzn);
             fz_face(Vc, dzc, Vn, dzn, G, Fzp, A.riemann);
             // stage plane z+1 into the other buffer, prefetch the halo of plane z+2
             if (z + 1 < ze) {
@@ -431,17 +531,14 @@ __global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY, OCC>::value))
                 Cells<T, NV>::get(sF, NF, fyb, fs);
                 Cells<T, NV>::get(sF, NF, fyb + BX, fn);
             }
+            T zm[NV], zp[NV];  // z fluxes in axis order (they come normal-first: mass, m_z, m_x, m_y, E)
 #pragma unroll
             for (int k = 0; k < NV; ++k) {
-                T sum = cx * (fw[k] - fe[k]);
-                if constexpr (D >= 2) sum = sum + cy * (fs[k] - fn[k]);
-                if constexpr (D == 3) {
-                    // z fluxes are normal-first: (mass, m_z, m_x, m_y, E)
-                    const int kk = (k == 0 || k == NV - 1) ? k : (k == 3 ? 1 : k + 1);
-                    sum = sum + cz * (Fzm[kk] - Fzp[kk]);
-                }
-                un[k] = base[k] + sum;
+                const int kk = (D < 3 || k == 0 || k == NV - 1) ? k : (k == 3 ? 1 : k + 1);
+                zm[k] = (D == 3) ? Fzm[kk] : T(0);
+                zp[k] = (D == 3) ? Fzp[kk] : T(0);
             }
+            add_fluxes<T, D>(base, cx, fw, fe, cy, fs, fn, cz, zm, zp, un);
             const int i = ((D == 3) ? z * nxy : 0) + y * nx + x;
 #pragma unroll
             for (int k = 0; k < NV; ++k) A.uout[k][i] = un[k];
