@@ -49,6 +49,43 @@ def build(force: bool = False, src: str = _SRC, out: str = _LIB) -> str:
     return out
 
 
+_OPC_SRC = os.path.join(_HERE, "opcount.cpp")
+_OPC_LIB = os.path.join(_HERE, "libhydro_oracle_opcount.so")
+OP_KINDS = ("add", "mul", "div", "sqrt", "cmp", "minmax", "abs", "neg")
+
+
+def build_opcount(force: bool = False, out: str = _OPC_LIB) -> str:
+    """Compile the operation-counting build (opcount.cpp: hydro_oracle.c as C++ with a counting
+    number type in place of double), single-threaded."""
+    newest = max(os.path.getmtime(_OPC_SRC), os.path.getmtime(_SRC))
+    if not force and os.path.exists(out) and os.path.getmtime(out) >= newest:
+        return out
+    tmp = out + f".tmp{os.getpid()}"
+    subprocess.run(["g++", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c++17",
+                    "-Wno-unknown-pragmas", "-shared", "-fPIC", "-o", tmp, _OPC_SRC, "-lm"],
+                   check=True, capture_output=True, text=True)
+    os.replace(tmp, out)
+    return out
+
+
+@contextlib.contextmanager
+def counting_ops():
+    """Route every oracle call through the counting build.  Yields `counts()`, which returns the
+    floating-point operations performed since entry, by kind (OP_KINDS), as a dict."""
+    path = build_opcount()
+    raw = ctypes.CDLL(path)
+    n = raw.oracle_opcount_kinds()
+    buf = (ctypes.c_ulonglong * n)()
+
+    def counts():
+        raw.oracle_opcount_get(buf)
+        return dict(zip(OP_KINDS, (int(v) for v in buf)))
+
+    with using_library(path):
+        raw.oracle_opcount_reset()
+        yield counts
+
+
 @contextlib.contextmanager
 def using_library(path: str):
     """Temporarily route every call through another build of the oracle (used by the tests

@@ -294,8 +294,8 @@ static int alloc_work(work_t *W, const grid_t *G) {
     W->nv = G->dim + 2;
     W->order = 2;
     for (int k = 0; k < W->nv; ++k) {
-        W->U[k] = calloc((size_t)G->npad, sizeof(double));
-        W->V[k] = calloc((size_t)G->npad, sizeof(double));
+        W->U[k] = (double *)calloc((size_t)G->npad, sizeof(double));
+        W->V[k] = (double *)calloc((size_t)G->npad, sizeof(double));
         if (!W->U[k] || !W->V[k]) return ORC_ENOMEM;
     }
     for (int a = 0; a < G->dim; ++a) {
@@ -304,9 +304,9 @@ static int alloc_work(work_t *W, const grid_t *G) {
             if (b != a) nf *= G->n[b];
         W->nface[a] = nf;
         for (int k = 0; k < W->nv; ++k) {
-            W->VL[a][k] = calloc((size_t)nf, sizeof(double));
-            W->VR[a][k] = calloc((size_t)nf, sizeof(double));
-            W->F[a][k] = calloc((size_t)nf, sizeof(double));
+            W->VL[a][k] = (double *)calloc((size_t)nf, sizeof(double));
+            W->VR[a][k] = (double *)calloc((size_t)nf, sizeof(double));
+            W->F[a][k] = (double *)calloc((size_t)nf, sizeof(double));
             if (!W->VL[a][k] || !W->VR[a][k] || !W->F[a][k]) return ORC_ENOMEM;
         }
     }
@@ -561,7 +561,7 @@ int oracle_run_opt(int dim, const long n[3], const double dr[3], double gamma,
     rc = alloc_work(&W, &G);
     W.order = order;
     W.riemann = riemann;
-    double *u1 = rc ? NULL : calloc((size_t)(dim + 2) * (size_t)G.ncell, sizeof(double));
+    double *u1 = rc ? NULL : (double *)calloc((size_t)(dim + 2) * (size_t)G.ncell, sizeof(double));
     if (rc || !u1) {
         free_work(&W);
         free(u1);
