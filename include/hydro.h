@@ -310,6 +310,15 @@ int hydro_step_static(const hydro_grid_t *grid, double gamma, const int32_t bc[3
                       double cfl, const hydro_state_t *state, int32_t n_steps, double t_end,
                       double *t_inout, int32_t *steps_done, void *stream);
 
+/* Diagnostic with no counterpart in the paper: the measured fused multiply-add throughput of
+ * the current device, in lane operations per second (one FMA counts one), for prec HYDRO_F32 or
+ * HYDRO_F64.  A grid of every SM's resident 256-thread CTAs runs eight independent FMA chains
+ * per thread; the best of three timed launches (CUDA events on `stream`, after one warm-up
+ * launch) is returned in *ops_per_s_out.  Takes a few tens of milliseconds, allocates one
+ * element with cudaMallocAsync on `stream` and frees it, and synchronises the stream.
+ * Errors: HYDRO_EINVAL (null output, other prec), HYDRO_ECUDA. */
+int hydro_fma_rate(int32_t prec, void *stream, double *ops_per_s_out);
+
 #ifdef __cplusplus
 }
 #endif

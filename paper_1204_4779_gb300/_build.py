@@ -36,6 +36,7 @@ UNITS = {
     "batch_abi.cu": [],
     "mlp.cu": [],
     "wave.cu": ["--fmad=false"],
+    "diag.cu": [],
 }
 HEADERS = ["hydro_device.cuh", "stage_kernel.cuh", "stage_launch.cuh", "hydro_internal.h",
            "batch_kernel.cuh"]

@@ -33,7 +33,7 @@ EXPORTS = (
     "hydro_batch_offsets", "hydro_batch_set_stream", "hydro_batch_step", "hydro_batch_totals",
     "hydro_batch_set_profiling", "hydro_batch_kernel_times",
     "hydro_mlp_sizes", "hydro_mlp_forward", "hydro_mlp_gradient", "hydro_mlp_adam", "hydro_mlp_train",
-    "hydro_wave_workspace_bytes", "hydro_wave_run",
+    "hydro_wave_workspace_bytes", "hydro_wave_run", "hydro_fma_rate",
 )
 
 
@@ -115,6 +115,7 @@ def load_library(path: str = LIB_PATH, build_if_missing: bool = True):
             "hydro_batch_set_profiling": ([vp, i32], ctypes.c_int),
             "hydro_batch_kernel_times": ([vp, P(dbl), P(i64), i32, i32], ctypes.c_int),
             "hydro_mlp_sizes": ([i32, i32, i64, P(i64), P(ctypes.c_size_t)], ctypes.c_int),
+            "hydro_fma_rate": ([i32, vp, P(dbl)], ctypes.c_int),
             "hydro_wave_workspace_bytes": ([i64, i32, i32, P(ctypes.c_size_t)], ctypes.c_int),
             "hydro_wave_run": ([i32, i64, dbl, dbl, dbl, vp, vp, i32, P(dbl), vp, ctypes.c_size_t, vp],
                                ctypes.c_int),
@@ -423,6 +424,16 @@ class BatchSolver:
         _check(self.lib.hydro_batch_kernel_times(self.ctx, ms, n, 3, 1 if reset else 0),
                "hydro_batch_kernel_times")
         return {k: (ms[i], n[i]) for i, k in enumerate(("cfl", "stage1", "stage2"))}
+
+
+def fma_rate(dtype=torch.float32, device=None) -> float:
+    """Measured FMA throughput of the device (hydro_fma_rate), in lane operations per second."""
+    lib = load_library()
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    out = ctypes.c_double()
+    with torch.cuda.device(dev):
+        _check(lib.hydro_fma_rate(_prec(dtype), _stream_ptr(dev), ctypes.byref(out)), "hydro_fma_rate")
+    return out.value
 
 
 def wave_run(f: torch.Tensor, g: torch.Tensor, c: float, length: float, dt: float, n_steps: int):
