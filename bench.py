@@ -48,6 +48,17 @@ def _kernel_digest() -> str:
     return h.hexdigest()[:16]
 
 
+def _oracle_opcounts():
+    """Floating-point operations per cell-update of one RK step, as counted in the oracle's
+    evaluation of the benchmark's blast (profiles/oracle_opcounts.json, written by
+    oracle/count_ops.py); None if the file is missing."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "oracle_opcounts.json")) as f:
+            return float(json.load(f)["per_cell_update"]["total"])
+    except Exception:
+        return None
+
+
 def _ncu_record(field: str, kernel: str):
     """Per-launch figure (`per_launch_bytes` or `per_launch_warp_instructions`) of `kernel` at
     512^3 from the committed ncu summary, if it was taken on the current kernel source; else
@@ -142,7 +153,7 @@ def _gpu_index(local_rank: int) -> int:
     return local_rank
 
 
-def cpu_oracle_cups(budget_s: float = 12.0, n: int = 64, max_steps: int = 200):
+def cpu_oracle_cups(budget_s: float = 12.0, n: int = 64, max_steps: int = 200, device=None):
     """The FP64 CPU oracle as it stands, on a bounded sample of the workload: the same blast
     at n^3 (radius 8 cells, periodic, CFL 0.4), all host cores, about `budget_s` of CPU work."""
     import oracle
@@ -154,12 +165,42 @@ def cpu_oracle_cups(budget_s: float = 12.0, n: int = 64, max_steps: int = 200):
     one = time.perf_counter() - t0
     steps = max(1, min(max_steps, int(budget_s / max(one, 1e-6))))
     t0 = time.perf_counter()
-    _, _, done, _ = oracle.run(U, GAMMA, CFL, steps, bc=(0, 0, 0), threads=threads)
+    Uo, _, done, _ = oracle.run(U, GAMMA, CFL, steps, bc=(0, 0, 0), threads=threads)
     el = time.perf_counter() - t0
-    return {"value": n ** 3 * done / el, "unit": "cell-updates/s", "cores": threads,
-            "kind": "oracle",
-            "sample": f"{n}^3 blast (radius {RADIUS:g} cells), {done} FP64 RK steps, "
-                      f"{el:.1f} s, OpenMP threads={threads}, host={os.uname().machine}"}
+    out = {"value": n ** 3 * done / el, "unit": "cell-updates/s", "cores": threads,
+           "kind": "oracle",
+           "sample": f"{n}^3 blast (radius {RADIUS:g} cells), {done} FP64 RK steps, "
+                     f"{el:.1f} s, OpenMP threads={threads}, host={os.uname().machine}"}
+    if device is not None:
+        out["gpu_error_vs_oracle"] = _gpu_error(n, 1 + done, Uo, device)
+    return out
+
+
+def _gpu_error(n, steps, Uo, device):
+    """The GPU's FP32 and FP64 results after the same steps from the same FP64 initial data as
+    the oracle's sample: L1 density error (FP32) and max relative error (FP64, per field:
+    elementwise for rho and E, normwise for the momenta)."""
+    import numpy as np
+    import torch
+
+    from paper_1204_4779_gb300 import hydro, inputs
+    V = torch.from_numpy(inputs.blast_3d(n, radius_cells=RADIUS)).to(device)
+    U64 = hydro.prim_to_cons(V, GAMMA)
+    res = {"steps": steps}
+    for dt, key in ((torch.float32, "fp32_l1_rho"), (torch.float64, "fp64_max_rel")):
+        U = U64.to(dt).contiguous()
+        S = hydro.Solver((n, n, n), GAMMA, bc="periodic", dtype=dt, cfl=CFL, device=device)
+        S.step(U, steps)
+        G = U.double().cpu().numpy()
+        S.close()
+        if dt == torch.float32:
+            res[key] = float(np.abs(G[0] - Uo[0]).sum() / np.abs(Uo[0]).sum())
+        else:
+            e = [float(np.max(np.abs(G[k] - Uo[k]) / np.abs(Uo[k]))) for k in (0, 4)]
+            e += [float(np.max(np.abs(G[k] - Uo[k])) / max(float(np.max(np.abs(Uo[k]))), 1e-300))
+                  for k in (1, 2, 3)]
+            res[key] = max(e)
+    return res
 
 
 def run_reference(args):
@@ -217,8 +258,12 @@ def run_ours(args):
     U_init = U.clone()
     del V
     S = hydro.Solver((n, n, n), GAMMA, bc="periodic", dtype=torch.float32, cfl=CFL)
+    # measured FMA throughput of this GPU (the FP32 roofline's denominator), before the warm-up
+    fma32 = hydro.fma_rate(torch.float32, dev)
+    fma64 = hydro.fma_rate(torch.float64, dev)
     S.step(U, args.warmup)
     torch.cuda.synchronize()
+    U_start = U.clone() if args.repeats > 0 else None
 
     # --- timed region: K RK steps, per-kernel CUDA events on the launching stream ----------
     S.set_profiling(True)
@@ -238,6 +283,33 @@ def run_ours(args):
     if done != args.steps:
         raise RuntimeError(f"only {done} of {args.steps} steps ran")
     value, ms_max = aggregate_replicas(ms, ncell * args.steps, device=dev)
+
+    # --- the paper's protocol: R runs of K steps replayed from CUDA graphs, mean and std ----
+    repeats = None
+    if args.repeats > 0:
+        U.copy_(U_start)
+        S.step(U, args.steps)  # capture the step graphs outside the timed runs
+        runs = []
+        for _ in range(args.repeats):
+            U.copy_(U_start)
+            barrier()
+            torch.cuda.synchronize()
+            r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            r0.record()
+            S.step(U, args.steps, sync=False)
+            r1.record()
+            torch.cuda.synchronize()
+            barrier()
+            v, _ = aggregate_replicas(r0.elapsed_time(r1), ncell * args.steps, device=dev)
+            runs.append(v)
+        mu = sum(runs) / len(runs)
+        sd = (sum((x - mu) ** 2 for x in runs) / max(len(runs) - 1, 1)) ** 0.5
+        repeats = {"runs": len(runs), "steps_each": args.steps, "mean": mu, "std": sd,
+                   "min": min(runs), "max": max(runs), "unit": "cell-updates/s",
+                   "how": "state reset to the post-warm-up state before each run; steps replayed "
+                          "from the context's CUDA graphs (no per-kernel events); CUDA events "
+                          "around each run"}
+        del U_start
 
     # --- roofline of the dominant kernel ---------------------------------------------------
     hbm, peak_kind = _peaks()
@@ -286,9 +358,46 @@ def run_ours(args):
                  "source": "ncu smsp__inst_executed.sum (profiles/ncu_counters.json) / live "
                            "CUDA-event launch time; peak = 4 x SMs x sampled SM clock"}
 
+    # FP64 throughput of the same workload (the FP64 form of the stage kernels), graph replay
+    fp64 = None
+    if args.fp64_steps > 0:
+        del U_init
+        V64 = inputs.blast_3d_torch(n, RADIUS, device=dev)
+        U64 = hydro.prim_to_cons(V64, GAMMA)
+        del V64
+        S64 = hydro.Solver((n, n, n), GAMMA, bc="periodic", dtype=torch.float64, cfl=CFL, device=dev)
+        S64.step(U64, args.fp64_steps)  # graphs and warm-up
+        barrier()
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record()
+        S64.step(U64, args.fp64_steps, sync=False)
+        f1.record()
+        torch.cuda.synchronize()
+        barrier()
+        v64, ms64 = aggregate_replicas(f0.elapsed_time(f1), ncell * args.fp64_steps, device=dev)
+        fp64 = {"value": v64, "unit": "cell-updates/s", "steps": args.fp64_steps,
+                "ms_per_step": ms64 / args.fp64_steps, "dtype": "f64"}
+        S64.close()
+        del U64, S64
+
+    # FP32 roofline of the whole step: the oracle's counted operations per cell-update times
+    # the cell-updates per second, against the measured FMA rate (one operation per lane per
+    # instruction; divisions and square roots take several instructions on the GPU, so this
+    # bound is generous to the kernel)
+    fp32 = None
+    opc = _oracle_opcounts()
+    if opc is not None:
+        ach = opc * ncell * args.steps / (ms_max * 1e-3)
+        fp32 = {"bound": "alu", "scope": "whole RK step", "achieved": ach, "peak": fma32,
+                "unit": "FP32 lane-operations/s", "frac": ach / fma32,
+                "ops_per_cell_update": opc, "fma_rate_f64": fma64,
+                "source": "operations counted in the FP64 oracle's own evaluation of one RK step "
+                          "(profiles/oracle_opcounts.json); peak = hydro_fma_rate measured live"}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_oracle_cups()
+        cpu = cpu_oracle_cups(device=dev)
 
     if rank == 0:
         line = {
@@ -309,6 +418,9 @@ def run_ours(args):
             "gpu_launches": int(sum(v[1] for v in kt.values())),
             "clocks": clocks,
             "issue_roofline": issue,
+            "fp32_roofline": fp32,
+            "repeats": repeats,
+            "fp64": fp64,
             "e2e": e2e,
             "cpu_baseline": cpu,
             "sim_time": t_sim,
@@ -382,6 +494,10 @@ def main():
     ap.add_argument("--config", choices=("blast512", "batched"), default="blast512",
                     help="blast512: the benchmark line; batched: the 4096-grid configuration")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=10,
+                    help="timed FP64 steps of the same workload after the FP32 run (0: none)")
+    ap.add_argument("--repeats", type=int, default=30,
+                    help="extra graph-replay runs of --steps steps for mean and std (0: none)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
