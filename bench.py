@@ -473,7 +473,8 @@ def run_batched(args):
             "config": {"workload": "4096 independent 2D grids, sides log-uniform on [32, 512] "
                                    "(seed 1204477904), smooth seeded data, FP32",
                        "cells": ncell, "l2": "inputs larger than L2 (1.9 GB state); no flush",
-                       "tile": [32, 8]},
+                       "variant": "library default: row tiles of 32 columns marching 32 rows "
+                                  "along y, one work item per strip and chunk"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": None, "kernel": "batch_" + dom,
                          "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"},

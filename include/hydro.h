@@ -74,21 +74,28 @@ typedef struct {
 } hydro_state_t;
 
 /* Kernel variant (the tuning space).  Zero-initialised = library default.
- *   tile_x, tile_y: in-plane CTA tile (cells); tile_y = 1 for dim 1.  The compiled shapes are
- *                   listed by hydro_variant_supported().
- *   march:          dim 3 only: z-planes one CTA marches through (>= 1), i.e. the cells each
- *                   thread updates per stage.
- *   split:          fusion split.  0 = library default (dim 3: fused; dims 1 and 2:
- *                   separate); 1 = a separate CFL pass after RK stage 2 (one more launch and
- *                   one more read of the state per step); 2 = the CFL signal and the next dt
- *                   reduced in the epilogue of stage 2 (fused).
- *   staging:        staging depth, dim 3 only.  0 = default (1); 1 = the next z-plane's loads
- *                   are issued one plane ahead of their use; 2 = each plane is loaded when it
- *                   is staged (no look-ahead, fewer registers).
- *   occupancy:      dim 3 FP32 only: resident 256-thread CTAs per SM the register budget of
- *                   the stage kernels targets.  0 = library default (3 for dim 3 FP32, else
- *                   2); 2 (about 128 registers a thread); 3 (about 80 registers, 24 warps per
- *                   SM).
+ *   tile_x, tile_y: CTA tile (cells).  dim 3: a tile of the (x, y) plane that marches along
+ *                   z; dim 2: a tile of the plane, or with tile_y = 1 a row of tile_x cells
+ *                   that marches along y ("row tile"); dim 1: a row (tile_y = 1).  Which shapes
+ *                   are compiled is answered by hydro_variant_supported().
+ *   march:          marching tiles only (dim 3, dim-2 row tiles): planes one CTA marches
+ *                   through (>= 1), i.e. the cells each thread updates per stage; 0 = default
+ *                   (64 in dim 3, 16 for row tiles).
+ *   split:          fusion split.  0 = library default (fused for marching tiles, separate
+ *                   for one-plane tiles); 1 = a separate CFL pass after RK stage 2 (one more
+ *                   launch and one more read of the state per step); 2 = the CFL signal and
+ *                   the next dt reduced in the epilogue of stage 2 (fused).
+ *   staging:        staging depth, marching tiles only.  0 = default (1); 1 = the next
+ *                   plane's loads are issued one plane ahead of their use; 2 = each plane is
+ *                   loaded when it is staged (no look-ahead, fewer registers).
+ *   occupancy:      FP32 marching tiles only: resident 256-thread CTAs' worth of warps per SM
+ *                   the register budget of the stage kernels targets.  0 = library default
+ *                   (3 for the default FP32 marching tiles, else 2); 2 (about 128 registers a
+ *                   thread); 3 (about 80 registers, 24 warps per SM).
+ * Library defaults (measured on GB300): dim 3 tile 32 x 8, march 64; dim 2 FP32 row tile
+ * 256 x 1, march 16; dim 2 FP64 tile 32 x 8; dim 1 tile 128.  A variant that names a tile other
+ * than the default gets that tile's default march (64 in dim 3, 16 for row tiles) and
+ * budget unless it names them too.
  * Every variant computes the same step; they differ in speed only. */
 typedef struct {
     int32_t tile_x;

@@ -39,27 +39,34 @@ bool shapes_ok(int32_t n_grids, const int64_t *nx, const int64_t *ny) {
     return true;
 }
 
-void tile_of(int prec, const hydro_variant_t *v, int *bx, int *by) {
+// Tile of the batch kernels and the rows of one work item (the tile height, or for row tiles,
+// tile_y = 1, the march along y).
+// Default: FP32 row tiles of 32 columns marching 32 rows (4096 uneven grids: 24.3 G
+// cell-updates/s against 16.4 G for the 32 x 8 tile kernel); FP64 the 32 x 8 tiles.
+void tile_of(int prec, const hydro_variant_t *v, int *bx, int *by, int *rows) {
     *bx = 32;
-    *by = 8;
+    *by = prec == HYDRO_F32 ? 1 : 8;
     if (v && v->tile_x) *bx = v->tile_x;
     if (v && v->tile_y) *by = v->tile_y;
-    (void)prec;
+    *rows = *by;
+    if (*by == 1) *rows = (v && v->march > 0) ? v->march : 32;
 }
 
-bool tile_ok(int prec, int bx, int by) {
+bool tile_ok(int prec, int bx, int by, const hydro_variant_t *v) {
+    if (v && v->march < 0) return false;
     if (bx == 32 && by == 8) return true;
+    if (by == 1) return prec == HYDRO_F32 ? (bx == 32 || bx == 64 || bx == 128) : bx == 64;
     return prec == HYDRO_F32 && bx == 16 && by == 16;
 }
 
 BatchLayout batch_layout(int32_t n_grids, const int64_t *nx, const int64_t *ny, int prec, int bx,
-                         int by) {
+                         int rows) {
     BatchLayout L;
     L.ncell = 0;
     L.n_items = 0;
     for (int g = 0; g < n_grids; ++g) {
         L.ncell += nx[g] * ny[g];
-        L.n_items += ((nx[g] + bx - 1) / bx) * ((ny[g] + by - 1) / by);
+        L.n_items += ((nx[g] + bx - 1) / bx) * ((ny[g] + rows - 1) / rows);
     }
     const size_t esz = prec == HYDRO_F32 ? 4 : 8;
     L.ctrl_off = 0;
@@ -99,6 +106,7 @@ struct hydro_batch {
     double gamma = 1.4, cfl = 0.4;
     int periodic[2] = {1, 1};
     int tile_x = 32, tile_y = 8;
+    int rows = 8;  // rows of a work item
     int n_blocks = 1;
     cudaStream_t stream = nullptr;
     cudaStream_t cap = nullptr;
@@ -142,6 +150,7 @@ BatchLaunch launch_args(const hydro_batch *b, const hydro_state_t *s, int kind, 
     L.n_blocks = b->n_blocks;
     L.tile_x = b->tile_x;
     L.tile_y = b->tile_y;
+    L.march = b->rows;
     return L;
 }
 
@@ -241,10 +250,10 @@ int hydro_batch_workspace_bytes(int32_t n_grids, const int64_t *nx, const int64_
                                 const hydro_variant_t *variant, size_t *bytes_out) {
     if (!bytes_out || !shapes_ok(n_grids, nx, ny)) return HYDRO_EINVAL;
     if (prec != HYDRO_F32 && prec != HYDRO_F64) return HYDRO_EINVAL;
-    int bx, by;
-    tile_of(prec, variant, &bx, &by);
-    if (!tile_ok(prec, bx, by)) return HYDRO_EUNSUPPORTED;
-    *bytes_out = batch_layout(n_grids, nx, ny, prec, bx, by).total;
+    int bx, by, rows;
+    tile_of(prec, variant, &bx, &by, &rows);
+    if (!tile_ok(prec, bx, by, variant)) return HYDRO_EUNSUPPORTED;
+    *bytes_out = batch_layout(n_grids, nx, ny, prec, bx, rows).total;
     return HYDRO_OK;
 }
 
@@ -260,10 +269,10 @@ int hydro_batch_create(int32_t n_grids, const int64_t *nx, const int64_t *ny, do
     for (int a = 0; a < 2; ++a)
         if (bc[a] != HYDRO_BC_PERIODIC && bc[a] != HYDRO_BC_OUTFLOW) return HYDRO_EINVAL;
     if (((uintptr_t)workspace) % kAlign) return HYDRO_EINVAL;
-    int bx, by;
-    tile_of(prec, variant, &bx, &by);
-    if (!tile_ok(prec, bx, by)) return HYDRO_EUNSUPPORTED;
-    const BatchLayout lay = batch_layout(n_grids, nx, ny, prec, bx, by);
+    int bx, by, rows;
+    tile_of(prec, variant, &bx, &by, &rows);
+    if (!tile_ok(prec, bx, by, variant)) return HYDRO_EUNSUPPORTED;
+    const BatchLayout lay = batch_layout(n_grids, nx, ny, prec, bx, rows);
     if (workspace_bytes < lay.total) return HYDRO_EINVAL;
     if (lay.n_items >= (1LL << 31)) return HYDRO_EUNSUPPORTED;
 
@@ -282,6 +291,7 @@ int hydro_batch_create(int32_t n_grids, const int64_t *nx, const int64_t *ny, do
     b->periodic[1] = bc[1] == HYDRO_BC_PERIODIC;
     b->tile_x = bx;
     b->tile_y = by;
+    b->rows = rows;
     b->stream = static_cast<cudaStream_t>(stream);
     b->ws = static_cast<unsigned char *>(workspace);
     b->ctrl = reinterpret_cast<Ctrl *>(b->ws + lay.ctrl_off);
@@ -307,11 +317,11 @@ int hydro_batch_create(int32_t n_grids, const int64_t *nx, const int64_t *ny, do
         G.dr[1] = 1.0 / (double)ny[g];
         G.inv_dr[0] = (float)(1.0 / G.dr[0]);
         G.inv_dr[1] = (float)(1.0 / G.dr[1]);
-        const int tx = (G.nx + bx - 1) / bx, ty = (G.ny + by - 1) / by;
+        const int tx = (G.nx + bx - 1) / bx, ty = (G.ny + rows - 1) / rows;
         G.ntiles = tx * ty;
         G.first_item = (int)hi.size();
         for (int j = 0; j < ty; ++j)
-            for (int i = 0; i < tx; ++i) hi.push_back(BatchItem{g, i * bx, j * by, 0});
+            for (int i = 0; i < tx; ++i) hi.push_back(BatchItem{g, i * bx, j * rows, 0});
         b->offsets[(size_t)g] = off;
         off += nx[g] * ny[g];
     }
@@ -322,6 +332,7 @@ int hydro_batch_create(int32_t n_grids, const int64_t *nx, const int64_t *ny, do
     memset(&P, 0, sizeof P);
     P.tile_x = bx;
     P.tile_y = by;
+    P.march = rows;
     int per_sm = 0, n_sm = 0;
     if (e == cudaSuccess)
         e = prec == HYDRO_F32 ? hydro::batch_f32(P, nullptr, 3, true, &per_sm)

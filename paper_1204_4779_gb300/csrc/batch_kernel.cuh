@@ -32,6 +32,7 @@ template <class T> struct BatchArgs {
     const double *t0;  // per-grid start time (init kernel), may be null
     double t_end, cfl;
     int periodic[2];
+    int rows;   // rows of a work item: the tile height, or the march of row tiles
     Gas<T> gas;
 };
 
@@ -143,7 +144,7 @@ __global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY>::value))
             Cells<T, NV>::get(sF, NF, fxl + 1, fe);
             Cells<T, NV>::get(sF, NF, fyb, fs);
             Cells<T, NV>::get(sF, NF, fyb + BX, fn);
-            add_fluxes<T, 2>(base, cx, fw, fe, cy, fs, fn, T(0), fw, fw, un);  // no z term in 2D
+            add_fluxes<T, NV, true, false>(base, cx, fw, fe, cy, fs, fn, T(0), fw, fw, un);
             const long long i = off + (long long)y * nx + x;
 #pragma unroll
             for (int k = 0; k < NV; ++k) A.uout[k][i] = un[k];
@@ -166,6 +167,52 @@ __global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY>::value))
         }
         if constexpr (STAGE == 2) {
             const T m = block_max<T, NT>(bad ? T(NAN) : smax, sRed);
+            if (threadIdx.x == 0) A.tile_sig[it] = m;
+        }
+    }
+}
+
+// Row tiles: a work item is a strip of BX columns of one grid and a chunk of `rows` rows,
+// advanced by the single-grid kernels' per-tile code (stage_tile) marching along y, with the
+// same per-tile CFL slot as the tile kernel above.
+template <class T, int BX, int STAGE, int OCC>
+__global__ void __launch_bounds__(BX, (MinBlocks<T, BX, OCC>::value))
+    batch_row_kernel(const BatchArgs<T> A) {
+    using S = StageShape<T, 2, BX, 1>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *const sRed = reinterpret_cast<T *>(smem_raw) + 2 * S::NV * S::PL + 2 * S::NV * S::NF;
+    for (int it = blockIdx.x; it < A.n_items; it += gridDim.x) {
+        const BatchItem W = A.items[it];
+        const BatchGrid R = A.grids[W.g];
+        Ctrl *ctrl = A.ctrl + W.g;
+        const double dt = __ldcg(&ctrl->dt);
+        if (!(dt > 0.0)) continue;  // this grid takes no step (same for the whole CTA)
+        const T cx = T(__ldcg(&ctrl->coef[STAGE - 1][0]));
+        const T cy = T(__ldcg(&ctrl->coef[STAGE - 1][1]));
+        StageArgs<T> V;  // the grid as a single-grid problem
+        for (int k = 0; k < 4; ++k) {
+            V.uin[k] = A.uin[k] + R.off;
+            V.ubase[k] = A.ubase[k] + R.off;
+            V.uout[k] = A.uout[k] + R.off;
+        }
+        V.uin[4] = V.ubase[4] = nullptr;
+        V.uout[4] = nullptr;
+        V.n[0] = R.nx, V.n[1] = R.ny, V.n[2] = 1;
+        V.periodic[0] = A.periodic[0], V.periodic[1] = A.periodic[1], V.periodic[2] = 1;
+        V.march = A.rows;
+        V.order = 2;
+        V.riemann = 0;
+        V.dr[0] = R.dr[0], V.dr[1] = R.dr[1], V.dr[2] = 1.0;
+        V.inv_dr[0] = T(R.inv_dr[0]), V.inv_dr[1] = T(R.inv_dr[1]), V.inv_dr[2] = T(1);
+        V.gas = A.gas;
+        V.ctrl = ctrl;
+        __syncthreads();  // the previous item's last shared-memory reads are done
+        T smax = T(0);
+        bool bad = false;
+        stage_tile<T, 2, BX, 1, STAGE, 1, (STAGE == 2)>(V, W.x0, 0, W.y0, min(W.y0 + A.rows, R.ny),
+                                                         smem_raw, cx, T(0), cy, smax, bad);
+        if constexpr (STAGE == 2) {
+            const T m = block_max<T, BX>(bad ? T(NAN) : smax, sRed);
             if (threadIdx.x == 0) A.tile_sig[it] = m;
         }
     }
@@ -195,10 +242,10 @@ __global__ void __launch_bounds__(BX * BY) batch_cfl_kernel(const BatchArgs<T> A
     for (int it = blockIdx.x; it < A.n_items; it += gridDim.x) {
         const BatchItem W = A.items[it];
         const BatchGrid R = A.grids[W.g];
-        const int x = W.x0 + tx, y = W.y0 + ty;
+        const int x = W.x0 + tx;
         T smax = T(0);
         bool bad = false;
-        if (x < R.nx && y < R.ny) {
+        for (int y = W.y0 + ty; y < W.y0 + A.rows && y < R.ny && x < R.nx; y += BY) {
             const long long i = R.off + (long long)y * R.nx + x;
             T u[4], v[4];
 #pragma unroll
@@ -214,8 +261,8 @@ __global__ void __launch_bounds__(BX * BY) batch_cfl_kernel(const BatchArgs<T> A
                 s = fmaf(fabsf(v[1]) + cs, R.inv_dr[0], s);
                 s = fmaf(fabsf(v[2]) + cs, R.inv_dr[1], s);
             }
-            smax = s;
-            bad = !(v[0] > T(0)) || !(v[3] > T(0));
+            smax = (s > smax || s != s) ? s : smax;
+            bad |= !(v[0] > T(0)) || !(v[3] > T(0));
         }
         const T m = block_max<T, NT>(bad ? T(NAN) : smax, sRed);
         if (threadIdx.x == 0) A.tile_sig[it] = m;
@@ -298,36 +345,47 @@ template <class T> BatchArgs<T> make_batch_args(const BatchLaunch &L) {
     A.cfl = L.cfl;
     A.periodic[0] = L.periodic[0];
     A.periodic[1] = L.periodic[1];
+    A.rows = L.tile_y == 1 ? L.march : L.tile_y;
     A.gas = make_gas<T>(L.gamma);
     return A;
 }
 
+// The two RK-stage kernels of a batch tile shape: row tiles or one-plane tiles.
+template <class T, int BX, int BY, int OCC, bool ROWS> struct BatchKernels {
+    static constexpr auto s1 = batch_stage_kernel<T, BX, BY, 1>;
+    static constexpr auto s2 = batch_stage_kernel<T, BX, BY, 2>;
+};
+template <class T, int BX, int BY, int OCC> struct BatchKernels<T, BX, BY, OCC, true> {
+    static constexpr auto s1 = batch_row_kernel<T, BX, 1, OCC>;
+    static constexpr auto s2 = batch_row_kernel<T, BX, 2, OCC>;
+};
+
 // Dispatch for one precision: kind 0 = init, 1 = CFL pass, 2/3 = RK stage 1/2, 4 = totals;
 // prepare_only sets the shared-memory attribute and returns the resident CTAs per SM of the
 // stage kernel in *blocks_per_sm.
-template <class T, int BX, int BY>
+template <class T, int BX, int BY, int OCC = 2>
 cudaError_t batch_dispatch_tile(const BatchLaunch &L, cudaStream_t st, int kind, bool prepare_only,
                                 int *blocks_per_sm) {
     using S = StageShape<T, 2, BX, BY>;
-    const size_t smem = sizeof(T) * (size_t)(4 * S::PL + 4 * S::NF + 2 * (S::NT / 32));
+    constexpr bool rows = (BY == 1);  // row tiles march along y
+    // the tile kernel keeps one primitive and one flux plane; row tiles use stage_tile's two each
+    const size_t smem = sizeof(T) * (size_t)((rows ? 2 : 1) * 4 * (S::PL + S::NF) + 2 * (S::NT / 32));
+    using K = BatchKernels<T, BX, BY, OCC, rows>;
+    const auto s1 = K::s1, s2 = K::s2;
     if (prepare_only) {
-        cudaError_t e = cudaFuncSetAttribute(batch_stage_kernel<T, BX, BY, 1>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(s1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(batch_stage_kernel<T, BX, BY, 2>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            e = cudaFuncSetAttribute(s2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess && blocks_per_sm)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm,
-                                                              batch_stage_kernel<T, BX, BY, 2>,
-                                                              S::NT, smem);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, s2, S::NT, smem);
         return e;
     }
     const BatchArgs<T> A = make_batch_args<T>(L);
     switch (kind) {
         case 0: batch_init_kernel<<<(L.n_grids + 255) / 256, 256, 0, st>>>(A.ctrl, A.grids, L.n_grids, A.t0, A.t_end, A.cfl); break;
         case 1: batch_cfl_kernel<T, BX, BY><<<L.n_blocks, S::NT, 0, st>>>(A); break;
-        case 2: batch_stage_kernel<T, BX, BY, 1><<<L.n_blocks, S::NT, smem, st>>>(A); break;
-        case 3: batch_stage_kernel<T, BX, BY, 2><<<L.n_blocks, S::NT, smem, st>>>(A); break;
+        case 2: s1<<<L.n_blocks, S::NT, smem, st>>>(A); break;
+        case 3: s2<<<L.n_blocks, S::NT, smem, st>>>(A); break;
         case 4: batch_totals_kernel<T><<<L.n_grids, 256, 0, st>>>(A, L.n_grids); break;
         case 5: batch_finalize_kernel<T, false><<<(L.n_grids * 32 + 255) / 256, 256, 0, st>>>(A, L.n_grids); break;
         case 6: batch_finalize_kernel<T, true><<<(L.n_grids * 32 + 255) / 256, 256, 0, st>>>(A, L.n_grids); break;

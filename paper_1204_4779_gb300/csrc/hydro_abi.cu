@@ -83,41 +83,69 @@ int tile_compiled(int prec, int dim, int bx, int by) {
     return 0;
 }
 
-// Defaults chosen by the variant tuner's measurements on GB300: in 3D the FP32 kernels with the
-// three-CTA register budget; in 1D and 2D, where a CTA updates one tile, the separate CFL pass
-// (a fused per-CTA reduction costs more there than one extra read of the state).
+// Defaults chosen by measurements on GB300.  dim 3: tile 32 x 8 marching 64 planes, in FP32 with
+// the three-CTA register budget (the variant tuner's best).  dim 2, FP32: row tiles of 256
+// cells marching 16 rows along y, three-CTA budget (2048^2: 28.4 G cell-updates/s against 20.8
+// G for the best one-plane tile).  dim 1 and FP64 dim 2: one-plane tiles.  The dt reduction is
+// fused into stage 2 for marching tiles; for one-plane tiles, where a CTA updates one tile, the
+// separate CFL pass (a fused per-CTA reduction costs more there than one extra read of the
+// state).  The split is settled in resolve_variant, once the tile is known.
 void default_variant(int prec, int dim, hydro_variant_t *v) {
-    v->split = dim < 3 ? 1 : 0;
+    v->split = 0;
     v->staging = 1;
-    v->occupancy = (dim == 3 && prec == HYDRO_F32) ? 3 : 2;
+    v->occupancy = 2;
     v->march = 0;
     if (dim == 1) {
         v->tile_x = 128;
         v->tile_y = 1;
+    } else if (dim == 2 && prec == HYDRO_F32) {
+        v->tile_x = 256;
+        v->tile_y = 1;
+        v->march = 16;
+        v->occupancy = 3;
     } else {
         v->tile_x = 32;
         v->tile_y = 8;
     }
-    if (dim == 3) v->march = 64;
+    if (dim == 3) {
+        v->march = 64;
+        if (prec == HYDRO_F32) v->occupancy = 3;
+    }
 }
 
 // Resolve a (possibly partial) variant against the defaults; false if not compiled.
 bool resolve_variant(int prec, int dim, const hydro_variant_t *in, hydro_variant_t *out) {
     default_variant(prec, dim, out);
     if (in) {
+        const bool tile_given = in->tile_x || in->tile_y;
         if (in->tile_x) out->tile_x = in->tile_x;
         if (in->tile_y) out->tile_y = in->tile_y;
+        if (tile_given) {  // the default march and budget belong to the default tile
+            hydro_variant_t d;
+            default_variant(prec, dim, &d);
+            if (out->tile_x != d.tile_x || out->tile_y != d.tile_y) {
+                out->march = 0;
+                out->occupancy = dim == 3 ? d.occupancy : 2;
+            }
+        }
         if (in->march) out->march = in->march;
-        if (in->split) out->split = in->split == 2 ? 0 : in->split;
+        if (in->split) out->split = in->split;
         if (in->staging) out->staging = in->staging;
         if (in->occupancy) out->occupancy = in->occupancy;
     }
     if (in && (in->split < 0 || in->split > 2)) return false;
     if (out->staging != 1 && out->staging != 2) return false;
     if (out->occupancy != 2 && out->occupancy != 3) return false;
-    if (out->occupancy == 3 && (dim != 3 || prec != HYDRO_F32)) return false;
-    if (dim == 3 && out->march < 1) return false;
-    if (dim < 3) {
+    // marching tiles: dim 3, and the row tiles of dim 2 (tile_y = 1), which march along y
+    const bool marching = dim == 3 || (dim == 2 && out->tile_y == 1);
+    // split 0 = default: fused for marching tiles, the separate CFL pass for one-plane tiles;
+    // internally 0 = fused, 1 = separate
+    if (out->split == 0) out->split = marching ? 0 : 1;
+    else if (out->split == 2) out->split = 0;
+    if (out->occupancy == 3 && (!marching || prec != HYDRO_F32)) return false;
+    if (marching && out->march == 0) out->march = dim == 3 ? 64 : 16;
+    if (marching && out->march < 1) return false;
+    if (!marching) {
         out->march = 1;
         out->staging = 1;  // one plane: nothing to look ahead to
     }
@@ -414,8 +442,12 @@ int hydro_create(const hydro_grid_t *grid, double gamma, const int32_t bc[3], in
     hydro_variant_t var;
     if (!resolve_variant(prec, grid->dim, variant, &var)) return HYDRO_EUNSUPPORTED;
     // grid-dimension limits of the stage launch
-    if (grid->dim >= 2 && (grid->n[1] + var.tile_y - 1) / var.tile_y > 65535) return HYDRO_EUNSUPPORTED;
-    if (grid->dim == 3 && (grid->n[2] + var.march - 1) / var.march > 65535) return HYDRO_EUNSUPPORTED;
+    const bool marching = grid->dim == 3 || (grid->dim == 2 && var.tile_y == 1);
+    if ((grid->dim == 3 || (grid->dim == 2 && !marching)) &&
+        (grid->n[1] + var.tile_y - 1) / var.tile_y > 65535)
+        return HYDRO_EUNSUPPORTED;
+    if (marching && (grid->n[grid->dim - 1] + var.march - 1) / var.march > 65535)
+        return HYDRO_EUNSUPPORTED;
 
     hydro_ctx *c = new (std::nothrow) hydro_ctx();
     if (!c) return HYDRO_EINVAL;
@@ -432,7 +464,7 @@ int hydro_create(const hydro_grid_t *grid, double gamma, const int32_t bc[3], in
         c->periodic[a] = act ? (bc[a] == HYDRO_BC_PERIODIC) : 1;
         c->dr[a] = act ? (grid->hi[a] - grid->lo[a]) / (double)grid->n[a] : 1.0;
     }
-    if (c->dim == 3 && var.march > c->n[2]) var.march = c->n[2];
+    if (marching && var.march > c->n[c->dim - 1]) var.march = c->n[c->dim - 1];
     c->gamma = gamma;
     c->cfl = cfl;
     c->var = var;

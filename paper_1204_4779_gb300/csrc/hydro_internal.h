@@ -93,7 +93,8 @@ struct BatchLaunch {
     double t_end, cfl, gamma;
     int periodic[2];
     int n_blocks;        // persistent grid size
-    int tile_x, tile_y;
+    int tile_x, tile_y;  // tile_y = 1: row tiles, which march along y
+    int march;           // rows of a row tile's work item
 };
 // kind: 0 init, 1 CFL pass (tile maxima), 2 RK stage 1, 3 RK stage 2 (+ tile maxima),
 // 4 per-grid totals, 5 per-grid dt from the tile maxima (first dt of a call), 6 the same after

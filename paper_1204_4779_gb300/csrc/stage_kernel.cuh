@@ -46,21 +46,33 @@ template <class T> struct StageArgs {
     Ctrl *ctrl;
 };
 
+// Tile geometry.  dim 3: a BX x BY tile of the (x, y) plane marching along z.  dim 2: a BX x BY
+// tile (one plane, no march), or with BY = 1 a row of BX cells marching along y ("row tiles").
+// dim 1: a row of BX cells.  IN = the in-plane axes whose faces go through shared memory; the
+// march axis D - 1 (if any) has its faces in the register pipeline.
+template <int D, int BY> struct Geom {
+    static constexpr bool rows = (D == 2 && BY == 1);
+    static constexpr bool march = (D == 3) || rows;
+    static constexpr int IN = (D == 3 || (D == 2 && BY > 1)) ? 2 : 1;
+    static constexpr int MA = D - 1;  // march axis
+};
+
 template <class T, int D, int BX, int BY> struct StageShape {
+    static constexpr int IN = Geom<D, BY>::IN;
     static constexpr int NV = D + 2;
     static constexpr int NT = BX * BY;
     static constexpr int HX = BX + 4;
-    static constexpr int HY = (D >= 2) ? BY + 4 : 1;
+    static constexpr int HY = (IN >= 2) ? BY + 4 : 1;
     // shared plane of one field, and the flux plane, in cells; multiples of four so that the
     // 16-byte records of Cells stay aligned from plane to plane
     static constexpr int PL = (HY * HX + 3) / 4 * 4;
     static constexpr int NFX = (BX + 1) * BY;
-    static constexpr int NFY = (D >= 2) ? BX * (BY + 1) : 0;
+    static constexpr int NFY = (IN >= 2) ? BX * (BY + 1) : 0;
     static constexpr int NF = (NFX + NFY + 3) / 4 * 4;
-    static constexpr int NH = (D >= 2) ? 4 * BY + 4 * BX : 4;
+    static constexpr int NH = (IN >= 2) ? 4 * BY + 4 * BX : 4;
     static constexpr int HPT = (NH + NT - 1) / NT;  // halo cells per thread
-    static constexpr int FPT = (D >= 2) ? 3 : 2;  // in-plane face rounds per thread
-    static_assert((D >= 2 ? BX + BY : 1) <= NT, "the tile's extra faces must fit in one round");
+    static constexpr int FPT = (IN >= 2) ? 3 : 2;  // in-plane face rounds per thread
+    static_assert((IN >= 2 ? BX + BY : 1) <= NT, "the tile's extra faces must fit in one round");
     static constexpr size_t smem_bytes = sizeof(T) * (size_t)(2 * NV * PL + 2 * NV * NF + 2 * (NT / 32));
 };
 
@@ -192,14 +204,15 @@ __device__ __forceinline__ void minbee_face_pair(const T (&q0)[NV], const T (&q1
     }
 }
 
-// AddFlux of one cell (Eq. eqAddFlux): un = base + cx (fw - fe) [+ cy (fs - fn) [+ cz (zm - zp)]],
-// the fluxes of its low and high faces per axis, all in axis order.
-template <class T, int D>
-__device__ __forceinline__ void add_fluxes(const T (&base)[D + 2], T cx, const T (&fw)[D + 2],
-                                           const T (&fe)[D + 2], T cy, const T (&fs)[D + 2],
-                                           const T (&fn)[D + 2], T cz, const T (&zm)[D + 2],
-                                           const T (&zp)[D + 2], T (&un)[D + 2]) {
-    constexpr int NV = D + 2;
+// AddFlux of one cell (Eq. eqAddFlux), the axes summed in order:
+//     un = base + cx (fw - fe) [+ cy (fs - fn)] [+ cz (zm - zp)],
+// the fluxes of its low and high faces per axis, all in axis order; HAS_Y: an in-plane y axis
+// (faces fs, fn); HAS_M: a march axis (the last axis; faces zm, zp).
+template <class T, int NV, bool HAS_Y, bool HAS_M>
+__device__ __forceinline__ void add_fluxes(const T (&base)[NV], T cx, const T (&fw)[NV],
+                                           const T (&fe)[NV], T cy, const T (&fs)[NV],
+                                           const T (&fn)[NV], T cz, const T (&zm)[NV],
+                                           const T (&zp)[NV], T (&un)[NV]) {
     using P = Pairs<T, NV>;
     if constexpr (P::n > 0) {
         const F2 CX = f2_pack(cx, cx), CY = f2_pack(cy, cy), CZ = f2_pack(cz, cz);
@@ -208,16 +221,16 @@ __device__ __forceinline__ void add_fluxes(const T (&base)[D + 2], T cx, const T
             const int k = 2 * j;
             auto pk = [k](const float (&a)[NV]) { return f2_pack(a[k], a[k + 1]); };
             F2 sum = f2_mul(CX, f2_sub(pk(fw), pk(fe)));
-            if constexpr (D >= 2) sum = f2_fma(CY, f2_sub(pk(fs), pk(fn)), sum);
-            if constexpr (D == 3) sum = f2_fma(CZ, f2_sub(pk(zm), pk(zp)), sum);
+            if constexpr (HAS_Y) sum = f2_fma(CY, f2_sub(pk(fs), pk(fn)), sum);
+            if constexpr (HAS_M) sum = f2_fma(CZ, f2_sub(pk(zm), pk(zp)), sum);
             f2_unpack(f2_add(pk(base), sum), un[k], un[k + 1]);
         }
     }
 #pragma unroll
     for (int k = P::first_scalar; k < NV; ++k) {
         T sum = cx * (fw[k] - fe[k]);
-        if constexpr (D >= 2) sum = sum + cy * (fs[k] - fn[k]);
-        if constexpr (D == 3) sum = sum + cz * (zm[k] - zp[k]);
+        if constexpr (HAS_Y) sum = sum + cy * (fs[k] - fn[k]);
+        if constexpr (HAS_M) sum = sum + cz * (zm[k] - zp[k]);
         un[k] = base[k] + sum;
     }
 }
@@ -262,31 +275,35 @@ __device__ __forceinline__ void inplane_face(const T *__restrict__ sV, T *__rest
     C::put(sF, NF, f, Fa);
 }
 
-// Flux of the z-face between a column's cells z (lower) and z+1 (upper) from their primitive
-// states and MinBee slopes.  Returned normal-first: (mass, m_z, m_x, m_y, E).
-template <class T>
-__device__ __forceinline__ void fz_face(const T (&Vlo)[5], const T (&dlo)[5], const T (&Vhi)[5],
-                                        const T (&dhi)[5], const Gas<T> &G, T (&F)[5],
-                                        int riemann = 0) {
-    T L[5], R[5];
-    half_step<T, 5>(Vlo, dlo, T(1), L);
-    half_step<T, 5>(Vhi, dhi, T(-1), R);
-    const T vl[3] = {L[3], L[1], L[2]};
-    const T vr[3] = {R[3], R[1], R[2]};
-    hllc<T, 3, true>(L[0], vl, L[4], R[0], vr, R[4], G, F, riemann);
+// Flux of the march-axis face (z in dim 3, y for row tiles in dim 2) between a column's cells
+// at plane z (lower) and z+1 (upper) from their primitive states and MinBee slopes.  Returned
+// normal-first: (mass, m_normal, tangential momenta in axis order, E).
+template <class T, int D>
+__device__ __forceinline__ void march_face(const T (&Vlo)[D + 2], const T (&dlo)[D + 2],
+                                           const T (&Vhi)[D + 2], const T (&dhi)[D + 2],
+                                           const Gas<T> &G, T (&F)[D + 2], int riemann = 0) {
+    T L[D + 2], R[D + 2];
+    half_step<T, D + 2>(Vlo, dlo, T(1), L);
+    half_step<T, D + 2>(Vhi, dhi, T(-1), R);
+    T vl[D], vr[D];
+    vl[0] = L[D];
+    vr[0] = R[D];
+#pragma unroll
+    for (int b = 1; b < D; ++b) vl[b] = L[b], vr[b] = R[b];
+    hllc<T, D, true>(L[0], vl, L[D + 1], R[0], vr, R[D + 1], G, F, riemann);
 }
 
 // Shared-memory position (lx, ly) of halo task h of a BX x BY tile (the cross-shaped two-cell
 // halo: two columns left and right of the tile rows, two rows below and above the tile
 // columns); false if h is past the last task.
-template <int D, int BX, int BY>
+template <int IN, int BX, int BY>
 __device__ __forceinline__ bool halo_task(int h, int &lx, int &ly) {
-    constexpr int NH = (D >= 2) ? 4 * BY + 4 * BX : 4;
+    constexpr int NH = (IN >= 2) ? 4 * BY + 4 * BX : 4;
     if (h >= NH) {
         lx = ly = 0;
         return false;
     }
-    if constexpr (D >= 2) {
+    if constexpr (IN >= 2) {
         if (h < 4 * BY) {
             const int c = h & 3;
             ly = (h >> 2) + 2;
@@ -306,10 +323,10 @@ __device__ __forceinline__ bool halo_task(int h, int &lx, int &ly) {
 }
 
 // In-plane face task j of thread tid: shared base index o, stride s, normal axis a, face id.
-// Round 0: the x-face on the low side of the thread's cell; round 1 (dim >= 2): the y-face on
+// Round 0: the x-face on the low side of the thread's cell; round 1 (IN = 2): the y-face on
 // its low side; last round: the tile's high x-column (BY faces) and high y-row (BX faces), on
 // the lowest threads.  Rounds 0 and 1 give each warp one row of unit-stride faces.
-template <int D, int BX, int BY>
+template <int IN, int BX, int BY>
 __device__ __forceinline__ bool face_task(int tid, int j, int &o, int &s, int &a, int &id) {
     constexpr int HX = BX + 4;
     constexpr int NFX = (BX + 1) * BY;
@@ -318,7 +335,7 @@ __device__ __forceinline__ bool face_task(int tid, int j, int &o, int &s, int &a
     bool ok = true;
     if (j == 0) {
         c = tx, r = ty, a = 0;
-    } else if (D >= 2 && j == 1) {
+    } else if (IN >= 2 && j == 1) {
         c = tx, r = ty, a = 1;
     } else {
         const int e = tid;
@@ -326,12 +343,12 @@ __device__ __forceinline__ bool face_task(int tid, int j, int &o, int &s, int &a
             c = BX, r = e, a = 0;
         } else {
             c = e - BY, r = BY, a = 1;
-            ok = (D >= 2) && e < BX + BY;
+            ok = (IN >= 2) && e < BX + BY;
         }
     }
     if (!ok) c = r = a = 0;
     if (a == 0) {  // x-face between tile cells (c-1, r) and (c, r)
-        o = ((D >= 2) ? (r + 2) * HX : 0) + c;
+        o = ((IN >= 2) ? (r + 2) * HX : 0) + c;
         s = 1;
         id = r * (BX + 1) + c;
     } else {  // y-face between (c, r-1) and (c, r)
@@ -349,44 +366,41 @@ template <class T, int NT, int OCC = 2> struct MinBlocks {
     static constexpr int value = (sizeof(T) == 4) ? (v > 1 ? v : 1) : 1;
 };
 
-// STAGE: RK stage (1 or 2).  PF (staging depth, dim 3): 1 = the next z-plane's loads are
-// issued one plane ahead of their use, 0 = each plane is loaded when it is staged.  FUSED
-// (stage 2): 1 = the CFL signal and the next dt are reduced in this kernel's epilogue, 0 = left
-// to a separate CFL pass.  OCC: resident CTAs per SM the register budget targets.
-template <class T, int D, int BX, int BY, int STAGE, int PF = 1, bool FUSED = true, int OCC = 2>
-__global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY, OCC>::value))
-    stage_kernel(const StageArgs<T> A) {
+// One CTA's work: the tile at (x0, y0) of the in-plane axes, planes [zb, ze) of the march axis
+// (one plane without a march).  The AddFlux coefficients (c dt)/dr_a of the in-plane x and y
+// axes and of the march axis are cx, cy, cz.  CFL (stage 2): also return the CFL signal maximum
+// of the thread's new cells in smax and whether any was non-positive or non-finite in bad.
+// Uses the caller's dynamic shared memory (StageShape::smem_bytes).  A caller that runs it
+// twice in one CTA puts a barrier between the calls: the second call's first shared-memory
+// writes may hit planes the first call's last reads still use.
+template <class T, int D, int BX, int BY, int STAGE, int PF, bool CFL>
+__device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int x0, int y0, int zb, int ze,
+                                           unsigned char *smem_raw, T cx, T cy, T cz, T &smax,
+                                           bool &bad) {
     using S = StageShape<T, D, BX, BY>;
-    constexpr int NV = S::NV, NT = S::NT, HX = S::HX, PL = S::PL;
+    using GM = Geom<D, BY>;
+    constexpr int NV = S::NV, NT = S::NT, HX = S::HX, PL = S::PL, IN = GM::IN, MA = GM::MA;
+    constexpr bool MARCH = GM::march;
     constexpr int NFX = S::NFX, NF = S::NF, HPT = S::HPT, FPT = S::FPT;
-    // shared memory: two primitive planes and two flux planes, alternating between z-planes
-    // so that one barrier per plane suffices
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    // two primitive planes and two flux planes, alternating between planes so that one barrier
+    // per plane suffices
     T *const sV0 = reinterpret_cast<T *>(smem_raw);
     T *const sV1 = sV0 + NV * PL;
     T *const sF0 = sV1 + NV * PL;
     T *const sF1 = sF0 + NV * NF;
-    T *const sRed = sF1 + NV * NF;
-
-    Ctrl *ctrl = A.ctrl;
-    const double dt = __ldcg(&ctrl->dt);
-    if (!(dt > 0.0)) return;  // uniform over the grid: no step to take
-    // (c dt)/dr_a, computed once per step in FP64 by the dt finaliser
-    const T cx = T(__ldcg(&ctrl->coef[STAGE - 1][0]));
-    const T cy = (D >= 2) ? T(__ldcg(&ctrl->coef[STAGE - 1][1])) : T(0);
-    const T cz = (D == 3) ? T(__ldcg(&ctrl->coef[STAGE - 1][2])) : T(0);
     const Gas<T> G = A.gas;
     const bool order2 = A.order == 2;
 
     const int tid = threadIdx.x;
     const int tx = tid % BX, ty = tid / BX;
-    const int nx = A.n[0], ny = A.n[1], nz = A.n[2];
-    const int nxy = nx * ny;
-    const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
+    const int nx = A.n[0];
+    const int ny = (IN >= 2) ? A.n[1] : 1;             // in-plane y extent
+    const int nz = MARCH ? A.n[MA] : 1;                // march extent
+    const int pstride = nx * ny;                       // cells per plane
     const int x = x0 + tx, y = y0 + ty;
     const bool active = (x < nx) && (y < ny);
     const int own_off = remap(y, ny, A.periodic[1]) * nx + remap(x, nx, A.periodic[0]);
-    const int own_s = (D >= 2) ? (ty + 2) * HX + (tx + 2) : (tx + 2);
+    const int own_s = (IN >= 2) ? (ty + 2) * HX + (tx + 2) : (tx + 2);
 
     // halo cells of this thread: plane offset and shared index.  Halo work goes to the
     // highest threads, the tile's extra row/column of faces to the lowest.
@@ -395,9 +409,9 @@ __global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY, OCC>::value))
 #pragma unroll
     for (int j = 0; j < HPT; ++j) {
         int lx, ly;
-        h_ok[j] = halo_task<D, BX, BY>((NT - 1 - tid) + j * NT, lx, ly);
+        h_ok[j] = halo_task<IN, BX, BY>((NT - 1 - tid) + j * NT, lx, ly);
         const int xg = remap(x0 + lx - 2, nx, A.periodic[0]);
-        const int yg = (D >= 2) ? remap(y0 + ly - 2, ny, A.periodic[1]) : 0;
+        const int yg = (IN >= 2) ? remap(y0 + ly - 2, ny, A.periodic[1]) : 0;
         h_off[j] = yg * nx + xg;
         h_s[j] = ly * HX + lx;
     }
@@ -406,14 +420,12 @@ __global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY, OCC>::value))
     int f_o[FPT], f_s[FPT], f_a[FPT], f_id[FPT];
     bool f_ok[FPT];
 #pragma unroll
-    for (int j = 0; j < FPT; ++j) f_ok[j] = face_task<D, BX, BY>(tid, j, f_o[j], f_s[j], f_a[j], f_id[j]);
+    for (int j = 0; j < FPT; ++j) f_ok[j] = face_task<IN, BX, BY>(tid, j, f_o[j], f_s[j], f_a[j], f_id[j]);
 
-    const int zb = (D == 3) ? blockIdx.z * A.march : 0;
-    const int ze = (D == 3) ? min(zb + A.march, nz) : 1;
-    const int pz = A.periodic[2];
+    const int pz = MARCH ? A.periodic[MA] : 1;
 
     auto load_u = [&](T (&u)[NV], int zr, int off) {
-        const int i = zr * nxy + off;
+        const int i = zr * pstride + off;
 #pragma unroll
         for (int k = 0; k < NV; ++k) u[k] = __ldg(A.uin[k] + i);
     };
@@ -431,13 +443,13 @@ __global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY, OCC>::value))
         }
     };
 
-    // register pipeline along z (dim 3): V(z), V(z+1), slope at z, flux of face z - 1/2,
+    // register pipeline along the march axis: V(z), V(z+1), slope at z, flux of face z - 1/2,
     // raw U of plane z+2 (own column) and of the next plane's halo
     T Vc[NV], Vn[NV], dzc[NV], Fzm[NV];
     T pown[NV];
     T phalo[HPT][NV];
 
-    if constexpr (D == 3) {
+    if constexpr (MARCH) {
         T u[NV], Vm2[NV], Vm1[NV], dzm[NV];
         load_u(u, remap(zb - 2, nz, pz), own_off);
         prim_of_cons<T, D>(u, Vm2, G);
@@ -449,7 +461,7 @@ __global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY, OCC>::value))
         prim_of_cons<T, D>(u, Vn, G);
         minbee_slopes<T, NV>(Vm2, Vm1, Vc, order2, dzm);
         minbee_slopes<T, NV>(Vm1, Vc, Vn, order2, dzc);
-        fz_face(Vm1, dzm, Vc, dzc, G, Fzm, A.riemann);
+        march_face<T, D>(Vm1, dzm, Vc, dzc, G, Fzm, A.riemann);
         if constexpr (PF == 1) load_u(pown, remap(zb + 2, nz, pz), own_off);
     } else {
         T u[NV];
@@ -458,9 +470,9 @@ __global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY, OCC>::value))
     }
 #pragma unroll
     for (int j = 0; j < HPT; ++j)
-        if (h_ok[j]) load_u(phalo[j], (D == 3) ? remap(zb, nz, pz) : 0, h_off[j]);
+        if (h_ok[j]) load_u(phalo[j], MARCH ? remap(zb, nz, pz) : 0, h_off[j]);
     stage_plane(sV0, Vc, phalo);
-    if constexpr (D == 3 && PF == 1) {
+    if constexpr (MARCH && PF == 1) {
         if (zb + 1 < ze) {
 #pragma unroll
             for (int j = 0; j < HPT; ++j)
@@ -468,9 +480,6 @@ __global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY, OCC>::value))
         }
     }
     __syncthreads();
-
-    T smax = T(0);
-    bool bad = false;
 
     for (int z = zb; z < ze; ++z) {
         const bool odd = ((z - zb) & 1) != 0;
@@ -480,12 +489,12 @@ __global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY, OCC>::value))
         // U_base of the plane, consumed after the barrier
         T base[NV];
         {
-            const int i = ((D == 3) ? z * nxy : 0) + (active ? y * nx + x : 0);
+            const int i = (MARCH ? z * pstride : 0) + (active ? y * nx + x : 0);
 #pragma unroll
             for (int k = 0; k < NV; ++k) base[k] = active ? A.ubase[k][i] : T(0);
         }
         T Vnn[NV];
-        if constexpr (D == 3) {
+        if constexpr (MARCH) {
             if constexpr (PF == 0) load_u(pown, remap(z + 2, nz, pz), own_off);
             prim_of_cons<T, D>(pown, Vnn, G);  // V(z+2)
             if constexpr (PF == 1) {
@@ -499,11 +508,11 @@ __global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY, OCC>::value))
             if (f_ok[j])
                 inplane_face<T, D, PL, NF>(sVc, sF, f_o[j], f_s[j], f_a[j], f_id[j], G, A.order,
                                            A.riemann);
-        // z-face above this column
+        // march-axis face above this column
         T Fzp[NV], dzn[NV];
-        if constexpr (D == 3) {
+        if constexpr (MARCH) {
             minbee_slopes<T, NV>(Vc, Vn, Vnn, order2, dzn);
-            fz_face(Vc, dzc, Vn, dzn, G, Fzp, A.riemann);
+            march_face<T, D>(Vc, dzc, Vn, dzn, G, Fzp, A.riemann);
             // stage plane z+1 into the other buffer, prefetch the halo of plane z+2
             if (z + 1 < ze) {
                 if constexpr (PF == 0) {
@@ -527,22 +536,24 @@ __global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY, OCC>::value))
             T un[NV], fw[NV], fe[NV], fs[NV], fn[NV];
             Cells<T, NV>::get(sF, NF, fxl, fw);
             Cells<T, NV>::get(sF, NF, fxl + 1, fe);
-            if constexpr (D >= 2) {
+            if constexpr (IN >= 2) {
                 Cells<T, NV>::get(sF, NF, fyb, fs);
                 Cells<T, NV>::get(sF, NF, fyb + BX, fn);
             }
-            T zm[NV], zp[NV];  // z fluxes in axis order (they come normal-first: mass, m_z, m_x, m_y, E)
+            // march-axis fluxes in axis order (they come normal-first: mass, m_normal, the
+            // tangential momenta in axis order, E)
+            T zm[NV], zp[NV];
 #pragma unroll
             for (int k = 0; k < NV; ++k) {
-                const int kk = (D < 3 || k == 0 || k == NV - 1) ? k : (k == 3 ? 1 : k + 1);
-                zm[k] = (D == 3) ? Fzm[kk] : T(0);
-                zp[k] = (D == 3) ? Fzp[kk] : T(0);
+                const int kk = (!MARCH || k == 0 || k == NV - 1) ? k : (k == D ? 1 : k + 1);
+                zm[k] = MARCH ? Fzm[kk] : T(0);
+                zp[k] = MARCH ? Fzp[kk] : T(0);
             }
-            add_fluxes<T, D>(base, cx, fw, fe, cy, fs, fn, cz, zm, zp, un);
-            const int i = ((D == 3) ? z * nxy : 0) + y * nx + x;
+            add_fluxes<T, NV, (IN >= 2), MARCH>(base, cx, fw, fe, cy, fs, fn, cz, zm, zp, un);
+            const int i = (MARCH ? z * pstride : 0) + y * nx + x;
 #pragma unroll
             for (int k = 0; k < NV; ++k) A.uout[k][i] = un[k];
-            if constexpr (STAGE == 2 && FUSED) {
+            if constexpr (STAGE == 2 && CFL) {
                 // CFL signal of the new state: sum_a (|v_a| + c_s) / dr_a
                 T v[NV];
                 prim_of_cons<T, D>(un, v, G);
@@ -560,7 +571,7 @@ __global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY, OCC>::value))
                 bad |= !(v[0] > T(0)) || !(v[NV - 1] > T(0));
             }
         }
-        if constexpr (D == 3) {
+        if constexpr (MARCH) {
 #pragma unroll
             for (int k = 0; k < NV; ++k) {
                 Vc[k] = Vn[k];
@@ -570,8 +581,36 @@ __global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY, OCC>::value))
             }
         }
     }
+}
 
-    if constexpr (STAGE == 2 && FUSED) reduce_signal_and_finalize<T, NT>(ctrl, smax, bad, true, sRed);
+// STAGE: RK stage (1 or 2).  PF (staging depth, march tiles): 1 = the next plane's loads are
+// issued one plane ahead of their use, 0 = each plane is loaded when it is staged.  FUSED
+// (stage 2): 1 = the CFL signal and the next dt are reduced in this kernel's epilogue, 0 = left
+// to a separate CFL pass.  OCC: resident CTAs per SM the register budget targets.
+template <class T, int D, int BX, int BY, int STAGE, int PF = 1, bool FUSED = true, int OCC = 2>
+__global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY, OCC>::value))
+    stage_kernel(const StageArgs<T> A) {
+    using S = StageShape<T, D, BX, BY>;
+    using GM = Geom<D, BY>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *const sRed = reinterpret_cast<T *>(smem_raw) + 2 * S::NV * S::PL + 2 * S::NV * S::NF;
+
+    Ctrl *ctrl = A.ctrl;
+    const double dt = __ldcg(&ctrl->dt);
+    if (!(dt > 0.0)) return;  // uniform over the grid: no step to take
+    // (c dt)/dr_a, computed once per step in FP64 by the dt finaliser
+    const T cx = T(__ldcg(&ctrl->coef[STAGE - 1][0]));
+    const T cy = (GM::IN >= 2) ? T(__ldcg(&ctrl->coef[STAGE - 1][1])) : T(0);
+    const T cz = GM::march ? T(__ldcg(&ctrl->coef[STAGE - 1][GM::MA])) : T(0);
+    const int x0 = blockIdx.x * BX;
+    const int y0 = (GM::IN >= 2) ? blockIdx.y * BY : 0;
+    const int zb = GM::march ? blockIdx.z * A.march : 0;
+    const int ze = GM::march ? min(zb + A.march, A.n[GM::MA]) : 1;
+    T smax = T(0);
+    bool bad = false;
+    stage_tile<T, D, BX, BY, STAGE, PF, (STAGE == 2 && FUSED)>(A, x0, y0, zb, ze, smem_raw, cx, cy,
+                                                                 cz, smax, bad);
+    if constexpr (STAGE == 2 && FUSED) reduce_signal_and_finalize<T, S::NT>(ctrl, smax, bad, true, sRed);
 }
 
 }  // namespace hydro

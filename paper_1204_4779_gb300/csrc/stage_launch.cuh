@@ -39,10 +39,11 @@ template <class T, int D, int BX, int BY, int PF, int OCC> struct StageKernels {
 template <class T, int D, int BX, int BY, int PF, int OCC = 2>
 static cudaError_t launch_stage_pf(const StageLaunch &L, const StageArgs<T> &A, cudaStream_t st) {
     using S = StageShape<T, D, BX, BY>;
+    using GM = Geom<D, BY>;
     using K = StageKernels<T, D, BX, BY, PF, OCC>;
     const dim3 grid((unsigned)((A.n[0] + BX - 1) / BX),
-                    (unsigned)((D >= 2) ? (A.n[1] + BY - 1) / BY : 1),
-                    (unsigned)((D == 3) ? (A.n[2] + A.march - 1) / A.march : 1));
+                    (unsigned)((GM::IN >= 2) ? (A.n[1] + BY - 1) / BY : 1),
+                    (unsigned)(GM::march ? (A.n[GM::MA] + A.march - 1) / A.march : 1));
     const size_t smem = S::smem_bytes;
     if (L.stage == 1)
         K::s1<<<grid, S::NT, smem, st>>>(A);
@@ -71,11 +72,11 @@ static cudaError_t run_or_prepare(const StageLaunch &L, cudaStream_t st, bool pr
     return launch_stage_pf<T, D, BX, BY, PF, OCC>(L, make_stage_args<T>(L), st);
 }
 
-// Both staging depths and both occupancy targets exist only in dim 3 (the z-march; dims 1 and
-// 2 have one plane and small register needs).
+// Both staging depths and both occupancy targets exist only for marching tiles (dim 3, and the
+// row tiles of dim 2); one-plane tiles have nothing to look ahead to and small register needs.
 template <class T, int D, int BX, int BY, bool BOTH_PF>
 static cudaError_t dispatch_tile(const StageLaunch &L, cudaStream_t st, bool prepare_only) {
-    if constexpr (BOTH_PF && D == 3) {
+    if constexpr (BOTH_PF && Geom<D, BY>::march) {
         const bool occ3 = L.occupancy == 3;
         if (L.prefetch == 0)
             return occ3 ? run_or_prepare<T, D, BX, BY, 0, 3>(L, st, prepare_only)

@@ -334,12 +334,14 @@ class BatchSolver:
     """Many independent 2D grids of uneven size advanced together (hydro_batch_* of the C ABI).
 
     shapes: sequence of (nx, ny); every grid is its own unit square with its own CFL dt.
+    tile: (bx, by) of the batch kernels, default (32, 8); (bx, 1) selects row tiles, which march
+    along y through `march` rows per work item (default 32).
     The packed state is a tensor of shape (4, total_cells): plane k holds grid g's cells at
     [offsets[g], offsets[g+1]), x fastest.
     """
 
     def __init__(self, shapes, gamma: float, bc="periodic", dtype=torch.float32, cfl: float = 0.4,
-                 tile=None, device=None):
+                 tile=None, march: int = 0, device=None):
         self.lib = load_library()
         self.shapes = [(int(a), int(b)) for a, b in shapes]
         self.n = len(self.shapes)
@@ -351,7 +353,7 @@ class BatchSolver:
                                      for b in bc])
         nx = (ctypes.c_int64 * self.n)(*[s[0] for s in self.shapes])
         ny = (ctypes.c_int64 * self.n)(*[s[1] for s in self.shapes])
-        var = Variant(int(tile[0]), int(tile[1]), 0, 0, 0, 0) if tile else None
+        var = Variant(int(tile[0]), int(tile[1]), int(march), 0, 0, 0) if tile else None
         nbytes = ctypes.c_size_t()
         _check(self.lib.hydro_batch_workspace_bytes(self.n, nx, ny, _prec(dtype),
                                                     ctypes.byref(var) if var else None,

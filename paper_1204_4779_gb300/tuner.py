@@ -1,10 +1,13 @@
 """Variant tuner of the stage kernels: the paper's evolutionary search (arXiv:1204.4779, section 3)
 and a learned cost model that ranks candidates before they are benchmarked.
 
-Variant space (the genome).  The C ABI's hydro_variant_t: in-plane tile shape, z-march length
-(cells each thread updates per stage: the threads-per-cell axis), fusion split (dt reduction in
-RK stage 2's epilogue, or a separate CFL pass) and staging depth (next z-plane's loads issued
-one plane ahead, or at use).  Every variant computes the same step; only speed differs.
+Variant space (the genome).  The C ABI's hydro_variant_t: tile shape, march length (cells each
+thread updates per stage: the threads-per-cell axis), fusion split (dt reduction in RK stage 2's
+epilogue, or a separate CFL pass), staging depth (next plane's loads issued one plane ahead, or
+at use) and register budget.  In 3D every tile marches along z; in 2D the row tiles (tile_y = 1)
+march along y and the one-plane tiles have no march, staging or budget genes (their genomes are
+kept canonical so that each variant has one genome).  Every variant computes the same step;
+only speed differs.
 
 Score.  As in the paper, an individual is benchmarked several times and scored by the mean and
 spread of its cell-updates per second (cups); an individual whose run fails or leaves a
@@ -38,13 +41,18 @@ import numpy as np
 
 TILES = {
     3: [(32, 8), (32, 4), (64, 4), (16, 16), (32, 16), (16, 8)],
-    2: [(32, 8), (64, 4), (16, 16), (32, 16)],
+    2: [(32, 8), (64, 4), (16, 16), (32, 16), (64, 1), (128, 1), (256, 1)],
     1: [(128, 1), (256, 1)],
 }
 MARCHES = [4, 8, 16, 32, 64, 128, 256]
 SPLITS = [2, 1]   # hydro_variant_t.split: 2 = fused dt reduction, 1 = separate CFL pass
 STAGINGS = [1, 2]
 OCCUPANCIES = [2, 3]
+
+
+def marching(dim: int, tile) -> bool:
+    """Tiles that march: every 3D tile, and the 2D row tiles."""
+    return dim == 3 or (dim == 2 and tile[1] == 1)
 
 
 @dataclass(frozen=True)
@@ -54,40 +62,58 @@ class Space:
 
     @property
     def genes(self):
-        if self.dim == 3:
-            return [("tile", TILES[3]), ("march", MARCHES), ("split", SPLITS), ("staging", STAGINGS),
-                    ("occupancy", OCCUPANCIES)]
+        if self.dim >= 2:
+            return [("tile", TILES[self.dim]), ("march", MARCHES), ("split", SPLITS),
+                    ("staging", STAGINGS), ("occupancy", OCCUPANCIES)]
         return [("tile", TILES[self.dim]), ("split", SPLITS)]
 
     @property
     def sizes(self):
         return [len(v) for _, v in self.genes]
 
+    def canonical(self, genome):
+        """The genome with the genes its tile does not use set to their first values."""
+        if self.dim == 2 and not marching(2, TILES[2][genome[0]]):
+            return (genome[0], 0, genome[2], 0, 0)
+        return tuple(genome)
+
     def all_genomes(self):
-        return list(itertools.product(*[range(n) for n in self.sizes]))
+        seen, out = set(), []
+        for g in itertools.product(*[range(n) for n in self.sizes]):
+            c = self.canonical(g)
+            if c not in seen:
+                seen.add(c)
+                out.append(c)
+        return out
 
     def variant(self, genome) -> dict:
         v = {name: vals[g] for (name, vals), g in zip(self.genes, genome)}
+        if self.dim == 2 and not marching(2, v["tile"]):
+            v = {"tile": v["tile"], "split": v["split"]}
         return v
 
     def default_genome(self):
-        d = {"tile": TILES[self.dim][0], "march": 64, "split": 2 if self.dim == 3 else 1,
-             "staging": 1, "occupancy": 3}
+        if self.dim == 3:
+            d = {"tile": (32, 8), "march": 64, "split": 2, "staging": 1, "occupancy": 3}
+        elif self.dim == 2:
+            d = {"tile": (256, 1), "march": 16, "split": 2, "staging": 1, "occupancy": 3}
+        else:
+            d = {"tile": (128, 1), "split": 1}
         return tuple(vals.index(d[name]) for name, vals in self.genes)
 
     def random_genome(self, rng):
-        return tuple(int(rng.integers(n)) for n in self.sizes)
+        return self.canonical(tuple(int(rng.integers(n)) for n in self.sizes))
 
 
 def features(space: Space, genome, shape) -> np.ndarray:
-    """Input vector of the cost model: one-hot tile, one-hot log2 march, split and staging bits
-    (3D), the grid dimension and the log2 sizes of the grid."""
+    """Input vector of the cost model: one-hot tile, one-hot march (marching tiles), split,
+    staging and budget bits, the grid dimension and the log2 sizes of the grid."""
     v = space.variant(genome)
     f = []
     for d in (1, 2, 3):
         tiles = TILES[d]
         f += [1.0 if (space.dim == d and v["tile"] == t) else 0.0 for t in tiles]
-    f += [1.0 if (space.dim == 3 and v.get("march") == m) else 0.0 for m in MARCHES]
+    f += [1.0 if v.get("march") == m else 0.0 for m in MARCHES]
     f.append(1.0 if v.get("split", 2) == 1 else 0.0)
     f.append(1.0 if v.get("staging", 1) == 2 else 0.0)
     f.append(1.0 if v.get("occupancy", 2) == 3 else 0.0)
@@ -261,7 +287,7 @@ class Evolution:
     def birth(self, max_retries: int = 200):
         """A genome not yet in the database (or None when the space is exhausted)."""
         sizes = self.space.sizes
-        if len(self.scores) >= int(np.prod(sizes)):
+        if len(self.scores) >= len(self.space.all_genomes()):
             return None
         T = self.temperature()
         for _ in range(max_retries):
@@ -286,8 +312,10 @@ class Evolution:
                 c = self.draw(T, exclude=(a, b))
                 base, sec, prim = sorted((a, b, c), key=lambda k: self.scores[k][0])
                 child = triangulate(base, sec, prim)
-            if child is not None and child not in self.scores:
-                return child
+            if child is not None:
+                child = self.space.canonical(child)
+                if child not in self.scores:
+                    return child
             T *= 1.2
         # exhausted retries: any unseen genome
         unseen = [g for g in self.space.all_genomes() if g not in self.scores]
@@ -513,11 +541,58 @@ def compare(db: DB, target, ga_evals: int, rng_seed: int, reps: int = 10, steps:
     return out
 
 
+BATCH_VARIANTS = ([((32, 8), 0), ((16, 16), 0)] +
+                  [(t, m) for t in ((32, 1), (64, 1), (128, 1)) for m in (8, 16, 32, 64)])
+
+
+def sweep_batched(reps: int = 3, steps: int = 10, seed: int = 1204477904):
+    """Cell-updates/s of the batched configuration (4096 grids, sides log-uniform on [32, 512],
+    seeded smooth data, FP32) for each (tile, march) of BATCH_VARIANTS: best of `reps` runs of
+    `steps` graph-replayed steps, CUDA events around each run."""
+    import torch
+
+    from . import hydro, inputs
+    shapes = [tuple(int(v) for v in s) for s in inputs.batch_shapes()]
+    P = np.concatenate([inputs.batch_grid(nx, ny, seed, i).reshape(4, -1)
+                        for i, (nx, ny) in enumerate(shapes)], 1)
+    U64 = hydro.prim_to_cons(torch.from_numpy(P).cuda().view(4, 1, -1), 1.4).view(4, -1)
+    out = []
+    for tile, march in BATCH_VARIANTS:
+        B = hydro.BatchSolver(shapes, 1.4, dtype=torch.float32, tile=tile, march=march)
+        U = U64.float().contiguous()
+        B.step(U, steps)  # capture the graphs
+        best = None
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            B.step(U, steps, sync=False)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        out.append({"tile": list(tile), "march": march,
+                    "cups": U.shape[1] * steps / (best * 1e-3)})
+        B.close()
+    return sorted(out, key=lambda r: -r["cups"])
+
+
+def sweep(shape, reps: int = 5, steps: int = 20):
+    """Every variant of the grid's space (Benchmark: `reps` runs of `steps` steps from the same
+    initial state), sorted by mean cell-updates/s."""
+    bench = Benchmark(shape, reps=reps, steps=steps)
+    recs = [bench(g) for g in bench.space.all_genomes()]
+    return sorted(({"variant": bench.space.variant(r.genome), "cups": r.mu, "sigma": r.sigma,
+                    "ok": r.ok} for r in recs), key=lambda d: -d["cups"])
+
+
 def main(argv=None):
     import argparse
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
-    ap.add_argument("command", choices=("collect", "compare"))
-    ap.add_argument("--db", required=True)
+    ap.add_argument("command", choices=("collect", "compare", "sweep"))
+    ap.add_argument("--db", default=None)
+    ap.add_argument("--shape", type=int, nargs="+", default=None,
+                    help="sweep: the grid (nx [ny [nz]]); omitted: the batched configuration")
     ap.add_argument("--per-shape", type=int, default=150)
     ap.add_argument("--ga-evals", type=int, default=60)
     ap.add_argument("--seed", type=int, default=1204477905)
@@ -525,6 +600,16 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)
+    if a.command == "sweep":
+        res = sweep(tuple(a.shape), a.reps, a.steps) if a.shape else sweep_batched(a.reps, a.steps)
+        text = json.dumps({"shape": a.shape or "batched 4096 grids", "results": res}, indent=1)
+        print(text)
+        if a.out:
+            with open(a.out, "w") as f:
+                f.write(text + "\n")
+        return
+    if not a.db:
+        ap.error("--db is required for collect and compare")
     db = DB(a.db)
     if a.command == "collect":
         collect(db, TRAIN_SHAPES, a.per_shape, np.random.default_rng(a.seed), a.reps, a.steps)

@@ -144,3 +144,53 @@ def test_full_batched_config_fp32():
         assert e <= 1e-4, (g, shapes[g], e)
         assert abs(t[g] - to) <= 1e-5 * to
     print(f"batched 4096 grids FP32: worst sampled L1(rho) rel = {worst:.3e}")
+
+
+# ---- row tiles: a work item is a strip of x columns marching along y -----------------------
+
+@pytest.mark.parametrize("march", [7, 32])
+@pytest.mark.parametrize("bc", [("periodic", (0, 0)), ("outflow", (1, 1))])
+def test_row_tiles_fp64_match_oracle_per_grid(bc, march):
+    Vs = _data(SMALL, 9)
+    B = hydro.BatchSolver(SMALL, G, bc=bc[0], dtype=F64, cfl=0.4, tile=(64, 1), march=march)
+    U = _packed(B, Vs, F64)
+    t, steps = B.step(U, 25)
+    assert steps == [25] * len(SMALL)
+    for g, V in enumerate(Vs):
+        O, to, so, _ = _oracle(V, bc[1], 25)
+        Gg = B.grid_view(U, g).cpu().numpy()
+        assert t[g] == to, (g, t[g], to)
+        assert max_rel_err(Gg, O) <= 1e-10, (g, march)
+
+
+@pytest.mark.parametrize("tile", [(32, 1), (64, 1), (128, 1)])
+def test_row_tiles_fp32_l1(tile):
+    Vs = _data(SMALL, 10)
+    B = hydro.BatchSolver(SMALL, G, dtype=F32, tile=tile, march=16)
+    U = _packed(B, Vs, F32)
+    t, steps = B.step(U, 40)
+    for g, V in enumerate(Vs):
+        O, to, _, _ = _oracle(V, (0, 0), 40)
+        Gg = B.grid_view(U, g).double().cpu().numpy()
+        assert l1_rel(Gg[0], O[0]) <= 1e-5, (tile, g)
+        assert abs(t[g] - to) <= 1e-5 * to
+
+
+def test_row_tiles_graph_and_direct_launches_agree():
+    Vs = _data(SMALL, 13)
+    A = hydro.BatchSolver(SMALL, G, dtype=F32, tile=(64, 1), march=16)
+    UA = _packed(A, Vs, F32)
+    A.step(UA, 30)
+    P = hydro.BatchSolver(SMALL, G, dtype=F32, tile=(64, 1), march=16)
+    P.set_profiling(True)
+    UP = _packed(P, Vs, F32)
+    P.step(UP, 30)
+    assert torch.equal(UA, UP)
+
+
+def test_row_tiles_reject_unsupported():
+    from paper_1204_4779_gb300.hydro import HydroError
+    with pytest.raises(HydroError):
+        hydro.BatchSolver(SMALL, G, dtype=F64, tile=(128, 1))
+    with pytest.raises(HydroError):
+        hydro.BatchSolver(SMALL, G, dtype=F32, tile=(64, 1), march=-1)

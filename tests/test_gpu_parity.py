@@ -169,3 +169,55 @@ def test_every_fp32_1d_tile(tile):
     V = inputs.smooth((300,), seed=13)
     e, _, _ = _l1_32(V, 1.4, (0,), 50, variant=dict(tile=tile))
     assert e <= 2e-6
+
+
+# ---- dim-2 row tiles: a row of x cells per CTA marching along y ---------------------------
+
+@pytest.mark.parametrize("march", [5, 32])
+@pytest.mark.parametrize("bc", [(0, 0), (1, 0), (0, 1)])
+def test_row_tiles_fp64_ragged(bc, march):
+    """Row tiles (128 x 1) marching along y: ragged x (100 = one partial tile) and ragged march
+    chunks (77 rows), every boundary combination, FP64 <= 1e-10."""
+    V = inputs.kh_2d(100, seed=1204477901, ny=77)
+    _compare64(V, 5.0 / 3.0, bc, 0.4, 30, variant=dict(tile=(128, 1), march=march))
+
+
+@pytest.mark.parametrize("split", [1, 2])
+@pytest.mark.parametrize("shape", [(300, 7), (7, 300), (70, 1), (1, 45)])
+def test_row_tiles_fp64_degenerate_shapes(shape, split):
+    """Narrow, tall, one-row and one-column grids through row tiles, both dt reductions."""
+    V = inputs.smooth(shape, seed=21)
+    _compare64(V, 1.4, (0, 1), 0.4, 12, variant=dict(tile=(128, 1), march=16, split=split))
+
+
+@pytest.mark.parametrize("order,riemann", [(1, 0), (2, 1)])
+def test_row_tiles_scheme_options_fp64(order, riemann):
+    V = inputs.smooth((70, 45), seed=22)
+    G, tg, sg = gpu_run(V, 1.4, (0, 0), F64, 0.4, 20, variant=dict(tile=(128, 1), march=8),
+                        scheme=(order, riemann))
+    O, to, so, _ = oracle_run(V, 1.4, (0, 0), 0.4, 20, order=order, riemann=riemann)
+    assert sg == so and tg == to
+    assert max_rel_err(G, O) <= 1e-10
+
+
+def test_row_tiles_fp64_kh_1024_full_config():
+    """The 1024^2 shear layer (gamma 5/3, periodic, 100 steps) through FP64 row tiles."""
+    V = inputs.kh_2d(1024, seed=1204477901)
+    _compare64(V, 5.0 / 3.0, (0, 0), 0.4, 100, variant=dict(tile=(128, 1), march=32))
+
+
+@pytest.mark.parametrize("occupancy", [2, 3])
+@pytest.mark.parametrize("staging", [1, 2])
+@pytest.mark.parametrize("split", [1, 2])
+@pytest.mark.parametrize("tile", [(64, 1), (128, 1), (256, 1)])
+def test_every_fp32_row_tile_variant(tile, split, staging, occupancy):
+    V = inputs.smooth((300, 77), seed=23)
+    e, _, _ = _l1_32(V, 1.4, (1, 0), 20, variant=dict(tile=tile, march=9, split=split,
+                                                      staging=staging, occupancy=occupancy))
+    assert e <= 2e-6
+
+
+def test_row_tiles_fp32_kh_1024_full_config():
+    V = inputs.kh_2d(1024, seed=1204477901)
+    e, _, _ = _l1_32(V, 5.0 / 3.0, (0, 0), 100, variant=dict(tile=(128, 1), march=32))
+    assert e <= 1e-4

@@ -20,6 +20,11 @@ def test_benchmark_records():
     assert r.ok and r.mu > 0 and r.sigma >= 0
     r2 = b((1, 2, 1, 1, 1))
     assert r2.ok and r2.genome == (1, 2, 1, 1, 1)
+    # 2D: the default row tile and a one-plane tile
+    b2 = T.Benchmark((300, 77), reps=3, steps=2)
+    for g in (b2.space.default_genome(), b2.space.all_genomes()[0]):
+        r = b2(g)
+        assert r.ok and r.mu > 0, b2.space.variant(g)
 
 
 @pytest.mark.slow

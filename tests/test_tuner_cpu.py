@@ -31,6 +31,16 @@ def test_space_and_features():
     f2 = T.features(T.Space(2), T.Space(2).default_genome(), (2048, 2048))
     assert f2.shape == (T.N_FEATURES,) and not np.array_equal(f, f2)
     assert len({tuple(T.features(s3, g, (64, 64, 64))) for g in s3.all_genomes()}) == 336
+    # 2D: four one-plane tiles (tile and split genes only) and three row tiles with every gene
+    s2 = T.Space(2)
+    g2 = s2.all_genomes()
+    assert len(g2) == 4 * 2 + 3 * 7 * 2 * 2 * 2 and len(set(g2)) == len(g2)
+    assert s2.variant(s2.default_genome()) == {"tile": (256, 1), "march": 16, "split": 2,
+                                               "staging": 1, "occupancy": 3}
+    assert all(set(s2.variant(g)) == {"tile", "split"} for g in g2 if s2.variant(g)["tile"][1] > 1)
+    assert len({tuple(T.features(s2, g, (64, 64))) for g in g2}) == len(g2)
+    rng = np.random.default_rng(3)
+    assert all(s2.random_genome(rng) in set(g2) for _ in range(200))
 
 
 def test_draw_prefers_high_scores_at_low_temperature():
