@@ -340,10 +340,25 @@ def run_ours(args):
         barrier()
         e2e_value, _ = aggregate_replicas(e0.elapsed_time(e1), ncell * args.e2e_steps, device=dev)
         nbytes = nv * 4 * ncell
+        # the CPU-GPU link alone: the same state copied each way (pinned memory, CUDA events)
+        link = {}
+        for name, dst, src in (("h2d_gbs", dev_state, host), ("d2h_gbs", host, dev_state)):
+            best = None
+            for _ in range(3):
+                torch.cuda.synchronize()
+                e0.record()
+                dst.copy_(src, non_blocking=True)
+                e1.record()
+                torch.cuda.synchronize()
+                t = e0.elapsed_time(e1)
+                best = t if best is None else min(best, t)
+            link[name] = nbytes / (best * 1e-3) / 1e9
         e2e = {"value": e2e_value,
                "unit": "cell-updates/s", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
                "steps": args.e2e_steps,
-               "call": "hydro_step_host: pinned host state in, 1 RK step, host state out"}
+               "call": "hydro_step_host: pinned host state in, 1 RK step, host state out",
+               "link": dict(link, note="plain copies of the state over the CPU-GPU link; the "
+                                       "step's copies alone take nbytes/h2d + nbytes/d2h")}
 
     # the kernel's real limit: instruction issue (4 warp-instructions per clock per SM)
     clocks = clk.summary()

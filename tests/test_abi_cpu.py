@@ -98,6 +98,11 @@ def test_variant_table():
     assert hydro.variant_supported(torch.float32, 3, (32, 8), 64)
     assert hydro.variant_supported(torch.float64, 2, (32, 8))
     assert not hydro.variant_supported(torch.float32, 3, (8, 8))
+    # row tiles (2D)
+    assert hydro.variant_supported(torch.float32, 2, (256, 1), 16, occupancy=3)
+    assert hydro.variant_supported(torch.float64, 2, (128, 1), 8)
+    assert not hydro.variant_supported(torch.float64, 2, (256, 1))
+    assert not hydro.variant_supported(torch.float32, 2, (32, 8), occupancy=3)
     assert not hydro.variant_supported(torch.float32, 4)
     assert hydro.variant_supported(torch.float32, 3, (16, 8), 32, split=1, staging=2)
     assert hydro.variant_supported(torch.float64, 3, (32, 8), 32, split=1)
