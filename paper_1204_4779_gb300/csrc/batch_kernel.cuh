@@ -200,6 +200,7 @@ __global__ void __launch_bounds__(BX, (MinBlocks<T, BX, OCC>::value))
         V.n[0] = R.nx, V.n[1] = R.ny, V.n[2] = 1;
         V.periodic[0] = A.periodic[0], V.periodic[1] = A.periodic[1], V.periodic[2] = 1;
         V.march = A.rows;
+        V.zchunk0 = 0;
         V.order = 2;
         V.riemann = 0;
         V.dr[0] = R.dr[0], V.dr[1] = R.dr[1], V.dr[2] = 1.0;

@@ -173,6 +173,8 @@ struct hydro_ctx {
     void *u1[5] = {};
     cudaStream_t stream = nullptr;
     cudaStream_t cap = nullptr;  // private stream used only to capture graphs
+    cudaStream_t copy = nullptr;  // private stream of hydro_step_host's copies back to the host
+    std::vector<cudaEvent_t> slab_events;  // one per stage-2 slab of hydro_step_host
     GraphEntry graphs[kGraphSlots];
     unsigned long long use_clock = 0;
     bool profiling = false;
@@ -476,7 +478,9 @@ int hydro_create(const hydro_grid_t *grid, double gamma, const int32_t bc[3], in
     for (int k = 0; k < c->dim + 2; ++k) c->u1[k] = c->ws + lay.u1_off + plane * (size_t)k;
     c->stream = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->copy, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
+        if (c->cap) cudaStreamDestroy(c->cap);
         delete c;
         return cuda_fail(e, "cudaStreamCreateWithFlags");
     }
@@ -485,6 +489,7 @@ int hydro_create(const hydro_grid_t *grid, double gamma, const int32_t bc[3], in
     e = launch_stage(c, stage_args(c, &dummy, 1), c->stream, /*prepare_only=*/true);
     if (e != cudaSuccess) {
         cudaStreamDestroy(c->cap);
+        cudaStreamDestroy(c->copy);
         delete c;
         return cuda_fail(e, "stage kernel attributes");
     }
@@ -498,7 +503,9 @@ int hydro_destroy(hydro_ctx_t *c) {
     for (auto &g : c->graphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);
     for (auto e : c->events) cudaEventDestroy(e);
+    for (auto e : c->slab_events) cudaEventDestroy(e);
     if (c->cap) cudaStreamDestroy(c->cap);
+    if (c->copy) cudaStreamDestroy(c->copy);
     delete c;
     return HYDRO_OK;
 }
@@ -539,6 +546,47 @@ int hydro_step(hydro_ctx_t *c, const hydro_state_t *state, int32_t n_steps, doub
     return finish_steps(c, t_inout, steps_done);
 }
 
+// The last step of hydro_step_host in dim 3, with the copy back overlapped: stage 1 over the
+// grid, then stage 2 slab by slab (groups of march chunks along z, the dt reduction left to a
+// CFL pass), each slab's finished planes copied to the host on the private copy stream while
+// the next slabs compute; the CFL pass (status, time, next dt) runs after the last slab.  A
+// slab's U is final when its stage-2 launch ends: stage 2 writes only its own cells and reads
+// other slabs' U1, not U.  Returns with the copy stream joined into the context's stream.
+static int last_step_overlapped(hydro_ctx *c, const hydro_state_t *s, void *const host_out[5]) {
+    const int march = c->var.march;
+    const int nchunks = (c->n[2] + march - 1) / march;
+    const int nslabs = nchunks < 8 ? nchunks : 8;
+    while ((int)c->slab_events.size() < nslabs + 1) {
+        cudaEvent_t e;
+        CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        c->slab_events.push_back(e);
+    }
+    const size_t esz = c->prec == HYDRO_F32 ? 4 : 8;
+    const size_t plane_cells = (size_t)c->n[0] * (size_t)c->n[1];
+    CK(launch_stage(c, stage_args(c, s, 1), c->stream));
+    hydro::StageLaunch L2 = stage_args(c, s, 2);
+    L2.split = 1;
+    for (int i = 0; i < nslabs; ++i) {
+        const int k0 = (int)((long long)nchunks * i / nslabs);
+        const int k1 = (int)((long long)nchunks * (i + 1) / nslabs);
+        L2.zchunk0 = k0;
+        L2.zchunks = k1 - k0;
+        CK(launch_stage(c, L2, c->stream));
+        CK(cudaEventRecord(c->slab_events[(size_t)i], c->stream));
+        CK(cudaStreamWaitEvent(c->copy, c->slab_events[(size_t)i], 0));
+        const int z0 = k0 * march, z1 = k1 * march < c->n[2] ? k1 * march : c->n[2];
+        const size_t off = (size_t)z0 * plane_cells * esz, bytes = (size_t)(z1 - z0) * plane_cells * esz;
+        for (int k = 0; k < c->dim + 2; ++k)
+            CK(cudaMemcpyAsync(static_cast<char *>(host_out[k]) + off,
+                               static_cast<const char *>(s->plane[k]) + off, bytes,
+                               cudaMemcpyDeviceToHost, c->copy));
+    }
+    CK(hydro::launch_cfl(aux_args(c, s), c->stream, /*advance=*/true));
+    CK(cudaEventRecord(c->slab_events[(size_t)nslabs], c->copy));
+    CK(cudaStreamWaitEvent(c->stream, c->slab_events[(size_t)nslabs], 0));
+    return HYDRO_OK;
+}
+
 int hydro_step_host(hydro_ctx_t *c, const hydro_state_t *dev, const void *const host_in[5],
                     void *const host_out[5], int32_t n_steps, double t_end, double *t_inout,
                     int32_t *steps_done) {
@@ -552,10 +600,14 @@ int hydro_step_host(hydro_ctx_t *c, const hydro_state_t *dev, const void *const 
     double t = t_inout ? *t_inout : 0.0;
     int32_t done = 0;
     int rc = begin_steps(c, dev, t, t_end);
-    if (!rc) rc = run_steps(c, dev, n_steps);
+    // dim 3 outside profiling: the last step overlaps its copy back with its stage 2
+    const bool overlap = c->dim == 3 && n_steps >= 1 && !c->profiling;
+    if (!rc) rc = run_steps(c, dev, overlap ? n_steps - 1 : n_steps);
+    if (!rc && overlap) rc = last_step_overlapped(c, dev, host_out);
     if (rc) return rc;
-    for (int k = 0; k < c->dim + 2; ++k)
-        CK(cudaMemcpyAsync(host_out[k], dev->plane[k], bytes, cudaMemcpyDeviceToHost, c->stream));
+    if (!overlap)
+        for (int k = 0; k < c->dim + 2; ++k)
+            CK(cudaMemcpyAsync(host_out[k], dev->plane[k], bytes, cudaMemcpyDeviceToHost, c->stream));
     rc = finish_steps(c, &t, &done);
     if (t_inout) *t_inout = t;
     if (steps_done) *steps_done = done;

@@ -25,6 +25,8 @@ struct StageLaunch {
     int occupancy;      // dim 3 FP32: resident CTAs per SM the register budget targets (2 or 3)
     int order;          // reconstruction order (2 MinBee, 1 first order); 0 = 2
     int riemann;        // HLLC wave speeds: 0 Davis, 1 pressure-based
+    int zchunk0;        // first march chunk to launch
+    int zchunks;        // march chunks to launch (0: all from zchunk0)
     double dr[3];
     double gamma;
     void *ctrl;

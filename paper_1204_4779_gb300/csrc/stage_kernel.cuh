@@ -37,7 +37,8 @@ template <class T> struct StageArgs {
     T *uout[5];         // U1 (stage 1) or U0 (stage 2, in place over ubase)
     int n[3];
     int periodic[3];
-    int march;          // z-planes per CTA (dim 3)
+    int march;          // planes per CTA along the march axis
+    int zchunk0;        // march chunk of blockIdx.z = 0 (a launch may cover a slab of chunks)
     int order;          // reconstruction order: 2 = MinBee slopes, 1 = face values = cell values
     int riemann;        // HLLC wave speeds: 0 = Davis, 1 = pressure-based
     double dr[3];       // cell sizes (the FP64 CFL signal divides by them)
@@ -604,7 +605,7 @@ __global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY, OCC>::value))
     const T cz = GM::march ? T(__ldcg(&ctrl->coef[STAGE - 1][GM::MA])) : T(0);
     const int x0 = blockIdx.x * BX;
     const int y0 = (GM::IN >= 2) ? blockIdx.y * BY : 0;
-    const int zb = GM::march ? blockIdx.z * A.march : 0;
+    const int zb = GM::march ? ((int)blockIdx.z + A.zchunk0) * A.march : 0;
     const int ze = GM::march ? min(zb + A.march, A.n[GM::MA]) : 1;
     T smax = T(0);
     bool bad = false;

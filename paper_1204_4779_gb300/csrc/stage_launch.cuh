@@ -21,6 +21,7 @@ template <class T> static StageArgs<T> make_stage_args(const StageLaunch &L) {
         A.inv_dr[a] = T(1.0 / L.dr[a]);
     }
     A.march = L.march;
+    A.zchunk0 = L.zchunk0;
     A.order = L.order == 1 ? 1 : 2;
     A.riemann = L.riemann;
     A.gas = make_gas<T>(L.gamma);
@@ -43,7 +44,9 @@ static cudaError_t launch_stage_pf(const StageLaunch &L, const StageArgs<T> &A, 
     using K = StageKernels<T, D, BX, BY, PF, OCC>;
     const dim3 grid((unsigned)((A.n[0] + BX - 1) / BX),
                     (unsigned)((GM::IN >= 2) ? (A.n[1] + BY - 1) / BY : 1),
-                    (unsigned)(GM::march ? (A.n[GM::MA] + A.march - 1) / A.march : 1));
+                    (unsigned)(GM::march ? (L.zchunks > 0 ? L.zchunks
+                                                          : (A.n[GM::MA] + A.march - 1) / A.march - L.zchunk0)
+                                         : 1));
     const size_t smem = S::smem_bytes;
     if (L.stage == 1)
         K::s1<<<grid, S::NT, smem, st>>>(A);

@@ -163,3 +163,24 @@ def test_single_cell_axes_and_tiny_grids():
         G, tg, sg = gpu_run(V, 1.4, bc, F64, 0.3, 6)
         O, to, so, _ = oracle_run(V, 1.4, bc, 0.3, 6)
         assert sg == so and np.allclose(G, O, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("n_steps,t_end", [(1, 0.0), (3, 0.0), (5, 0.002)])
+def test_host_stepping_3d_overlapped_copy_back(n_steps, t_end):
+    """In 3D the last step of hydro_step_host copies each z-slab back while later slabs compute
+    (13 march chunks of 8 planes, the last one ragged, in 8 slabs): the host result, time and
+    step count equal stepping on the device."""
+    V = inputs.blast_3d(shape=(40, 36, 100), radius_cells=6.0)
+    U = gpu_state(V, 1.4, F32)
+    var = dict(march=8)
+    S = hydro.Solver((40, 36, 100), 1.4, dtype=F32, variant=var)
+    Ud = U.clone()
+    td, nd = S.step(Ud, n_steps, t_end=t_end)
+    host = U.cpu().pin_memory()
+    out = torch.empty_like(host).pin_memory()
+    out.fill_(float("nan"))
+    dev = torch.empty_like(U)
+    th, nh = S.step_host(dev, host, out, n_steps, t_end=t_end)
+    assert nh == nd and th == td
+    assert torch.equal(out, Ud.cpu())
+    assert torch.equal(dev, Ud)
