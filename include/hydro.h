@@ -50,7 +50,10 @@ enum {
                              workspace too small or misaligned */
     HYDRO_ECUDA = 2,      /* a CUDA runtime call failed (hydro_last_cuda_error tells which) */
     HYDRO_ENONFINITE = 3, /* non-finite value, rho <= 0 or p <= 0 seen on the device */
-    HYDRO_ETIMEOUT = 4,   /* a bounded device-side wait gave up */
+    HYDRO_ETIMEOUT = 4,   /* reserved for a bounded device-side wait that gives up; no kernel
+                             of this library waits on another CTA (the dt reductions use a
+                             last-CTA counter or per-item slots and a finaliser kernel), so
+                             no call returns it */
     HYDRO_EUNSUPPORTED = 5 /* valid request that this build has no kernel for */
 };
 
