@@ -40,9 +40,15 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-def _kernel_digest() -> str:
+# the sources each committed ncu record depends on: a record whose digest differs was taken on
+# other kernel code and is not used
+STAGE_SOURCES = ("hydro_device.cuh", "stage_kernel.cuh", "stage_launch.cuh", "stage_f32_d3.cu")
+BATCH_SOURCES = ("hydro_device.cuh", "stage_kernel.cuh", "batch_kernel.cuh", "batch_f32.cu")
+
+
+def _kernel_digest(sources=STAGE_SOURCES) -> str:
     h = hashlib.sha256()
-    for name in ("hydro_device.cuh", "stage_kernel.cuh", "stage_launch.cuh", "stage_f32_d3.cu"):
+    for name in sources:
         with open(os.path.join(ROOT, "paper_1204_4779_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -59,14 +65,14 @@ def _oracle_opcounts():
         return None
 
 
-def _ncu_record(field: str, kernel: str):
-    """Per-launch figure (`per_launch_bytes` or `per_launch_warp_instructions`) of `kernel` at
-    512^3 from the committed ncu summary, if it was taken on the current kernel source; else
-    None."""
+def _ncu_record(field: str, kernel: str, name: str = "ncu_counters.json", sources=STAGE_SOURCES):
+    """Per-launch figure (`per_launch_bytes` or `per_launch_warp_instructions`) of `kernel` in
+    the benchmark's workload from a committed ncu summary (profiles/<name>), if it was taken on
+    the current kernel source; else None."""
     try:
-        with open(os.path.join(ROOT, "profiles", "ncu_counters.json")) as f:
+        with open(os.path.join(ROOT, "profiles", name)) as f:
             rec = json.load(f)
-        if rec.get("kernel_digest") != _kernel_digest():
+        if rec.get("kernel_digest") != _kernel_digest(sources):
             return None
         return rec[field].get(kernel)
     except Exception:
@@ -258,6 +264,11 @@ def run_ours(args):
     U_init = U.clone()
     del V
     S = hydro.Solver((n, n, n), GAMMA, bc="periodic", dtype=torch.float32, cfl=CFL)
+    variant = S.variant()
+    variant = {"tile": list(variant["tile"]), "march": variant["march"],
+               "split": "fused dt reduction" if variant["split"] == 2 else "separate CFL pass",
+               "staging": "look-ahead" if variant["staging"] == 1 else "at use",
+               "occupancy": variant["occupancy"]}
     # measured FMA throughput of this GPU (the FP32 roofline's denominator), before the warm-up
     fma32 = hydro.fma_rate(torch.float32, dev)
     fma64 = hydro.fma_rate(torch.float64, dev)
@@ -425,8 +436,7 @@ def run_ours(args):
                        "grid": [n, n, n], "gamma": GAMMA, "cfl": CFL,
                        "blast_radius_cells": RADIUS, "parallelism": f"replicas x{world}",
                        "l2": f"inputs larger than L2 ({5 * 4 * ncell / 2**30:.2f} GiB state vs 129 MB L2); no flush",
-                       "variant": {"tile": [32, 8], "march": 64, "split": "fused dt reduction",
-                                   "staging": "look-ahead", "occupancy": 3}},
+                       "variant": variant},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": traffic, "kernel": dom,
                          "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"},
@@ -492,7 +502,10 @@ def run_batched(args):
                        "variant": "library default: row tiles of 32 columns marching 32 rows "
                                   "along y, one work item per strip and chunk"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": None, "kernel": "batch_" + dom,
+                         "frac": achieved / hbm,
+                         "traffic": _ncu_record("per_launch_bytes", dom, "ncu_counters_batched.json",
+                                                BATCH_SOURCES),
+                         "kernel": "batch_" + dom,
                          "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"},
             "kernels": {k: {"avg_ms": v[0] / max(v[1], 1), "launches": v[1]} for k, v in kt.items()},
             "gpu_launches": int(sum(v[1] for v in kt.values())), "clocks": clk.summary(),

@@ -95,8 +95,8 @@ typedef struct {
  *                   the register budget of the stage kernels targets.  0 = library default
  *                   (3 for the default FP32 marching tiles, else 2); 2 (about 128 registers a
  *                   thread); 3 (about 80 registers, 24 warps per SM).
- * Library defaults (measured on GB300): dim 3 tile 32 x 8, march 64; dim 2 FP32 row tile
- * 256 x 1, march 16; dim 2 FP64 tile 32 x 8; dim 1 tile 128.  A variant that names a tile other
+ * Library defaults (measured on GB300): dim 3 FP32 tile 16 x 8, FP64 32 x 8, march 64; dim 2
+ * FP32 row tile 256 x 1, march 16; dim 2 FP64 tile 32 x 8; dim 1 tile 128.  A variant that names a tile other
  * than the default gets that tile's default march (64 in dim 3, 16 for row tiles) and
  * budget unless it names them too.
  * Every variant computes the same step; they differ in speed only. */
@@ -142,6 +142,10 @@ int hydro_workspace_bytes(const hydro_grid_t *grid, int32_t prec, size_t *bytes_
 int hydro_create(const hydro_grid_t *grid, double gamma, const int32_t bc[3], int32_t prec,
                  double cfl, const hydro_variant_t *variant, void *workspace,
                  size_t workspace_bytes, void *stream, hydro_ctx_t **out);
+
+/* The variant a context runs: the one given to hydro_create with every default filled in
+ * (split spelled 1 = separate CFL pass, 2 = fused).  Errors: HYDRO_EINVAL (null pointer). */
+int hydro_get_variant(const hydro_ctx_t *ctx, hydro_variant_t *out);
 
 int hydro_destroy(hydro_ctx_t *ctx);
 

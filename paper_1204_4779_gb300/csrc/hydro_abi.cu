@@ -83,8 +83,9 @@ int tile_compiled(int prec, int dim, int bx, int by) {
     return 0;
 }
 
-// Defaults chosen by measurements on GB300.  dim 3: tile 32 x 8 marching 64 planes, in FP32 with
-// the three-CTA register budget (the variant tuner's best).  dim 2, FP32: row tiles of 256
+// Defaults chosen by measurements on GB300.  dim 3: marching 64 planes; FP32 tile 16 x 8 with
+// the three-CTA register budget (the variant tuner's best: 23.03 against 22.82 G
+// cell-updates/s for 32 x 8 at 512^3), FP64 tile 32 x 8 (its one compiled 3D tile).  dim 2, FP32: row tiles of 256
 // cells marching 16 rows along y, three-CTA budget (2048^2: 28.4 G cell-updates/s against 20.8
 // G for the best one-plane tile).  dim 1 and FP64 dim 2: one-plane tiles.  The dt reduction is
 // fused into stage 2 for marching tiles; for one-plane tiles, where a CTA updates one tile, the
@@ -103,6 +104,9 @@ void default_variant(int prec, int dim, hydro_variant_t *v) {
         v->tile_y = 1;
         v->march = 16;
         v->occupancy = 3;
+    } else if (dim == 3 && prec == HYDRO_F32) {
+        v->tile_x = 16;
+        v->tile_y = 8;
     } else {
         v->tile_x = 32;
         v->tile_y = 8;
@@ -494,6 +498,13 @@ int hydro_create(const hydro_grid_t *grid, double gamma, const int32_t bc[3], in
         return cuda_fail(e, "stage kernel attributes");
     }
     *out = c;
+    return HYDRO_OK;
+}
+
+int hydro_get_variant(const hydro_ctx_t *c, hydro_variant_t *out) {
+    if (!c || !out) return HYDRO_EINVAL;
+    *out = c->var;
+    out->split = c->var.split ? 1 : 2;  // the ABI's spelling: 1 separate CFL pass, 2 fused
     return HYDRO_OK;
 }
 

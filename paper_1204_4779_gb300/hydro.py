@@ -26,7 +26,8 @@ HYDRO_F64, HYDRO_F32 = 0, 1
 # every symbol include/hydro.h declares
 EXPORTS = (
     "hydro_version", "hydro_strerror", "hydro_last_cuda_error", "hydro_variant_supported",
-    "hydro_workspace_bytes", "hydro_create", "hydro_destroy", "hydro_set_stream", "hydro_step",
+    "hydro_workspace_bytes", "hydro_create", "hydro_get_variant", "hydro_destroy", "hydro_set_stream",
+    "hydro_step",
     "hydro_step_host", "hydro_set_scheme", "hydro_cfl_dt", "hydro_totals", "hydro_status", "hydro_prim_to_cons",
     "hydro_cons_to_prim", "hydro_set_profiling", "hydro_kernel_times", "hydro_step_static",
     "hydro_batch_workspace_bytes", "hydro_batch_create", "hydro_batch_destroy",
@@ -90,6 +91,7 @@ def load_library(path: str = LIB_PATH, build_if_missing: bool = True):
             "hydro_create": ([P(Grid), dbl, P(i32), i32, dbl, P(Variant), vp, ctypes.c_size_t, vp,
                               P(vp)], ctypes.c_int),
             "hydro_destroy": ([vp], ctypes.c_int),
+            "hydro_get_variant": ([vp, P(Variant)], ctypes.c_int),
             "hydro_set_stream": ([vp, vp], ctypes.c_int),
             "hydro_set_scheme": ([vp, i32, i32], ctypes.c_int),
             "hydro_step": ([vp, P(State), i32, dbl, P(dbl), P(i32)], ctypes.c_int),
@@ -248,6 +250,13 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+    def variant(self) -> dict:
+        """The variant this context runs, defaults filled in (hydro_get_variant)."""
+        v = Variant()
+        _check(self.lib.hydro_get_variant(self.ctx, ctypes.byref(v)), "hydro_get_variant")
+        return {"tile": (v.tile_x, v.tile_y), "march": v.march, "split": v.split,
+                "staging": v.staging, "occupancy": v.occupancy}
 
     # -- helpers ---------------------------------------------------------------------------
     def empty_state(self) -> torch.Tensor:

@@ -94,7 +94,7 @@ class Space:
 
     def default_genome(self):
         if self.dim == 3:
-            d = {"tile": (32, 8), "march": 64, "split": 2, "staging": 1, "occupancy": 3}
+            d = {"tile": (16, 8), "march": 64, "split": 2, "staging": 1, "occupancy": 3}
         elif self.dim == 2:
             d = {"tile": (256, 1), "march": 16, "split": 2, "staging": 1, "occupancy": 3}
         else:

@@ -184,3 +184,26 @@ def test_host_stepping_3d_overlapped_copy_back(n_steps, t_end):
     assert nh == nd and th == td
     assert torch.equal(out, Ud.cpu())
     assert torch.equal(dev, Ud)
+
+
+def test_resolved_default_variants():
+    """hydro_get_variant: the library defaults per dimension and precision, and the defaults a
+    variant that names another tile gets (that tile's march and register budget)."""
+    cases = [
+        ((40, 36, 30), F32, None, dict(tile=(16, 8), march=30, split=2, staging=1, occupancy=3)),
+        ((40, 36, 100), F64, None, dict(tile=(32, 8), march=64, split=2, staging=1, occupancy=2)),
+        ((300, 77), F32, None, dict(tile=(256, 1), march=16, split=2, staging=1, occupancy=3)),
+        ((300, 77), F64, None, dict(tile=(32, 8), march=1, split=1, staging=1, occupancy=2)),
+        ((300,), F32, None, dict(tile=(128, 1), march=1, split=1, staging=1, occupancy=2)),
+        ((300, 77), F32, dict(tile=(32, 8)), dict(tile=(32, 8), march=1, split=1, staging=1,
+                                                  occupancy=2)),
+        ((300, 77), F32, dict(tile=(64, 1)), dict(tile=(64, 1), march=16, split=2, staging=1,
+                                                  occupancy=2)),
+        ((40, 36, 100), F32, dict(tile=(32, 8)), dict(tile=(32, 8), march=64, split=2, staging=1,
+                                                      occupancy=3)),
+    ]
+    for shape, dt, var, want in cases:
+        S = hydro.Solver(shape, 1.4, dtype=dt, variant=var)
+        got = S.variant()
+        S.close()
+        assert got == want, (shape, dt, var, got)

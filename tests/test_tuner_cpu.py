@@ -24,7 +24,7 @@ def test_triangulation_truth_table():
 def test_space_and_features():
     s3 = T.Space(3)
     assert len(s3.all_genomes()) == 6 * 7 * 2 * 2 * 2
-    assert s3.variant(s3.default_genome()) == {"tile": (32, 8), "march": 64, "split": 2,
+    assert s3.variant(s3.default_genome()) == {"tile": (16, 8), "march": 64, "split": 2,
                                                "staging": 1, "occupancy": 3}
     f = T.features(s3, s3.default_genome(), (512, 512, 512))
     assert f.shape == (T.N_FEATURES,)
