@@ -456,6 +456,57 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_kh2d(args):
+    """A 2D line: the shear layer (Kelvin-Helmholtz data, gamma 5/3, periodic, seed 1204477901) at
+    --size^2 (default 2048) in FP32 with the library's default 2D variant (row tiles), steps
+    timed with per-launch events like the main line."""
+    import torch
+
+    from paper_1204_4779_gb300 import hydro, inputs
+    torch.cuda.set_device(0)
+    n = args.size if args.size != N else 2048
+    V = torch.from_numpy(inputs.kh_2d(n, seed=1204477901)).cuda()
+    U = hydro.prim_to_cons(V, 5.0 / 3.0).to(torch.float32).contiguous()
+    del V
+    S = hydro.Solver((n, n), 5.0 / 3.0, bc="periodic", dtype=torch.float32, cfl=CFL)
+    variant = S.variant()
+    S.step(U, args.warmup)
+    torch.cuda.synchronize()
+    S.set_profiling(True)
+    S.kernel_times(reset=True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(_gpu_index(0)) as clk:
+        torch.cuda.synchronize()
+        ev0.record()
+        _, done = S.step(U, args.steps)
+        ev1.record()
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    kt = S.kernel_times(reset=True)
+    ncell = n * n
+    hbm, peak_kind = _peaks()
+    alg = {"stage1": 2 * 4 * 4 * ncell, "stage2": 3 * 4 * 4 * ncell}
+    dom = max(("stage1", "stage2"), key=lambda k: kt[k][0])
+    avg_ms = kt[dom][0] / max(kt[dom][1], 1)
+    achieved = alg[dom] / (avg_ms * 1e-3) / 1e9
+    line = {"metric": f"cell-updates/s per RK step, 2D shear layer {n}^2 (FP32)",
+            "value": ncell * args.steps / (ms * 1e-3), "unit": "cell-updates/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"2D periodic {n}^2 shear layer, gamma 5/3, FP32",
+                       "l2": f"state {4 * 4 * ncell / 2**20:.0f} MiB vs 129 MB L2; no flush",
+                       "variant": {"tile": list(variant["tile"]), "march": variant["march"],
+                                   "split": variant["split"], "occupancy": variant["occupancy"]}},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": None, "kernel": dom,
+                         "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"},
+            "kernels": {k: {"avg_ms": v[0] / max(v[1], 1), "launches": v[1]} for k, v in kt.items()},
+            "gpu_launches": int(sum(v[1] for v in kt.values())),
+            "clocks": clk.summary(), "steps_done": done}
+    print(json.dumps(line), flush=True)
+
+
 def run_batched(args):
     """The batched configuration: 4096 independent 2D grids, sides log-uniform on [32, 512]
     (seed 1204477904), seeded smooth data, gamma 1.4, FP32, one persistent launch per RK
@@ -522,8 +573,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10,
                     help="timed hydro_step_host calls of one step each (mean over the calls)")
     ap.add_argument("--size", type=int, default=N, help="cube side (the benchmark config is 512)")
-    ap.add_argument("--config", choices=("blast512", "batched"), default="blast512",
-                    help="blast512: the benchmark line; batched: the 4096-grid configuration")
+    ap.add_argument("--config", choices=("blast512", "batched", "kh2d"), default="blast512",
+                    help="blast512: the benchmark line; batched: the 4096-grid configuration; "
+                         "kh2d: the 2D shear layer (--size, default 2048)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=10,
                     help="timed FP64 steps of the same workload after the FP32 run (0: none)")
@@ -536,6 +588,8 @@ def main():
         run_reference(args)
     elif args.config == "batched":
         run_batched(args)
+    elif args.config == "kh2d":
+        run_kh2d(args)
     else:
         run_ours(args)
 
