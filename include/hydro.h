@@ -95,6 +95,18 @@ typedef struct {
  *                   the register budget of the stage kernels targets.  0 = library default
  *                   (3 for the default FP32 marching tiles, else 2); 2 (about 128 registers a
  *                   thread); 3 (about 80 registers, 24 warps per SM).
+ *   manifest:       what a stage stores in HBM between its parts (the paper's choice of what
+ *                   to "Manifest", section 3.1).  0 = library default (1); 1 = nothing: V, the
+ *                   face states and fluxes live in registers and shared memory; 2 = V: a pass
+ *                   stores the primitive planes of the stage's input, which the stage kernel
+ *                   reads instead of U; 3 = F: the stage kernel stores every face flux and a
+ *                   pass applies AddFlux (and stage 2's dt reduction).  All three compute the
+ *                   same step: bit for bit in FP64; in FP32 to rounding (where V or a flux
+ *                   stays in registers the compiler may fuse a product into its consumer).
+ *                   dim 3 only, for the tiles compiled with them (FP32
+ *                   16 x 8, 32 x 8, 16 x 16; FP64 32 x 8), with look-ahead staging and the
+ *                   precision's default budget; 2 and 3 need more workspace
+ *                   (hydro_workspace_bytes_variant).
  * Library defaults (measured on GB300): dim 3 FP32 tile 16 x 8, FP64 32 x 8, march 64; dim 2
  * FP32 row tile 256 x 1, march 16; dim 2 FP64 tile 32 x 8; dim 1 tile 128.  A variant that names a tile other
  * than the default gets that tile's default march (64 in dim 3, 16 for row tiles) and
@@ -107,6 +119,7 @@ typedef struct {
     int32_t split;
     int32_t staging;
     int32_t occupancy;
+    int32_t manifest;
 } hydro_variant_t;
 
 typedef struct hydro_ctx hydro_ctx_t;
@@ -126,6 +139,12 @@ int hydro_variant_supported(int32_t prec, int32_t dim, const hydro_variant_t *va
 /* Bytes of device workspace hydro_create needs for this grid and precision: the RK stage
  * buffer U1 (dim+2 planes), the step control block and reduction partials. */
 int hydro_workspace_bytes(const hydro_grid_t *grid, int32_t prec, size_t *bytes_out);
+
+/* Workspace bytes for a given variant (the manifest forms store V or the face fluxes there);
+ * the same as hydro_workspace_bytes for variants that store nothing.  Errors: HYDRO_EINVAL,
+ * HYDRO_EUNSUPPORTED (variant not compiled). */
+int hydro_workspace_bytes_variant(const hydro_grid_t *grid, int32_t prec,
+                                  const hydro_variant_t *variant, size_t *bytes_out);
 
 /* Create a solver context.
  *   grid      grid and box (copied)

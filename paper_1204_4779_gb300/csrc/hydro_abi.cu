@@ -48,6 +48,9 @@ struct GraphEntry {
 
 struct Layout {
     size_t ctrl_off, parts_off, u1_off, total;
+    size_t v_off;            // manifest V: the primitive planes
+    size_t f_off[3];         // manifest F: the face-flux planes of each axis
+    size_t plane, fplane[3]; // bytes of one cell plane and of one face plane per axis
 };
 
 bool grid_ok(const hydro_grid_t *g, long long *ncell) {
@@ -63,14 +66,28 @@ bool grid_ok(const hydro_grid_t *g, long long *ncell) {
     return true;
 }
 
-Layout layout_for(int dim, long long ncell, int prec) {
+// Workspace: control block, totals partials, the stage buffer U1, and for the manifest forms
+// (manifest: 1 none, 2 V, 3 F in the ABI's spelling) the V planes or the face-flux planes.
+Layout layout_for(int dim, const int64_t n[3], long long ncell, int prec, int manifest = 1) {
     Layout L;
+    memset(&L, 0, sizeof L);
     const size_t esz = prec == HYDRO_F32 ? 4 : 8;
     L.ctrl_off = 0;
     L.parts_off = align_up(sizeof(Ctrl));
     L.u1_off = align_up(L.parts_off + sizeof(double) * 5 * hydro::kTotalsParts);
-    const size_t plane = align_up((size_t)ncell * esz);
-    L.total = L.u1_off + plane * (size_t)(dim + 2);
+    L.plane = align_up((size_t)ncell * esz);
+    L.total = L.u1_off + L.plane * (size_t)(dim + 2);
+    if (manifest == 2) {
+        L.v_off = L.total;
+        L.total += L.plane * (size_t)(dim + 2);
+    } else if (manifest == 3) {
+        for (int a = 0; a < dim; ++a) {
+            const size_t faces = (size_t)ncell / (size_t)n[a] * (size_t)(n[a] + 1);
+            L.fplane[a] = align_up(faces * esz);
+            L.f_off[a] = L.total;
+            L.total += L.fplane[a] * (size_t)(dim + 2);
+        }
+    }
     return L;
 }
 
@@ -79,6 +96,15 @@ int tile_compiled(int prec, int dim, int bx, int by) {
     for (int i = 0; i < hydro::kNumTiles; ++i) {
         const hydro::TileShape &t = hydro::kTiles[i];
         if (t.prec == prec && t.dim == dim && t.bx == bx && t.by == by) return t.both_pf ? 2 : 1;
+    }
+    return 0;
+}
+
+// 1 if the tile is also compiled in the manifest forms.
+int tile_compiled_manifest(int prec, int dim, int bx, int by) {
+    for (int i = 0; i < hydro::kNumTiles; ++i) {
+        const hydro::TileShape &t = hydro::kTiles[i];
+        if (t.prec == prec && t.dim == dim && t.bx == bx && t.by == by) return t.manifest;
     }
     return 0;
 }
@@ -96,6 +122,7 @@ void default_variant(int prec, int dim, hydro_variant_t *v) {
     v->staging = 1;
     v->occupancy = 2;
     v->march = 0;
+    v->manifest = 1;
     if (dim == 1) {
         v->tile_x = 128;
         v->tile_y = 1;
@@ -136,6 +163,14 @@ bool resolve_variant(int prec, int dim, const hydro_variant_t *in, hydro_variant
         if (in->split) out->split = in->split;
         if (in->staging) out->staging = in->staging;
         if (in->occupancy) out->occupancy = in->occupancy;
+        if (in->manifest) out->manifest = in->manifest;
+    }
+    // manifest forms: dim 3, tiles compiled with them, look-ahead staging, the default budget
+    if (out->manifest < 1 || out->manifest > 3) return false;
+    if (out->manifest > 1) {
+        const int tm = tile_compiled_manifest(prec, dim, out->tile_x, out->tile_y);
+        const int occ = prec == HYDRO_F32 ? 3 : 2;
+        if (dim != 3 || !tm || out->staging != 1 || out->occupancy != occ) return false;
     }
     if (in && (in->split < 0 || in->split > 2)) return false;
     if (out->staging != 1 && out->staging != 2) return false;
@@ -175,6 +210,8 @@ struct hydro_ctx {
     Ctrl *ctrl = nullptr;
     double *parts = nullptr;
     void *u1[5] = {};
+    void *vbuf[5] = {};     // manifest V: primitive planes
+    void *flux[3][5] = {};  // manifest F: face-flux planes per axis
     cudaStream_t stream = nullptr;
     cudaStream_t cap = nullptr;  // private stream used only to capture graphs
     cudaStream_t copy = nullptr;  // private stream of hydro_step_host's copies back to the host
@@ -216,6 +253,10 @@ hydro::StageLaunch stage_args(const hydro_ctx *c, const hydro_state_t *s, int st
     L.prefetch = c->var.staging == 2 ? 0 : 1;
     L.split = c->var.split;
     L.occupancy = c->var.occupancy;
+    L.manifest = c->var.manifest == 2 ? 1 : (c->var.manifest == 3 ? 2 : 0);
+    for (int k = 0; k < 5; ++k) L.vbuf[k] = c->vbuf[k];
+    for (int a = 0; a < 3; ++a)
+        for (int k = 0; k < 5; ++k) L.flux[a][k] = c->flux[a][k];
     L.order = c->order;
     L.riemann = c->riemann;
     L.gamma = c->gamma;
@@ -427,7 +468,18 @@ int hydro_workspace_bytes(const hydro_grid_t *grid, int32_t prec, size_t *bytes_
     long long ncell = 0;
     if (!bytes_out || !grid_ok(grid, &ncell)) return HYDRO_EINVAL;
     if (prec != HYDRO_F32 && prec != HYDRO_F64) return HYDRO_EINVAL;
-    *bytes_out = layout_for(grid->dim, ncell, prec).total;
+    *bytes_out = layout_for(grid->dim, grid->n, ncell, prec).total;
+    return HYDRO_OK;
+}
+
+int hydro_workspace_bytes_variant(const hydro_grid_t *grid, int32_t prec,
+                                  const hydro_variant_t *variant, size_t *bytes_out) {
+    long long ncell = 0;
+    if (!bytes_out || !grid_ok(grid, &ncell)) return HYDRO_EINVAL;
+    if (prec != HYDRO_F32 && prec != HYDRO_F64) return HYDRO_EINVAL;
+    hydro_variant_t var;
+    if (!resolve_variant(prec, grid->dim, variant, &var)) return HYDRO_EUNSUPPORTED;
+    *bytes_out = layout_for(grid->dim, grid->n, ncell, prec, var.manifest).total;
     return HYDRO_OK;
 }
 
@@ -443,10 +495,10 @@ int hydro_create(const hydro_grid_t *grid, double gamma, const int32_t bc[3], in
     for (int a = 0; a < grid->dim; ++a)
         if (bc[a] != HYDRO_BC_PERIODIC && bc[a] != HYDRO_BC_OUTFLOW) return HYDRO_EINVAL;
     if (((uintptr_t)workspace) % kAlign) return HYDRO_EINVAL;
-    const Layout lay = layout_for(grid->dim, ncell, prec);
-    if (workspace_bytes < lay.total) return HYDRO_EINVAL;
     hydro_variant_t var;
     if (!resolve_variant(prec, grid->dim, variant, &var)) return HYDRO_EUNSUPPORTED;
+    const Layout lay = layout_for(grid->dim, grid->n, ncell, prec, var.manifest);
+    if (workspace_bytes < lay.total) return HYDRO_EINVAL;
     // grid-dimension limits of the stage launch
     const bool marching = grid->dim == 3 || (grid->dim == 2 && var.tile_y == 1);
     if ((grid->dim == 3 || (grid->dim == 2 && !marching)) &&
@@ -480,6 +532,12 @@ int hydro_create(const hydro_grid_t *grid, double gamma, const int32_t bc[3], in
     c->parts = reinterpret_cast<double *>(c->ws + lay.parts_off);
     const size_t plane = align_up((size_t)ncell * (prec == HYDRO_F32 ? 4 : 8));
     for (int k = 0; k < c->dim + 2; ++k) c->u1[k] = c->ws + lay.u1_off + plane * (size_t)k;
+    if (var.manifest == 2)
+        for (int k = 0; k < c->dim + 2; ++k) c->vbuf[k] = c->ws + lay.v_off + lay.plane * (size_t)k;
+    if (var.manifest == 3)
+        for (int a = 0; a < c->dim; ++a)
+            for (int k = 0; k < c->dim + 2; ++k)
+                c->flux[a][k] = c->ws + lay.f_off[a] + lay.fplane[a] * (size_t)k;
     c->stream = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->copy, cudaStreamNonBlocking);
@@ -612,7 +670,7 @@ int hydro_step_host(hydro_ctx_t *c, const hydro_state_t *dev, const void *const 
     int32_t done = 0;
     int rc = begin_steps(c, dev, t, t_end);
     // dim 3 outside profiling: the last step overlaps its copy back with its stage 2
-    const bool overlap = c->dim == 3 && n_steps >= 1 && !c->profiling;
+    const bool overlap = c->dim == 3 && n_steps >= 1 && !c->profiling && c->var.manifest == 1;
     if (!rc) rc = run_steps(c, dev, overlap ? n_steps - 1 : n_steps);
     if (!rc && overlap) rc = last_step_overlapped(c, dev, host_out);
     if (rc) return rc;

@@ -27,6 +27,9 @@ struct StageLaunch {
     int riemann;        // HLLC wave speeds: 0 Davis, 1 pressure-based
     int zchunk0;        // first march chunk to launch
     int zchunks;        // march chunks to launch (0: all from zchunk0)
+    int manifest;       // dim 3: 0 nothing stored, 1 V stored by a pass, 2 face fluxes stored
+    void *vbuf[5];      // manifest V: the primitive planes
+    void *flux[3][5];   // manifest F: face-flux planes per axis
     double dr[3];
     double gamma;
     void *ctrl;
@@ -42,6 +45,7 @@ cudaError_t stage_f64(int dim, const StageLaunch &L, cudaStream_t st, bool prepa
 // Compiled tile shapes (both_pf: both staging depths compiled).
 struct TileShape {
     int prec, dim, bx, by, both_pf;
+    int manifest;  // also compiled in the manifest forms (V and F)
 };
 extern const TileShape kTiles[];
 extern const int kNumTiles;

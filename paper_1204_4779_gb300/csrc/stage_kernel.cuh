@@ -45,7 +45,31 @@ template <class T> struct StageArgs {
     T inv_dr[3];        // 1 / dr in the element type (the FP32 CFL signal multiplies)
     Gas<T> gas;
     Ctrl *ctrl;
+    T *flux[3][5];      // manifest F: face-flux planes per axis (faces of the cells' low sides
+                        // plus the grid's high boundary, x fastest, the face axis n_a + 1 long)
 };
+
+// CFL signal of one cell's new state, sum_a (|v_a| + c_s) / dr_a, folded into the running
+// maximum smax (NaN propagates); bad: rho <= 0 or p <= 0 seen.
+template <class T, int D>
+__device__ __forceinline__ void cfl_signal(const T (&un)[D + 2], const StageArgs<T> &A, T &smax,
+                                           bool &bad) {
+    constexpr int NV = D + 2;
+    T v[NV];
+    prim_of_cons<T, D>(un, v, A.gas);
+    T cs, s = T(0);
+    if constexpr (Arith<T>::exact) {
+        cs = sqrt(A.gas.g * v[NV - 1] / v[0]);
+#pragma unroll
+        for (int a = 0; a < D; ++a) s = s + (fabs(v[1 + a]) + cs) / A.dr[a];
+    } else {
+        cs = Arith<float>::sqrt_(A.gas.g * v[NV - 1] * Arith<float>::rcp(v[0]));
+#pragma unroll
+        for (int a = 0; a < D; ++a) s = fmaf(fabsf(v[1 + a]) + cs, A.inv_dr[a], s);
+    }
+    smax = (s > smax || s != s) ? s : smax;
+    bad |= !(v[0] > T(0)) || !(v[NV - 1] > T(0));
+}
 
 // Tile geometry.  dim 3: a BX x BY tile of the (x, y) plane marching along z.  dim 2: a BX x BY
 // tile (one plane, no march), or with BY = 1 a row of BX cells marching along y ("row tiles").
@@ -374,10 +398,14 @@ template <class T, int NT, int OCC = 2> struct MinBlocks {
 // Uses the caller's dynamic shared memory (StageShape::smem_bytes).  A caller that runs it
 // twice in one CTA puts a barrier between the calls: the second call's first shared-memory
 // writes may hit planes the first call's last reads still use.
-template <class T, int D, int BX, int BY, int STAGE, int PF, bool CFL>
+// MAN (dim 3 only): 0 = nothing stored in HBM between the parts of a stage; 1 = manifest V:
+// A.uin holds primitive planes (a pass stored V(U_in)), so loaded cells need no recovery;
+// 2 = manifest F: store every face flux in A.flux instead of updating (a pass applies them).
+template <class T, int D, int BX, int BY, int STAGE, int PF, bool CFL, int MAN = 0>
 __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int x0, int y0, int zb, int ze,
                                            unsigned char *smem_raw, T cx, T cy, T cz, T &smax,
                                            bool &bad) {
+    static_assert(MAN == 0 || D == 3, "the manifest forms are compiled for 3D grids");
     using S = StageShape<T, D, BX, BY>;
     using GM = Geom<D, BY>;
     constexpr int NV = S::NV, NT = S::NT, HX = S::HX, PL = S::PL, IN = GM::IN, MA = GM::MA;
@@ -391,6 +419,15 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int x0, int y0
     T *const sF1 = sF0 + NV * NF;
     const Gas<T> G = A.gas;
     const bool order2 = A.order == 2;
+    // V of a loaded cell: recovered from U, or already V (manifest V)
+    auto recover = [&](const T (&u)[NV], T (&v)[NV]) {
+        if constexpr (MAN == 1) {
+#pragma unroll
+            for (int k = 0; k < NV; ++k) v[k] = u[k];
+        } else {
+            prim_of_cons<T, D>(u, v, G);
+        }
+    };
 
     const int tid = threadIdx.x;
     const int tx = tid % BX, ty = tid / BX;
@@ -438,7 +475,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int x0, int y0
         for (int j = 0; j < HPT; ++j) {
             if (h_ok[j]) {
                 T vh[NV];
-                prim_of_cons<T, D>(ph[j], vh, G);
+                recover(ph[j], vh);
                 Cells<T, NV>::put(sV, PL, h_s[j], vh);
             }
         }
@@ -453,13 +490,13 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int x0, int y0
     if constexpr (MARCH) {
         T u[NV], Vm2[NV], Vm1[NV], dzm[NV];
         load_u(u, remap(zb - 2, nz, pz), own_off);
-        prim_of_cons<T, D>(u, Vm2, G);
+        recover(u, Vm2);
         load_u(u, remap(zb - 1, nz, pz), own_off);
-        prim_of_cons<T, D>(u, Vm1, G);
+        recover(u, Vm1);
         load_u(u, remap(zb, nz, pz), own_off);
-        prim_of_cons<T, D>(u, Vc, G);
+        recover(u, Vc);
         load_u(u, remap(zb + 1, nz, pz), own_off);
-        prim_of_cons<T, D>(u, Vn, G);
+        recover(u, Vn);
         minbee_slopes<T, NV>(Vm2, Vm1, Vc, order2, dzm);
         minbee_slopes<T, NV>(Vm1, Vc, Vn, order2, dzc);
         march_face<T, D>(Vm1, dzm, Vc, dzc, G, Fzm, A.riemann);
@@ -467,7 +504,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int x0, int y0
     } else {
         T u[NV];
         load_u(u, 0, own_off);
-        prim_of_cons<T, D>(u, Vc, G);
+        recover(u, Vc);
     }
 #pragma unroll
     for (int j = 0; j < HPT; ++j)
@@ -497,7 +534,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int x0, int y0
         T Vnn[NV];
         if constexpr (MARCH) {
             if constexpr (PF == 0) load_u(pown, remap(z + 2, nz, pz), own_off);
-            prim_of_cons<T, D>(pown, Vnn, G);  // V(z+2)
+            recover(pown, Vnn);  // V(z+2)
             if constexpr (PF == 1) {
                 if (z + 1 < ze) load_u(pown, remap(z + 3, nz, pz), own_off);
             }
@@ -550,26 +587,27 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int x0, int y0
                 zm[k] = MARCH ? Fzm[kk] : T(0);
                 zp[k] = MARCH ? Fzp[kk] : T(0);
             }
-            add_fluxes<T, NV, (IN >= 2), MARCH>(base, cx, fw, fe, cy, fs, fn, cz, zm, zp, un);
-            const int i = (MARCH ? z * pstride : 0) + y * nx + x;
+            if constexpr (MAN == 2) {
+                // face fluxes to HBM: each cell its low faces, the last cell of a line also
+                // the high face on the grid's boundary
+                const long long ix = ((long long)z * ny + y) * (nx + 1) + x;
+                const long long iy = ((long long)z * (ny + 1) + y) * nx + x;
+                const long long iz = ((long long)z * ny + y) * nx + x;
 #pragma unroll
-            for (int k = 0; k < NV; ++k) A.uout[k][i] = un[k];
-            if constexpr (STAGE == 2 && CFL) {
-                // CFL signal of the new state: sum_a (|v_a| + c_s) / dr_a
-                T v[NV];
-                prim_of_cons<T, D>(un, v, G);
-                T cs, s = T(0);
-                if constexpr (Arith<T>::exact) {
-                    cs = sqrt(G.g * v[NV - 1] / v[0]);
-#pragma unroll
-                    for (int a = 0; a < D; ++a) s = s + (fabs(v[1 + a]) + cs) / A.dr[a];
-                } else {
-                    cs = Arith<float>::sqrt_(G.g * v[NV - 1] * Arith<float>::rcp(v[0]));
-#pragma unroll
-                    for (int a = 0; a < D; ++a) s = fmaf(fabsf(v[1 + a]) + cs, A.inv_dr[a], s);
+                for (int k = 0; k < NV; ++k) {
+                    A.flux[0][k][ix] = fw[k];
+                    A.flux[1][k][iy] = fs[k];
+                    A.flux[2][k][iz] = zm[k];
+                    if (x == nx - 1) A.flux[0][k][ix + 1] = fe[k];
+                    if (y == ny - 1) A.flux[1][k][iy + nx] = fn[k];
+                    if (z == nz - 1) A.flux[2][k][iz + (long long)nx * ny] = zp[k];
                 }
-                smax = (s > smax || s != s) ? s : smax;
-                bad |= !(v[0] > T(0)) || !(v[NV - 1] > T(0));
+            } else {
+                add_fluxes<T, NV, (IN >= 2), MARCH>(base, cx, fw, fe, cy, fs, fn, cz, zm, zp, un);
+                const int i = (MARCH ? z * pstride : 0) + y * nx + x;
+#pragma unroll
+                for (int k = 0; k < NV; ++k) A.uout[k][i] = un[k];
+                if constexpr (STAGE == 2 && CFL) cfl_signal<T, D>(un, A, smax, bad);
             }
         }
         if constexpr (MARCH) {
@@ -588,7 +626,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int x0, int y0
 // issued one plane ahead of their use, 0 = each plane is loaded when it is staged.  FUSED
 // (stage 2): 1 = the CFL signal and the next dt are reduced in this kernel's epilogue, 0 = left
 // to a separate CFL pass.  OCC: resident CTAs per SM the register budget targets.
-template <class T, int D, int BX, int BY, int STAGE, int PF = 1, bool FUSED = true, int OCC = 2>
+template <class T, int D, int BX, int BY, int STAGE, int PF = 1, bool FUSED = true, int OCC = 2,
+          int MAN = 0>
 __global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY, OCC>::value))
     stage_kernel(const StageArgs<T> A) {
     using S = StageShape<T, D, BX, BY>;
@@ -609,9 +648,74 @@ __global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY, OCC>::value))
     const int ze = GM::march ? min(zb + A.march, A.n[GM::MA]) : 1;
     T smax = T(0);
     bool bad = false;
-    stage_tile<T, D, BX, BY, STAGE, PF, (STAGE == 2 && FUSED)>(A, x0, y0, zb, ze, smem_raw, cx, cy,
-                                                                 cz, smax, bad);
-    if constexpr (STAGE == 2 && FUSED) reduce_signal_and_finalize<T, S::NT>(ctrl, smax, bad, true, sRed);
+    constexpr bool CFL = STAGE == 2 && FUSED && MAN != 2;
+    stage_tile<T, D, BX, BY, STAGE, PF, CFL, MAN>(A, x0, y0, zb, ze, smem_raw, cx, cy, cz, smax, bad);
+    if constexpr (CFL) reduce_signal_and_finalize<T, S::NT>(ctrl, smax, bad, true, sRed);
+}
+
+// ---- the passes of the manifest forms (dim 3) ---------------------------------------------
+
+constexpr int kPassThreads = 256;
+
+// Manifest V: the primitive planes of the stage's input, V(U_in) -> A.uout, with the same
+// recovery the stage kernel applies to the cells it loads.
+template <class T>
+__global__ void __launch_bounds__(kPassThreads) manifest_v_kernel(const StageArgs<T> A) {
+    constexpr int D = 3, NV = 5;
+    const long long ncell = (long long)A.n[0] * A.n[1] * A.n[2];
+    for (long long i = (long long)blockIdx.x * kPassThreads + threadIdx.x; i < ncell;
+         i += (long long)gridDim.x * kPassThreads) {
+        T u[NV], v[NV];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) u[k] = __ldg(A.uin[k] + i);
+        prim_of_cons<T, D>(u, v, A.gas);
+#pragma unroll
+        for (int k = 0; k < NV; ++k) A.uout[k][i] = v[k];
+    }
+}
+
+// Manifest F: AddFlux from the stored face fluxes (Eq. eqAddFlux, the same arithmetic as the
+// fused stage kernel's update), with stage 2's CFL signal and dt reduction when FUSED.
+template <class T, int STAGE, bool FUSED>
+__global__ void __launch_bounds__(kPassThreads) addflux_kernel(const StageArgs<T> A) {
+    constexpr int D = 3, NV = 5;
+    __shared__ T sRed[2 * kPassThreads / 32];
+    Ctrl *ctrl = A.ctrl;
+    const double dt = __ldcg(&ctrl->dt);
+    if (!(dt > 0.0)) return;
+    const T cx = T(__ldcg(&ctrl->coef[STAGE - 1][0]));
+    const T cy = T(__ldcg(&ctrl->coef[STAGE - 1][1]));
+    const T cz = T(__ldcg(&ctrl->coef[STAGE - 1][2]));
+    const int nx = A.n[0], ny = A.n[1], nz = A.n[2];
+    const long long plane = (long long)nx * ny, ncell = plane * nz;
+    T smax = T(0);
+    bool bad = false;
+    for (long long i = (long long)blockIdx.x * kPassThreads + threadIdx.x; i < ncell;
+         i += (long long)gridDim.x * kPassThreads) {
+        const int x = (int)(i % nx);
+        const long long yz = i / nx;
+        const int y = (int)(yz % ny);
+        const long long z = yz / ny;
+        const long long ix = (z * ny + y) * (nx + 1) + x;
+        const long long iy = (z * (ny + 1) + y) * nx + x;
+        T base[NV], fw[NV], fe[NV], fs[NV], fn[NV], zm[NV], zp[NV], un[NV];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            base[k] = A.ubase[k][i];
+            fw[k] = A.flux[0][k][ix];
+            fe[k] = A.flux[0][k][ix + 1];
+            fs[k] = A.flux[1][k][iy];
+            fn[k] = A.flux[1][k][iy + nx];
+            zm[k] = A.flux[2][k][i];
+            zp[k] = A.flux[2][k][i + plane];
+        }
+        add_fluxes<T, NV, true, true>(base, cx, fw, fe, cy, fs, fn, cz, zm, zp, un);
+#pragma unroll
+        for (int k = 0; k < NV; ++k) A.uout[k][i] = un[k];
+        if constexpr (STAGE == 2 && FUSED) cfl_signal<T, D>(un, A, smax, bad);
+    }
+    if constexpr (STAGE == 2 && FUSED)
+        reduce_signal_and_finalize<T, kPassThreads>(ctrl, smax, bad, true, sRed);
 }
 
 }  // namespace hydro

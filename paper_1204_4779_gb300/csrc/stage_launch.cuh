@@ -22,6 +22,8 @@ template <class T> static StageArgs<T> make_stage_args(const StageLaunch &L) {
     }
     A.march = L.march;
     A.zchunk0 = L.zchunk0;
+    for (int a = 0; a < 3; ++a)
+        for (int k = 0; k < 5; ++k) A.flux[a][k] = static_cast<T *>(L.flux[a][k]);
     A.order = L.order == 1 ? 1 : 2;
     A.riemann = L.riemann;
     A.gas = make_gas<T>(L.gamma);
@@ -31,54 +33,94 @@ template <class T> static StageArgs<T> make_stage_args(const StageLaunch &L) {
 
 // The kernels of one (T, D, tile) for one staging depth PF and occupancy target OCC: stage 1,
 // stage 2 with the fused dt reduction, stage 2 without it.
-template <class T, int D, int BX, int BY, int PF, int OCC> struct StageKernels {
-    static constexpr auto s1 = stage_kernel<T, D, BX, BY, 1, PF, true, OCC>;
-    static constexpr auto s2 = stage_kernel<T, D, BX, BY, 2, PF, true, OCC>;
-    static constexpr auto s2_split = stage_kernel<T, D, BX, BY, 2, PF, false, OCC>;
+// MAN 2 (manifest F): s1 is the flux kernel of both stages (it stores fluxes and never updates).
+template <class T, int D, int BX, int BY, int PF, int OCC, int MAN = 0> struct StageKernels {
+    static constexpr auto s1 = stage_kernel<T, D, BX, BY, 1, PF, true, OCC, MAN>;
+    static constexpr auto s2 = stage_kernel<T, D, BX, BY, 2, PF, true, OCC, MAN>;
+    static constexpr auto s2_split = stage_kernel<T, D, BX, BY, 2, PF, false, OCC, MAN>;
 };
 
-template <class T, int D, int BX, int BY, int PF, int OCC = 2>
-static cudaError_t launch_stage_pf(const StageLaunch &L, const StageArgs<T> &A, cudaStream_t st) {
+// Grid of a manifest pass: enough CTAs to fill every SM several times.
+inline unsigned pass_blocks(long long ncell) {
+    long long b = (ncell + kPassThreads - 1) / kPassThreads;
+    return (unsigned)(b < 1 ? 1 : (b > 152LL * 8 ? 152LL * 8 : b));
+}
+
+template <class T, int D, int BX, int BY, int PF, int OCC = 2, int MAN = 0>
+static cudaError_t launch_stage_pf(const StageLaunch &L, const StageArgs<T> &A0, cudaStream_t st) {
     using S = StageShape<T, D, BX, BY>;
     using GM = Geom<D, BY>;
-    using K = StageKernels<T, D, BX, BY, PF, OCC>;
+    using K = StageKernels<T, D, BX, BY, PF, OCC, MAN>;
+    StageArgs<T> A = A0;
+    const long long ncell = (long long)A.n[0] * A.n[1] * A.n[2];
+    if constexpr (MAN == 1) {  // V(U_in) into the V planes, which the stage kernel then reads
+        StageArgs<T> P = A0;
+        for (int k = 0; k < 5; ++k) P.uout[k] = static_cast<T *>(L.vbuf[k]);
+        manifest_v_kernel<T><<<pass_blocks(ncell), kPassThreads, 0, st>>>(P);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        for (int k = 0; k < 5; ++k) A.uin[k] = static_cast<const T *>(L.vbuf[k]);
+    }
     const dim3 grid((unsigned)((A.n[0] + BX - 1) / BX),
                     (unsigned)((GM::IN >= 2) ? (A.n[1] + BY - 1) / BY : 1),
                     (unsigned)(GM::march ? (L.zchunks > 0 ? L.zchunks
                                                           : (A.n[GM::MA] + A.march - 1) / A.march - L.zchunk0)
                                          : 1));
     const size_t smem = S::smem_bytes;
-    if (L.stage == 1)
+    if constexpr (MAN == 2) {  // fluxes to HBM, then AddFlux from them
+        if (L.zchunk0 != 0 || L.zchunks != 0) return cudaErrorInvalidValue;  // whole grid only
         K::s1<<<grid, S::NT, smem, st>>>(A);
-    else if (L.split)
-        K::s2_split<<<grid, S::NT, smem, st>>>(A);
-    else
-        K::s2<<<grid, S::NT, smem, st>>>(A);
-    return cudaGetLastError();
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        if (L.stage == 1)
+            addflux_kernel<T, 1, true><<<pass_blocks(ncell), kPassThreads, 0, st>>>(A);
+        else if (L.split)
+            addflux_kernel<T, 2, false><<<pass_blocks(ncell), kPassThreads, 0, st>>>(A);
+        else
+            addflux_kernel<T, 2, true><<<pass_blocks(ncell), kPassThreads, 0, st>>>(A);
+        return cudaGetLastError();
+    } else {
+        if (L.stage == 1)
+            K::s1<<<grid, S::NT, smem, st>>>(A);
+        else if (L.split)
+            K::s2_split<<<grid, S::NT, smem, st>>>(A);
+        else
+            K::s2<<<grid, S::NT, smem, st>>>(A);
+        return cudaGetLastError();
+    }
 }
 
-template <class T, int D, int BX, int BY, int PF, int OCC = 2>
+template <class T, int D, int BX, int BY, int PF, int OCC = 2, int MAN = 0>
 static cudaError_t prepare_stage_pf() {
-    using K = StageKernels<T, D, BX, BY, PF, OCC>;
+    using K = StageKernels<T, D, BX, BY, PF, OCC, MAN>;
     const int smem = (int)StageShape<T, D, BX, BY>::smem_bytes;
     cudaError_t e = cudaFuncSetAttribute(K::s1, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(K::s2, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(K::s2_split, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if constexpr (MAN != 2) {  // the flux kernel is the only stage kernel of manifest F
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(K::s2, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(K::s2_split, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    }
     return e;
 }
 
-template <class T, int D, int BX, int BY, int PF, int OCC>
+template <class T, int D, int BX, int BY, int PF, int OCC, int MAN = 0>
 static cudaError_t run_or_prepare(const StageLaunch &L, cudaStream_t st, bool prepare_only) {
-    if (prepare_only) return prepare_stage_pf<T, D, BX, BY, PF, OCC>();
-    return launch_stage_pf<T, D, BX, BY, PF, OCC>(L, make_stage_args<T>(L), st);
+    if (prepare_only) return prepare_stage_pf<T, D, BX, BY, PF, OCC, MAN>();
+    return launch_stage_pf<T, D, BX, BY, PF, OCC, MAN>(L, make_stage_args<T>(L), st);
 }
 
 // Both staging depths and both occupancy targets exist only for marching tiles (dim 3, and the
 // row tiles of dim 2); one-plane tiles have nothing to look ahead to and small register needs.
-template <class T, int D, int BX, int BY, bool BOTH_PF>
+// The manifest forms (3D tiles compiled with them) exist for the look-ahead staging and the
+// default budget of the precision.
+template <class T, int D, int BX, int BY, bool BOTH_PF, bool MANIFEST = false>
 static cudaError_t dispatch_tile(const StageLaunch &L, cudaStream_t st, bool prepare_only) {
+    if constexpr (MANIFEST && D == 3) {
+        constexpr int OCC = sizeof(T) == 4 ? 3 : 2;
+        if (L.manifest == 1) return run_or_prepare<T, D, BX, BY, 1, OCC, 1>(L, st, prepare_only);
+        if (L.manifest == 2) return run_or_prepare<T, D, BX, BY, 1, OCC, 2>(L, st, prepare_only);
+    }
     if constexpr (BOTH_PF && Geom<D, BY>::march) {
         const bool occ3 = L.occupancy == 3;
         if (L.prefetch == 0)
@@ -95,3 +137,6 @@ static cudaError_t dispatch_tile(const StageLaunch &L, cudaStream_t st, bool pre
 // only the default one.
 #define HYDRO_STAGE_CASE(T, D, BX, BY, PF2) \
     if (L.tile_x == BX && L.tile_y == BY) return dispatch_tile<T, D, BX, BY, PF2>(L, st, prepare_only);
+// The same with the manifest forms compiled too (dim 3).
+#define HYDRO_STAGE_CASE_M(T, D, BX, BY, PF2) \
+    if (L.tile_x == BX && L.tile_y == BY) return dispatch_tile<T, D, BX, BY, PF2, true>(L, st, prepare_only);

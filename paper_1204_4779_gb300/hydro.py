@@ -26,7 +26,8 @@ HYDRO_F64, HYDRO_F32 = 0, 1
 # every symbol include/hydro.h declares
 EXPORTS = (
     "hydro_version", "hydro_strerror", "hydro_last_cuda_error", "hydro_variant_supported",
-    "hydro_workspace_bytes", "hydro_create", "hydro_get_variant", "hydro_destroy", "hydro_set_stream",
+    "hydro_workspace_bytes", "hydro_workspace_bytes_variant", "hydro_create", "hydro_get_variant",
+    "hydro_destroy", "hydro_set_stream",
     "hydro_step",
     "hydro_step_host", "hydro_set_scheme", "hydro_cfl_dt", "hydro_totals", "hydro_status", "hydro_prim_to_cons",
     "hydro_cons_to_prim", "hydro_set_profiling", "hydro_kernel_times", "hydro_step_static",
@@ -60,7 +61,7 @@ class State(ctypes.Structure):
 class Variant(ctypes.Structure):
     _fields_ = [("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32),
                 ("march", ctypes.c_int32), ("split", ctypes.c_int32), ("staging", ctypes.c_int32),
-                ("occupancy", ctypes.c_int32)]
+                ("occupancy", ctypes.c_int32), ("manifest", ctypes.c_int32)]
 
 
 _lib = None
@@ -88,6 +89,8 @@ def load_library(path: str = LIB_PATH, build_if_missing: bool = True):
             "hydro_last_cuda_error": ([], ctypes.c_char_p),
             "hydro_variant_supported": ([i32, i32, P(Variant)], ctypes.c_int),
             "hydro_workspace_bytes": ([P(Grid), i32, P(ctypes.c_size_t)], ctypes.c_int),
+            "hydro_workspace_bytes_variant": ([P(Grid), i32, P(Variant), P(ctypes.c_size_t)],
+                                              ctypes.c_int),
             "hydro_create": ([P(Grid), dbl, P(i32), i32, dbl, P(Variant), vp, ctypes.c_size_t, vp,
                               P(vp)], ctypes.c_int),
             "hydro_destroy": ([vp], ctypes.c_int),
@@ -166,9 +169,10 @@ def state_struct(t: torch.Tensor, nv: int) -> State:
 
 
 def variant_supported(dtype, dim: int, tile=(0, 0), march: int = 0, split: int = 0,
-                      staging: int = 0, occupancy: int = 0) -> bool:
+                      staging: int = 0, occupancy: int = 0, manifest: int = 0) -> bool:
     lib = load_library()
-    v = Variant(int(tile[0]), int(tile[1]), int(march), int(split), int(staging), int(occupancy))
+    v = Variant(int(tile[0]), int(tile[1]), int(march), int(split), int(staging), int(occupancy),
+                int(manifest))
     return bool(lib.hydro_variant_supported(_prec(dtype), dim, ctypes.byref(v)))
 
 
@@ -196,8 +200,8 @@ class Solver:
     """One context of libhydro.so on the current CUDA device.
 
     shape: cells per axis (nx, [ny, [nz]]); bc: per-axis "periodic"/"outflow" (or 0/1);
-    variant: dict(tile=(bx, by), march=m, split=0|1, staging=0|1|2, occupancy=0|2|3) or None for
-    the default.
+    variant: dict(tile=(bx, by), march=m, split=0|1|2, staging=0|1|2, occupancy=0|2|3,
+    manifest=0|1|2|3) or None for the default.
     """
 
     def __init__(self, shape, gamma: float, bc="periodic", dtype=torch.float32, cfl: float = 0.4,
@@ -220,16 +224,18 @@ class Solver:
             g.lo[a] = 0.0 if lo is None else float(lo[a]) if a < self.dim else 0.0
             g.hi[a] = 1.0 if hi is None else float(hi[a]) if a < self.dim else 1.0
         self.grid = g
-        nbytes = ctypes.c_size_t()
-        _check(self.lib.hydro_workspace_bytes(ctypes.byref(g), _prec(dtype), ctypes.byref(nbytes)),
-               "hydro_workspace_bytes")
-        self.workspace = torch.empty(int(nbytes.value), dtype=torch.uint8, device=self.device)
         var = None
         if variant:
             tile = variant.get("tile", (0, 0))
             var = Variant(int(tile[0]), int(tile[1]), int(variant.get("march", 0)),
                           int(variant.get("split", 0)), int(variant.get("staging", 0)),
-                          int(variant.get("occupancy", 0)))
+                          int(variant.get("occupancy", 0)), int(variant.get("manifest", 0)))
+        nbytes = ctypes.c_size_t()
+        _check(self.lib.hydro_workspace_bytes_variant(ctypes.byref(g), _prec(dtype),
+                                                      ctypes.byref(var) if var is not None else None,
+                                                      ctypes.byref(nbytes)),
+               "hydro_workspace_bytes_variant")
+        self.workspace = torch.empty(int(nbytes.value), dtype=torch.uint8, device=self.device)
         bcs = (ctypes.c_int32 * 3)(*(self.bc + [0] * (3 - self.dim)))
         ctx = ctypes.c_void_p()
         with torch.cuda.device(self.device):
@@ -256,7 +262,7 @@ class Solver:
         v = Variant()
         _check(self.lib.hydro_get_variant(self.ctx, ctypes.byref(v)), "hydro_get_variant")
         return {"tile": (v.tile_x, v.tile_y), "march": v.march, "split": v.split,
-                "staging": v.staging, "occupancy": v.occupancy}
+                "staging": v.staging, "occupancy": v.occupancy, "manifest": v.manifest}
 
     # -- helpers ---------------------------------------------------------------------------
     def empty_state(self) -> torch.Tensor:

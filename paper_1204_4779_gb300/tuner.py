@@ -48,6 +48,8 @@ MARCHES = [4, 8, 16, 32, 64, 128, 256]
 SPLITS = [2, 1]   # hydro_variant_t.split: 2 = fused dt reduction, 1 = separate CFL pass
 STAGINGS = [1, 2]
 OCCUPANCIES = [2, 3]
+MANIFESTS = [1, 2, 3]  # hydro_variant_t.manifest: 1 nothing stored, 2 V stored, 3 fluxes stored
+MANIFEST_TILES = [(16, 8), (32, 8), (16, 16)]  # 3D FP32 tiles compiled in the manifest forms
 
 
 def marching(dim: int, tile) -> bool:
@@ -62,9 +64,12 @@ class Space:
 
     @property
     def genes(self):
-        if self.dim >= 2:
-            return [("tile", TILES[self.dim]), ("march", MARCHES), ("split", SPLITS),
-                    ("staging", STAGINGS), ("occupancy", OCCUPANCIES)]
+        g = [("tile", TILES[self.dim]), ("march", MARCHES), ("split", SPLITS),
+             ("staging", STAGINGS), ("occupancy", OCCUPANCIES)]
+        if self.dim == 3:
+            return g + [("manifest", MANIFESTS)]
+        if self.dim == 2:
+            return g
         return [("tile", TILES[self.dim]), ("split", SPLITS)]
 
     @property
@@ -72,9 +77,16 @@ class Space:
         return [len(v) for _, v in self.genes]
 
     def canonical(self, genome):
-        """The genome with the genes its tile does not use set to their first values."""
+        """The genome with the genes its tile does not use set to their first values; in 3D a
+        manifest form only on the tiles compiled with it, with look-ahead staging and the
+        three-CTA budget (else nothing stored)."""
         if self.dim == 2 and not marching(2, TILES[2][genome[0]]):
             return (genome[0], 0, genome[2], 0, 0)
+        if self.dim == 3 and MANIFESTS[genome[5]] != 1:
+            if TILES[3][genome[0]] not in MANIFEST_TILES:
+                return tuple(genome[:5]) + (0,)
+            return (genome[0], genome[1], genome[2], STAGINGS.index(1), OCCUPANCIES.index(3),
+                    genome[5])
         return tuple(genome)
 
     def all_genomes(self):
@@ -94,7 +106,8 @@ class Space:
 
     def default_genome(self):
         if self.dim == 3:
-            d = {"tile": (16, 8), "march": 64, "split": 2, "staging": 1, "occupancy": 3}
+            d = {"tile": (16, 8), "march": 64, "split": 2, "staging": 1, "occupancy": 3,
+                 "manifest": 1}
         elif self.dim == 2:
             d = {"tile": (256, 1), "march": 16, "split": 2, "staging": 1, "occupancy": 3}
         else:
@@ -117,6 +130,7 @@ def features(space: Space, genome, shape) -> np.ndarray:
     f.append(1.0 if v.get("split", 2) == 1 else 0.0)
     f.append(1.0 if v.get("staging", 1) == 2 else 0.0)
     f.append(1.0 if v.get("occupancy", 2) == 3 else 0.0)
+    f += [1.0 if v.get("manifest", 1) == m else 0.0 for m in MANIFESTS[1:]]
     f += [1.0 if space.dim == d else 0.0 for d in (1, 2, 3)]
     n = list(shape) + [1] * (3 - len(shape))
     f += [math.log2(max(x, 1)) / 10.0 for x in n]
@@ -148,7 +162,10 @@ class Record:
     @staticmethod
     def from_json(s: str) -> "Record":
         d = json.loads(s)
-        return Record(d["dim"], tuple(d["shape"]), tuple(d["genome"]), d["mu"], d["sigma"],
+        genome = tuple(d["genome"])
+        if d["dim"] == 3 and len(genome) == 5:  # records from before the manifest gene
+            genome = genome + (0,)
+        return Record(d["dim"], tuple(d["shape"]), genome, d["mu"], d["sigma"],
                       d.get("ok", True), d.get("seconds", 0.0))
 
 
@@ -218,7 +235,8 @@ class Benchmark:
             S = hydro.Solver(self.shape, self.gamma, bc="periodic", dtype=self.dt, cfl=0.4,
                              variant=dict(tile=v["tile"], march=v.get("march", 0),
                                           split=v.get("split", 0), staging=v.get("staging", 0),
-                                          occupancy=v.get("occupancy", 0)))
+                                          occupancy=v.get("occupancy", 0),
+                                          manifest=v.get("manifest", 0)))
             self.U.copy_(self.U0)
             S.step(self.U, 1)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

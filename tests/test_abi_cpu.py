@@ -103,6 +103,15 @@ def test_variant_table():
     assert hydro.variant_supported(torch.float64, 2, (128, 1), 8)
     assert not hydro.variant_supported(torch.float64, 2, (256, 1))
     assert not hydro.variant_supported(torch.float32, 2, (32, 8), occupancy=3)
+    # the manifest forms: dim 3, compiled tiles, look-ahead staging, default budget
+    for m in (1, 2, 3):
+        assert hydro.variant_supported(torch.float32, 3, (16, 8), manifest=m)
+        assert hydro.variant_supported(torch.float64, 3, (32, 8), manifest=m)
+    assert not hydro.variant_supported(torch.float32, 3, (32, 4), manifest=2)
+    assert not hydro.variant_supported(torch.float32, 2, (256, 1), manifest=2)
+    assert not hydro.variant_supported(torch.float32, 3, (16, 8), staging=2, manifest=3)
+    assert not hydro.variant_supported(torch.float32, 3, (16, 8), occupancy=2, manifest=2)
+    assert not hydro.variant_supported(torch.float32, 3, (16, 8), manifest=4)
     assert not hydro.variant_supported(torch.float32, 4)
     assert hydro.variant_supported(torch.float32, 3, (16, 8), 32, split=1, staging=2)
     assert hydro.variant_supported(torch.float64, 3, (32, 8), 32, split=1)
@@ -113,3 +122,37 @@ def test_variant_table():
     assert hydro.variant_supported(torch.float32, 3, (32, 8), 64, occupancy=3)
     assert not hydro.variant_supported(torch.float64, 3, (32, 8), 64, occupancy=3)
     assert not hydro.variant_supported(torch.float32, 2, (32, 8), occupancy=3)
+    # the manifest forms: dim 3, compiled tiles, look-ahead staging, default budget
+    for m in (1, 2, 3):
+        assert hydro.variant_supported(torch.float32, 3, (16, 8), manifest=m)
+        assert hydro.variant_supported(torch.float64, 3, (32, 8), manifest=m)
+    assert not hydro.variant_supported(torch.float32, 3, (32, 4), manifest=2)
+    assert not hydro.variant_supported(torch.float32, 2, (256, 1), manifest=2)
+    assert not hydro.variant_supported(torch.float32, 3, (16, 8), staging=2, manifest=3)
+    assert not hydro.variant_supported(torch.float32, 3, (16, 8), occupancy=2, manifest=2)
+    assert not hydro.variant_supported(torch.float32, 3, (16, 8), manifest=4)
+
+
+def test_workspace_bytes_of_the_manifest_forms():
+    lib = hydro.load_library()
+    g = hydro.Grid()
+    g.dim = 3
+    for a, n in enumerate((40, 36, 30)):
+        g.n[a], g.lo[a], g.hi[a] = n, 0.0, 1.0
+    sizes = {}
+    for m in (1, 2, 3):
+        v = hydro.Variant(0, 0, 0, 0, 0, 0, m)
+        b = ctypes.c_size_t()
+        assert lib.hydro_workspace_bytes_variant(ctypes.byref(g), hydro.HYDRO_F32, ctypes.byref(v),
+                                                 ctypes.byref(b)) == 0
+        sizes[m] = b.value
+    base = ctypes.c_size_t()
+    assert lib.hydro_workspace_bytes(ctypes.byref(g), hydro.HYDRO_F32, ctypes.byref(base)) == 0
+    ncell = 40 * 36 * 30
+    assert sizes[1] == base.value
+    assert sizes[2] - sizes[1] >= 5 * ncell * 4                       # the V planes
+    faces = 41 * 36 * 30 + 40 * 37 * 30 + 40 * 36 * 31
+    assert sizes[3] - sizes[1] >= 5 * faces * 4                       # the face-flux planes
+    bad = hydro.Variant(32, 4, 0, 0, 0, 0, 2)
+    assert lib.hydro_workspace_bytes_variant(ctypes.byref(g), hydro.HYDRO_F32, ctypes.byref(bad),
+                                             ctypes.byref(base)) == hydro.HYDRO_EUNSUPPORTED

@@ -206,4 +206,17 @@ def test_resolved_default_variants():
         S = hydro.Solver(shape, 1.4, dtype=dt, variant=var)
         got = S.variant()
         S.close()
-        assert got == want, (shape, dt, var, got)
+        assert got == dict(want, manifest=1), (shape, dt, var, got)
+
+
+def test_host_stepping_with_a_manifest_form():
+    V = inputs.blast_3d(shape=(40, 36, 30), radius_cells=6.0)
+    U = gpu_state(V, 1.4, F32)
+    S = hydro.Solver((40, 36, 30), 1.4, dtype=F32, variant=dict(manifest=3, march=8))
+    Ud = U.clone()
+    td, nd = S.step(Ud, 3)
+    host = U.cpu().pin_memory()
+    out = torch.empty_like(host).pin_memory()
+    dev = torch.empty_like(U)
+    th, nh = S.step_host(dev, host, out, 3)
+    assert (th, nh) == (td, nd) and torch.equal(out, Ud.cpu())

@@ -221,3 +221,34 @@ def test_row_tiles_fp32_kh_1024_full_config():
     V = inputs.kh_2d(1024, seed=1204477901)
     e, _, _ = _l1_32(V, 5.0 / 3.0, (0, 0), 100, variant=dict(tile=(128, 1), march=32))
     assert e <= 1e-4
+
+
+# ---- the manifest forms (V or the face fluxes stored in HBM between the parts of a stage) ---
+
+@pytest.mark.parametrize("manifest", [2, 3])
+@pytest.mark.parametrize("split", [1, 2])
+@pytest.mark.parametrize("dtype,tile", [(F32, (16, 8)), (F32, (32, 8)), (F32, (16, 16)),
+                                        (F64, (32, 8))])
+def test_manifest_forms_are_the_same_step(dtype, tile, split, manifest):
+    """Storing V or the face fluxes changes where intermediates live, not the arithmetic: in
+    FP64 (no contraction) the same step bit for bit; in FP32 the compiler may fuse a product
+    of the recovery into its consumer when V stays in registers, so the forms agree to
+    rounding (ragged x, y and march chunks, time clipping on the last step)."""
+    V = inputs.blast_3d(shape=(37, 29, 23), radius_cells=5.0)
+    base = dict(tile=tile, march=6, split=split)
+    G0, t0, s0 = gpu_run(V, 1.4, (0, 1, 0), dtype, 0.4, 40, t_end=0.012, variant=base)
+    G1, t1, s1 = gpu_run(V, 1.4, (0, 1, 0), dtype, 0.4, 40, t_end=0.012,
+                         variant=dict(base, manifest=manifest))
+    assert s0 == s1
+    if dtype == F64:
+        assert t0 == t1 and np.array_equal(G0, G1)
+    else:
+        assert abs(t0 - t1) <= 1e-6 * t0
+        assert l1_rel(G1[0], G0[0]) <= 1e-6
+        assert np.max(np.abs(G1 - G0)) <= 1e-4 * np.max(np.abs(G0))
+
+
+@pytest.mark.parametrize("manifest", [2, 3])
+def test_manifest_forms_fp64_match_oracle(manifest):
+    V = inputs.smooth((21, 18, 19), seed=24)
+    _compare64(V, 1.4, (1, 0, 1), 0.4, 10, variant=dict(march=5, manifest=manifest))

@@ -18,8 +18,12 @@ def test_benchmark_records():
     b = T.Benchmark((40, 36, 33), reps=3, steps=2)
     r = b(b.space.default_genome())
     assert r.ok and r.mu > 0 and r.sigma >= 0
-    r2 = b((1, 2, 1, 1, 1))
-    assert r2.ok and r2.genome == (1, 2, 1, 1, 1)
+    r2 = b((1, 2, 1, 1, 1, 0))
+    assert r2.ok and r2.genome == (1, 2, 1, 1, 1, 0)
+    # a manifest form (fluxes stored) of a tile compiled with it
+    g3 = b.space.canonical((b.space.genes[0][1].index((16, 8)), 2, 0, 0, 1, 2))
+    r3 = b(g3)
+    assert r3.ok and b.space.variant(g3)["manifest"] == 3
     # 2D: the default row tile and a one-plane tile
     b2 = T.Benchmark((300, 77), reps=3, steps=2)
     for g in (b2.space.default_genome(), b2.space.all_genomes()[0]):

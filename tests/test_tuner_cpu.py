@@ -23,14 +23,23 @@ def test_triangulation_truth_table():
 
 def test_space_and_features():
     s3 = T.Space(3)
-    assert len(s3.all_genomes()) == 6 * 7 * 2 * 2 * 2
+    # 3D: every tile x march x split x staging x budget storing nothing, plus the two manifest
+    # forms on the three tiles compiled with them (look-ahead staging, three-CTA budget)
+    assert len(s3.all_genomes()) == 6 * 7 * 2 * 2 * 2 + 3 * 7 * 2 * 2
     assert s3.variant(s3.default_genome()) == {"tile": (16, 8), "march": 64, "split": 2,
-                                               "staging": 1, "occupancy": 3}
+                                               "staging": 1, "occupancy": 3, "manifest": 1}
+    for g in s3.all_genomes():
+        v = s3.variant(g)
+        if v["manifest"] != 1:
+            assert v["tile"] in T.MANIFEST_TILES and v["staging"] == 1 and v["occupancy"] == 3
+    old = T.Record.from_json('{"dim": 3, "shape": [64, 64, 64], "genome": [0, 4, 0, 0, 1], '
+                             '"mu": 1.0, "sigma": 0.0}')
+    assert old.genome == (0, 4, 0, 0, 1, 0) and s3.variant(old.genome)["manifest"] == 1
     f = T.features(s3, s3.default_genome(), (512, 512, 512))
     assert f.shape == (T.N_FEATURES,)
     f2 = T.features(T.Space(2), T.Space(2).default_genome(), (2048, 2048))
     assert f2.shape == (T.N_FEATURES,) and not np.array_equal(f, f2)
-    assert len({tuple(T.features(s3, g, (64, 64, 64))) for g in s3.all_genomes()}) == 336
+    assert len({tuple(T.features(s3, g, (64, 64, 64))) for g in s3.all_genomes()}) == 336 + 84
     # 2D: four one-plane tiles (tile and split genes only) and three row tiles with every gene
     s2 = T.Space(2)
     g2 = s2.all_genomes()
@@ -76,16 +85,17 @@ def test_births_are_new_and_exhaust_the_space():
 
 
 def synthetic_cups(space, genome, shape, noise_rng=None):
-    """A cost landscape with structure shared across grid sizes: tile and march matter most,
-    the split and staging a little; larger grids favour longer marches."""
+    """A cost landscape with structure shared across grid sizes: tile, march and the manifest
+    form matter most, the split and staging a little; larger grids favour longer marches."""
     v = space.variant(genome)
     tile_cost = {(32, 8): 0.12, (32, 4): 0.15, (64, 4): 0.1, (16, 16): 0.0, (32, 16): 0.2,
                  (16, 8): 0.3}[v["tile"]]
     nz = shape[2]
     best_march = min(256, max(4, nz // 4))
     march_cost = 0.05 * (math.log2(v["march"]) - math.log2(best_march)) ** 2
+    manifest_cost = {1: 0.0, 2: 0.15, 3: 0.35}[v.get("manifest", 1)]  # HBM round trips cost
     logt = (-23.0 + tile_cost + march_cost + 0.08 * (v["split"] == 1) + 0.04 * (v["staging"] == 2)
-            - 0.03 * (v["occupancy"] == 3))
+            - 0.03 * (v["occupancy"] == 3) + manifest_cost)
     if noise_rng is not None:
         logt += noise_rng.normal(0, 0.005)
     return math.exp(-logt)
@@ -141,7 +151,7 @@ def test_model_guided_search_gains_over_search_without_the_model():
     rng = np.random.default_rng(7)
     for sh in train_shapes:
         ev = _evaluator(space, sh, 11)
-        for g in rng.permutation(len(space.all_genomes()))[:60]:
+        for g in rng.permutation(len(space.all_genomes()))[:80]:
             records.append(ev(space.all_genomes()[g]))
     target = (512, 512, 512)
     truth = max(synthetic_cups(space, g, target) for g in space.all_genomes())
