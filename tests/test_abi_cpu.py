@@ -156,3 +156,26 @@ def test_workspace_bytes_of_the_manifest_forms():
     bad = hydro.Variant(32, 4, 0, 0, 0, 0, 2)
     assert lib.hydro_workspace_bytes_variant(ctypes.byref(g), hydro.HYDRO_F32, ctypes.byref(bad),
                                              ctypes.byref(base)) == hydro.HYDRO_EUNSUPPORTED
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/hydro.h is a C header: it compiles as C99 with -pedantic, warning-free, and every
+    type a signature uses is a plain C type."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use_header.c"
+    src.write_text('#include "hydro.h"\n'
+                   "int main(void) {\n"
+                   "    hydro_variant_t v = {0, 0, 0, 0, 0, 0, 0};\n"
+                   "    hydro_grid_t g;\n"
+                   "    (void)v; (void)g;\n"
+                   "    return hydro_version() > 0 ? 0 : 1;\n"
+                   "}\n")
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", inc,
+                        "-c", str(src), "-o", str(tmp_path / "use_header.o")],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
