@@ -130,7 +130,7 @@ def _bind(lib):
     lib.oracle_run.argtypes = [c_int, lp, dp, c_double, ip, c_double, dp, c_int, c_double,
                                dp, ip, c_int]
     lib.oracle_run_opt.argtypes = [c_int, lp, dp, c_double, ip, c_double, c_int, c_int, dp, c_int,
-                                   c_double, dp, ip, c_int]
+                                   c_double, dp, ip, c_int, c_int, c_double, c_double]
     lib.oracle_run_opt.restype = c_int
     lib.oracle_hllc_opt.argtypes = [c_int, c_int, c_double, c_int, dp, dp, dp]
     lib.oracle_hllc_opt.restype = None
@@ -242,11 +242,17 @@ def fluxes(U, gamma: float, bc=(0, 0, 0), dr=None):
         [n[b] + (1 if b == a else 0) for b in range(dim)]))) for a, o in enumerate(outs)]
 
 
+ANALYTIC_ENTROPY_WAVE, ANALYTIC_SOUND_WAVE = 1, 2
+
+
 def run(U, gamma: float, cfl: float, n_steps: int, bc=(0, 0, 0), t_end: float = 0.0,
         t0: float = 0.0, dr=None, threads: int = 1, check: bool = True, order: int = 2,
-        riemann: int = 0):
+        riemann: int = 0, analytic=None):
     """Advance a copy of U by up to n_steps midpoint-RK steps (order: reconstruction order 1
-    or 2; riemann: HLLC wave speeds, 0 Davis, 1 pressure-based).
+    or 2; riemann: HLLC wave speeds, 0 Davis, 1 pressure-based).  bc per axis: 0 periodic,
+    1 outflow, 2 the analytic solution analytic = (kind, theta, amplitude) substituted into the
+    ghost cells at each stage's time (kind: ANALYTIC_ENTROPY_WAVE or ANALYTIC_SOUND_WAVE, the
+    wave rotated by theta about (1/2, 1/2); section 4.3's convergence tests).
 
     Returns (U_new, t, steps_done, rc).  With t_end > 0 the last step is clipped onto t_end.
     """
@@ -255,13 +261,15 @@ def run(U, gamma: float, cfl: float, n_steps: int, bc=(0, 0, 0), t_end: float = 
     bcs = (ctypes.c_int * 3)(*(list(bc) + [0] * (3 - len(bc))))
     t = ctypes.c_double(t0)
     done = ctypes.c_int()
-    if order == 2 and riemann == 0:
+    ana = analytic or (0, 0.0, 0.0)
+    if order == 2 and riemann == 0 and analytic is None:
         rc = _load().oracle_run(dim, n, _dr(dim, n, dr), gamma, bcs, cfl, _dp(u), int(n_steps),
                                 float(t_end), ctypes.byref(t), ctypes.byref(done), int(threads))
     else:
         rc = _load().oracle_run_opt(dim, n, _dr(dim, n, dr), gamma, bcs, cfl, int(order),
                                     int(riemann), _dp(u), int(n_steps), float(t_end),
-                                    ctypes.byref(t), ctypes.byref(done), int(threads))
+                                    ctypes.byref(t), ctypes.byref(done), int(threads),
+                                    int(ana[0]), float(ana[1]), float(ana[2]))
     if check and rc not in (ORC_OK,):
         raise OracleError(f"oracle_run rc={rc}")
     return u, t.value, done.value, rc

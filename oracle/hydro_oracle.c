@@ -31,7 +31,9 @@
  *    |dy01| < |dy12|, dy12 otherwise, applied to the primitive variables V
  *    along the face normal only (Eq. eqInterpolateV).
  *  - Boundaries: periodic wrap, or outflow = zero-gradient copy of the nearest
- *    interior cell, into two ghost layers, refilled before every stage.
+ *    interior cell, into two ghost layers, refilled before every stage; or (the
+ *    convergence tests of section 4.3) the analytic solution substituted into the
+ *    ghost layers at the time of each stage (t for stage 1, t + dt/2 for stage 2).
  *  - Time: the last step is clipped so that t lands on t_end; a clipped step
  *    sets t = t_end exactly.
  *  - No positivity floors.
@@ -61,9 +63,11 @@ typedef struct {
     long g[3];       /* ghost offset per axis: NG on active axes, else 0 */
     double dr[3];    /* cell size per axis */
     double gamma;
-    int bc[3];       /* 0 periodic, 1 outflow */
+    int bc[3];       /* 0 periodic, 1 outflow, 2 analytic solution */
     long ncell;      /* interior cells */
     long npad;       /* padded cells */
+    int ana;         /* analytic solution of bc 2: 1 entropy wave, 2 sound wave */
+    double ana_theta, ana_amp;  /* its direction (radians from x) and amplitude */
 } grid_t;
 
 static int make_grid(grid_t *G, int dim, const long n[3], const double dr[3],
@@ -105,6 +109,7 @@ static long wrap(long i, long n) {
  * by axis; each pass covers the full padded extent of the other axes. */
 static void fill_ghosts(const grid_t *G, double *q) {
     for (int a = 0; a < G->dim; ++a) {
+        if (G->bc[a] == 2) continue; /* analytic: filled from the solution, all fields at once */
         long lo[3], hi[3];
         for (int b = 0; b < 3; ++b) {
             lo[b] = -G->g[b];
@@ -124,6 +129,56 @@ static void fill_ghosts(const grid_t *G, double *q) {
                     q[pidx(G, i0, i1, i2)] = q[pidx(G, src[0], src[1], src[2])];
                 }
     }
+}
+
+/* The analytic solutions of the convergence tests of section 4.3, rotated by theta about
+ * (1/2, 1/2): the coordinate along the wave s = (x - 1/2) cos(theta) + (y - 1/2) sin(theta) + 1/2
+ * and the phase 2 pi (s - t).
+ *  1 entropy wave: rho = 2 + sin(phase), v = (cos theta, sin theta), p = 1 (exact);
+ *  2 sound wave:   rho = gamma (1 + A sin(phase)), v = A sin(phase) (cos theta, sin theta),
+ *                  p = 1 + gamma A sin(phase) (sound speed 1 for rho = gamma, p = 1; exact to
+ *                  first order in the amplitude A). */
+static void analytic_prim(const grid_t *G, double x, double y, double t, double *V) {
+    const double pi = 3.14159265358979323846;
+    double c = cos(G->ana_theta), sn = sin(G->ana_theta);
+    double s = (x - 0.5) * c + (y - 0.5) * sn + 0.5;
+    double w = sin(2.0 * pi * (s - t));
+    int dim = G->dim;
+    double dir[3] = {c, sn, 0.0};
+    if (G->ana == 1) {
+        V[0] = 2.0 + w;
+        for (int a = 0; a < dim; ++a) V[1 + a] = dir[a];
+        V[dim + 1] = 1.0;
+    } else {
+        double A = G->ana_amp;
+        V[0] = G->gamma * (1.0 + A * w);
+        for (int a = 0; a < dim; ++a) V[1 + a] = A * w * dir[a];
+        V[dim + 1] = 1.0 + G->gamma * A * w;
+    }
+}
+
+static void cons_of_prim(int dim, double gamma, const double *V, double *U);
+
+/* Ghost cells outside the interior on an analytic axis: the conserved form of the analytic
+ * solution at the cell centre and time t. */
+static void fill_analytic(const grid_t *G, double *const *Upad, double t) {
+    int nv = G->dim + 2;
+    for (long i2 = -G->g[2]; i2 < G->n[2] + G->g[2]; ++i2)
+        for (long i1 = -G->g[1]; i1 < G->n[1] + G->g[1]; ++i1)
+            for (long i0 = -G->g[0]; i0 < G->n[0] + G->g[0]; ++i0) {
+                long c[3] = {i0, i1, i2};
+                int outside = 0;
+                for (int a = 0; a < G->dim; ++a)
+                    if (G->bc[a] == 2 && (c[a] < 0 || c[a] >= G->n[a])) outside = 1;
+                if (!outside) continue;
+                double V[5], U[5];
+                double x = (i0 + 0.5) * G->dr[0];
+                double y = G->dim >= 2 ? (i1 + 0.5) * G->dr[1] : 0.5;
+                analytic_prim(G, x, y, t, V);
+                cons_of_prim(G->dim, G->gamma, V, U);
+                long p = pidx(G, i0, i1, i2);
+                for (int k = 0; k < nv; ++k) Upad[k][p] = U[k];
+            }
 }
 
 /* ------------------------------------------------- variables (Eqs. 1-2) -- */
@@ -323,7 +378,7 @@ static long fidx(const grid_t *G, int a, const long c[3]) {
 
 /* Flux_a(U) for every axis: V = V(U); Interpolate -> (VR, VL); F = HLLC_a.
  * U_int holds interior planes (unpadded, caller layout). */
-static void flux_all_axes(work_t *W, double *const *U_int) {
+static void flux_all_axes(work_t *W, double *const *U_int, double t_stage) {
     const grid_t *G = &W->G;
     int nv = W->nv, dim = G->dim;
     /* load the stage input into the padded scratch and fill the ghosts */
@@ -335,6 +390,11 @@ static void flux_all_axes(work_t *W, double *const *U_int) {
                         U_int[k][(i2 * G->n[1] + i1) * G->n[0] + i0];
         fill_ghosts(G, W->U[k]);
     }
+    for (int a = 0; a < dim; ++a)
+        if (G->bc[a] == 2) {
+            fill_analytic(G, W->U, t_stage);
+            break;
+        }
     /* V0 = V(U0) on interior and ghost cells */
 #pragma omp parallel for schedule(static)
     for (long c = 0; c < G->npad; ++c) {
@@ -444,10 +504,10 @@ static int all_finite_positive(const grid_t *G, double *const *U) {
 /* One midpoint RK step (section 4.1):
  *   F0 = Flux(U0); U1 = AddFlux(dt/2, F0, U0); F1 = Flux(U1); U2 = AddFlux(dt, F1, U0)
  * U (in/out) holds U0 on entry and U2 on return. */
-static void rk_step(work_t *W, double *const *U, double *const *U1, double dt) {
-    flux_all_axes(W, U);
+static void rk_step(work_t *W, double *const *U, double *const *U1, double dt, double t) {
+    flux_all_axes(W, U, t);
     add_flux(W, 0.5 * dt, U, U1);
-    flux_all_axes(W, U1);
+    flux_all_axes(W, U1, t + 0.5 * dt);
     add_flux(W, dt, U, U);
 }
 
@@ -533,9 +593,14 @@ int oracle_fluxes(int dim, const long n[3], const double dr[3], double gamma,
         free_work(&W);
         return rc;
     }
+    for (int a = 0; a < dim; ++a)
+        if (bc[a] == 2) { /* no analytic solution is given here */
+            free_work(&W);
+            return ORC_EINVAL;
+        }
     double *P[5];
     split_planes((double *)U, dim + 2, G.ncell, P);
-    flux_all_axes(&W, P);
+    flux_all_axes(&W, P, 0.0);
     for (int a = 0; a < dim; ++a)
         for (int k = 0; k < dim + 2; ++k)
             memcpy(F_out[a] + (size_t)k * W.nface[a], W.F[a][k],
@@ -551,11 +616,17 @@ int oracle_fluxes(int dim, const long n[3], const double dr[3], double gamma,
  * rho <= 0 or p <= 0 (the state then holds that step's output). */
 int oracle_run_opt(int dim, const long n[3], const double dr[3], double gamma,
                    const int bc[3], double cfl, int order, int riemann, double *U, int n_steps,
-                   double t_end, double *t_inout, int *steps_done, int nthreads) {
+                   double t_end, double *t_inout, int *steps_done, int nthreads, int ana,
+                   double ana_theta, double ana_amp) {
     grid_t G;
     int rc = make_grid(&G, dim, n, dr, gamma, bc);
     if (rc) return rc;
     if ((order != 1 && order != 2) || (riemann != 0 && riemann != 1)) return ORC_EINVAL;
+    for (int a = 0; a < dim; ++a)
+        if (bc[a] < 0 || bc[a] > 2 || (bc[a] == 2 && ana != 1 && ana != 2)) return ORC_EINVAL;
+    G.ana = ana;
+    G.ana_theta = ana_theta;
+    G.ana_amp = ana_amp;
     set_threads(nthreads);
     work_t W;
     rc = alloc_work(&W, &G);
@@ -581,7 +652,7 @@ int oracle_run_opt(int dim, const long n[3], const double dr[3], double gamma,
             dt = t_end - t;
             clipped = 1;
         }
-        rk_step(&W, P, P1, dt);
+        rk_step(&W, P, P1, dt, t);
         t = clipped ? t_end : t + dt;
         ++done;
         if (!all_finite_positive(&G, P)) {
@@ -600,7 +671,7 @@ int oracle_run(int dim, const long n[3], const double dr[3], double gamma,
                const int bc[3], double cfl, double *U, int n_steps, double t_end,
                double *t_inout, int *steps_done, int nthreads) {
     return oracle_run_opt(dim, n, dr, gamma, bc, cfl, 2, 0, U, n_steps, t_end, t_inout,
-                          steps_done, nthreads);
+                          steps_done, nthreads, 0, 0.0, 0.0);
 }
 
 /* fixed-order pairwise sum of x[0..n) */

@@ -129,6 +129,36 @@ def sound_wave(shape_xyz, gamma: float = 1.4, amp: float = 1e-5, k=(1,)) -> np.n
     return V
 
 
+def oblique_wave(shape_xyz, kind: str, theta: float, t: float = 0.0, amp: float = 1.0,
+                 gamma: float = 1.4) -> np.ndarray:
+    """The convergence-test waves of section 4.3 on the unit square (1D: the line y = 1/2),
+    travelling at angle theta from the x axis, at time t: with the coordinate along the wave
+    s = (x - 1/2) cos theta + (y - 1/2) sin theta + 1/2 and w = sin(2 pi (s - t)),
+    kind "entropy": rho = 2 + amp w, v = (cos theta, sin theta), p = 1;
+    kind "sound":   rho = gamma (1 + amp w), v = amp w (cos theta, sin theta), p = 1 + gamma amp w.
+    Unlike entropy_wave / sound_wave the grid need not be periodic along the wave."""
+    dim = len(shape_xyz)
+    X = _mesh(tuple(shape_xyz))
+    x = X[0]
+    y = X[1] if dim >= 2 else np.full_like(x, 0.5)
+    d = (math.cos(theta), math.sin(theta))
+    w = np.sin(2.0 * math.pi * ((x - 0.5) * d[0] + (y - 0.5) * d[1] + 0.5 - t))
+    V = np.empty((dim + 2,) + tuple(reversed(shape_xyz)))
+    if kind == "entropy":
+        V[0] = 2.0 + amp * w
+        for a in range(dim):
+            V[1 + a] = d[a]
+        V[dim + 1] = 1.0
+    elif kind == "sound":
+        V[0] = gamma * (1.0 + amp * w)
+        for a in range(dim):
+            V[1 + a] = amp * w * d[a]
+        V[dim + 1] = 1.0 + gamma * amp * w
+    else:
+        raise ValueError(kind)
+    return V
+
+
 def uniform(shape_xyz, rho: float = 1.0, v=(0.0, 0.0, 0.0), p: float = 1.0) -> np.ndarray:
     dim = len(shape_xyz)
     V = np.empty((dim + 2,) + tuple(reversed(shape_xyz)))

@@ -37,6 +37,11 @@ MUTANTS = [
     ("star_contact_speed_sign", "(pr - pl + rl * ul * (SL - ul) - rr * ur * (SR - ur))",
      "(pl - pr + rl * ul * (SL - ul) - rr * ur * (SR - ur))"),
     ("hllc_side_choice", "int left = 0.0 <= Ss;", "int left = 0.0 <= -Ss;"),
+    ("analytic_stage2_time", "flux_all_axes(W, U1, t + 0.5 * dt);", "flux_all_axes(W, U1, t);"),
+    ("analytic_phase_sign", "sin(2.0 * pi * (s - t))", "sin(2.0 * pi * (s + t))"),
+    ("analytic_rotation_sign", "(y - 0.5) * sn + 0.5", "(y - 0.5) * -sn + 0.5"),
+    ("analytic_ghost_centre", "double x = (i0 + 0.5) * G->dr[0];", "double x = (i0 + 1.0) * G->dr[0];"),
+    ("analytic_sound_pressure", "V[dim + 1] = 1.0 + G->gamma * A * w;", "V[dim + 1] = 1.0 + A * w;"),
 ]
 
 
@@ -137,9 +142,22 @@ def _battery():
         T0, T1 = oracle.totals(U), oracle.totals(U2)
         return abs(T1[0] - T0[0]) < 1e-13 * T0[0] and abs(T1[4] - T0[4]) < 1e-13 * T0[4]
 
+    def analytic():
+        from test_oracle_analytic_bc import analytic_upwind_residual
+        if analytic_upwind_residual((12, 10)) > 1e-13:
+            return False
+        # sound wave at 60 degrees: second-order accurate with exact inflow and outflow values
+        n, A = 32, 1e-5
+        V = inputs.oblique_wave((n, n), "sound", math.pi / 3, amp=A)
+        U2, *_ = oracle.run(oracle.prim_to_cons(V, G), G, 0.4, 10 ** 6, bc=(2, 2), t_end=0.25,
+                            analytic=(oracle.ANALYTIC_SOUND_WAVE, math.pi / 3, A), check=False)
+        E = inputs.oblique_wave((n, n), "sound", math.pi / 3, t=0.25, amp=A)
+        return np.mean(np.abs(oracle.cons_to_prim(U2, G)[0] - E[0])) < 1.7e-2 * A
+
     for name, fn in [("sod", sod), ("entropy", entropy), ("ywave", ywave), ("contact", contact),
                      ("consistency", consistency), ("moving_contact", moving_contact),
-                     ("euler_def", euler_def), ("star_rh", star_rh), ("limiter", limiter), ("cfl", cfl), ("conservation", conservation)]:
+                     ("euler_def", euler_def), ("star_rh", star_rh), ("limiter", limiter), ("cfl", cfl), ("conservation", conservation),
+                     ("analytic", analytic)]:
         check(name, fn)
     return fails
 
