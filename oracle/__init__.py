@@ -134,6 +134,8 @@ def _bind(lib):
     lib.oracle_run_opt.restype = c_int
     lib.oracle_hllc_opt.argtypes = [c_int, c_int, c_double, c_int, dp, dp, dp]
     lib.oracle_hllc_opt.restype = None
+    lib.oracle_sod_sample.argtypes = [c_double, c_double, dp, dp]
+    lib.oracle_sod_sample.restype = None
     lib.oracle_totals.argtypes = [c_int, lp, dp, dp, dp]
     for f in ("oracle_prim_to_cons", "oracle_cons_to_prim", "oracle_cfl_dt", "oracle_fluxes",
               "oracle_run", "oracle_totals", "oracle_has_openmp", "oracle_max_threads"):
@@ -242,7 +244,16 @@ def fluxes(U, gamma: float, bc=(0, 0, 0), dr=None):
         [n[b] + (1 if b == a else 0) for b in range(dim)]))) for a, o in enumerate(outs)]
 
 
-ANALYTIC_ENTROPY_WAVE, ANALYTIC_SOUND_WAVE = 1, 2
+ANALYTIC_ENTROPY_WAVE, ANALYTIC_SOUND_WAVE, ANALYTIC_SHOCK_TUBE = 1, 2, 3
+
+
+def sod_sample(gamma: float, xi: float):
+    """Exact solution of Sod's shock tube (1, 0, 1) | (0.125, 0, 0.1) at xi = (x - x0) / t:
+    ((rho, u, p), (p*, u*))."""
+    out = np.zeros(3)
+    star = np.zeros(2)
+    _load().oracle_sod_sample(float(gamma), float(xi), _dp(out), _dp(star))
+    return out, star
 
 
 def run(U, gamma: float, cfl: float, n_steps: int, bc=(0, 0, 0), t_end: float = 0.0,
@@ -251,8 +262,9 @@ def run(U, gamma: float, cfl: float, n_steps: int, bc=(0, 0, 0), t_end: float = 
     """Advance a copy of U by up to n_steps midpoint-RK steps (order: reconstruction order 1
     or 2; riemann: HLLC wave speeds, 0 Davis, 1 pressure-based).  bc per axis: 0 periodic,
     1 outflow, 2 the analytic solution analytic = (kind, theta, amplitude) substituted into the
-    ghost cells at each stage's time (kind: ANALYTIC_ENTROPY_WAVE or ANALYTIC_SOUND_WAVE, the
-    wave rotated by theta about (1/2, 1/2); section 4.3's convergence tests).
+    ghost cells at each stage's time (kind: ANALYTIC_ENTROPY_WAVE, ANALYTIC_SOUND_WAVE or
+    ANALYTIC_SHOCK_TUBE, the solution rotated by theta about (1/2, 1/2); section 4.3's
+    convergence tests).
 
     Returns (U_new, t, steps_done, rc).  With t_end > 0 the last step is clipped onto t_end.
     """

@@ -33,7 +33,8 @@
  *  - Boundaries: periodic wrap, or outflow = zero-gradient copy of the nearest
  *    interior cell, into two ghost layers, refilled before every stage; or (the
  *    convergence tests of section 4.3) the analytic solution substituted into the
- *    ghost layers at the time of each stage (t for stage 1, t + dt/2 for stage 2).
+ *    ghost layers at the time of each stage (t for stage 1, t + dt/2 for stage 2): the
+ *    entropy and sound waves, or Sod's shock tube (its exact Riemann solution).
  *  - Time: the last step is clipped so that t lands on t_end; a clipped step
  *    sets t = t_end exactly.
  *  - No positivity floors.
@@ -68,6 +69,7 @@ typedef struct {
     long npad;       /* padded cells */
     int ana;         /* analytic solution of bc 2: 1 entropy wave, 2 sound wave */
     double ana_theta, ana_amp;  /* its direction (radians from x) and amplitude */
+    double ana_ps, ana_us;      /* shock tube: star pressure and velocity */
 } grid_t;
 
 static int make_grid(grid_t *G, int dim, const long n[3], const double dr[3],
@@ -131,20 +133,119 @@ static void fill_ghosts(const grid_t *G, double *q) {
     }
 }
 
+/* ------------------------------------- exact Riemann solution (Sod's tube) -- */
+
+/* The exact solution of the Riemann problem of an ideal gas (Toro, Riemann Solvers and
+ * Numerical Methods for Fluid Dynamics, ch. 4): across the left and right waves the pressure
+ * p* and velocity u* of the star region satisfy f_L(p*) + f_R(p*) + u_R - u_L = 0 with
+ *   f_K(p) = (p - p_K) sqrt(A_K / (p + B_K)),  A_K = 2 / ((gamma+1) rho_K),
+ *            B_K = (gamma-1)/(gamma+1) p_K                         if p > p_K (shock),
+ *   f_K(p) = 2 a_K / (gamma-1) ((p / p_K)^((gamma-1)/(2 gamma)) - 1) otherwise (rarefaction),
+ * and u* = (u_L + u_R)/2 + (f_R(p*) - f_L(p*))/2.  f_L + f_R is increasing in p, so p* is found
+ * by bisection. */
+static double riemann_f(double p, double rk, double pk, double g) {
+    if (p > pk) {
+        double A = 2.0 / ((g + 1.0) * rk), B = (g - 1.0) / (g + 1.0) * pk;
+        return (p - pk) * sqrt(A / (p + B));
+    }
+    double a = sqrt(g * pk / rk);
+    return 2.0 * a / (g - 1.0) * (pow(p / pk, (g - 1.0) / (2.0 * g)) - 1.0);
+}
+
+static void riemann_star(const double L[3], const double R[3], double g, double *ps, double *us) {
+    double lo = 0.0, hi = L[2] > R[2] ? L[2] : R[2];
+    while (riemann_f(hi, L[0], L[2], g) + riemann_f(hi, R[0], R[2], g) + R[1] - L[1] < 0.0)
+        hi *= 2.0;
+    for (int it = 0; it < 200; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break; /* adjacent doubles */
+        if (riemann_f(mid, L[0], L[2], g) + riemann_f(mid, R[0], R[2], g) + R[1] - L[1] < 0.0)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    *ps = 0.5 * (lo + hi);
+    *us = 0.5 * (L[1] + R[1]) + 0.5 * (riemann_f(*ps, R[0], R[2], g) - riemann_f(*ps, L[0], L[2], g));
+}
+
+/* (rho, u, p) of the self-similar solution at xi = (x - x0) / t.  One side of the contact
+ * (speed u*): with side sign q = -1 (left) or +1 (right) the outer state K, the wave between K
+ * and the star region is a shock of speed u_K + q a_K sqrt((gamma+1)/(2 gamma) p* / p_K +
+ * (gamma-1)/(2 gamma)) if p* > p_K, else a rarefaction with head u_K + q a_K, tail
+ * u* + q a_K (p* / p_K)^((gamma-1)/(2 gamma)) and, inside the fan, the isentropic state with
+ * u = 2/(gamma+1) (-q a_K + (gamma-1)/2 u_K + xi).  At a discontinuity the state on the
+ * outer (K) side is taken, and at the contact the left star state. */
+static void riemann_sample(const double L[3], const double R[3], double g, double ps, double us,
+                           double xi, double out[3]) {
+    int right = xi > us;
+    const double *K = right ? R : L;
+    double q = right ? 1.0 : -1.0;
+    double a = sqrt(g * K[2] / K[0]);
+    if (ps > K[2]) {
+        double S = K[1] + q * a * sqrt((g + 1.0) / (2.0 * g) * ps / K[2] + (g - 1.0) / (2.0 * g));
+        if (q * (xi - S) >= 0.0) { /* outside the shock */
+            out[0] = K[0], out[1] = K[1], out[2] = K[2];
+        } else {
+            double r = ps / K[2], m = (g - 1.0) / (g + 1.0);
+            out[0] = K[0] * (r + m) / (m * r + 1.0), out[1] = us, out[2] = ps;
+        }
+        return;
+    }
+    double head = K[1] + q * a;
+    double astar = a * pow(ps / K[2], (g - 1.0) / (2.0 * g));
+    double tail = us + q * astar;
+    if (q * (xi - head) >= 0.0) {
+        out[0] = K[0], out[1] = K[1], out[2] = K[2];
+    } else if (q * (xi - tail) <= 0.0) {
+        out[0] = K[0] * pow(ps / K[2], 1.0 / g), out[1] = us, out[2] = ps;
+    } else {
+        double u = 2.0 / (g + 1.0) * (-q * a + 0.5 * (g - 1.0) * K[1] + xi);
+        double c = q * (xi - u); /* sound speed in the fan: xi = u + q c */
+        out[0] = K[0] * pow(c / a, 2.0 / (g - 1.0));
+        out[1] = u;
+        out[2] = K[2] * pow(c / a, 2.0 * g / (g - 1.0));
+    }
+}
+
+/* Sod's shock tube of section 4.3: (rho, u, p) = (1, 0, 1) | (0.125, 0, 0.1). */
+static const double SOD_L[3] = {1.0, 0.0, 1.0}, SOD_R[3] = {0.125, 0.0, 0.1};
+
+/* Exact Sod solution at xi for the tests: out = (rho, u, p); also p*, u*. */
+void oracle_sod_sample(double gamma, double xi, double out[3], double star[2]) {
+    double ps, us;
+    riemann_star(SOD_L, SOD_R, gamma, &ps, &us);
+    riemann_sample(SOD_L, SOD_R, gamma, ps, us, xi, out);
+    if (star) star[0] = ps, star[1] = us;
+}
+
 /* The analytic solutions of the convergence tests of section 4.3, rotated by theta about
  * (1/2, 1/2): the coordinate along the wave s = (x - 1/2) cos(theta) + (y - 1/2) sin(theta) + 1/2
  * and the phase 2 pi (s - t).
  *  1 entropy wave: rho = 2 + sin(phase), v = (cos theta, sin theta), p = 1 (exact);
  *  2 sound wave:   rho = gamma (1 + A sin(phase)), v = A sin(phase) (cos theta, sin theta),
  *                  p = 1 + gamma A sin(phase) (sound speed 1 for rho = gamma, p = 1; exact to
- *                  first order in the amplitude A). */
+ *                  first order in the amplitude A);
+ *  3 shock tube:   Sod's problem with the discontinuity at s = 1/2, the exact solution at
+ *                  xi = (s - 1/2) / t (t = 0: the left state for s < 1/2, else the right one),
+ *                  its velocity along (cos theta, sin theta). */
 static void analytic_prim(const grid_t *G, double x, double y, double t, double *V) {
     const double pi = 3.14159265358979323846;
     double c = cos(G->ana_theta), sn = sin(G->ana_theta);
     double s = (x - 0.5) * c + (y - 0.5) * sn + 0.5;
-    double w = sin(2.0 * pi * (s - t));
     int dim = G->dim;
     double dir[3] = {c, sn, 0.0};
+    if (G->ana == 3) {
+        double W[3];
+        if (t > 0.0)
+            riemann_sample(SOD_L, SOD_R, G->gamma, G->ana_ps, G->ana_us, (s - 0.5) / t, W);
+        else
+            for (int k = 0; k < 3; ++k) W[k] = s < 0.5 ? SOD_L[k] : SOD_R[k];
+        V[0] = W[0];
+        for (int a = 0; a < dim; ++a) V[1 + a] = W[1] * dir[a];
+        V[dim + 1] = W[2];
+        return;
+    }
+    double w = sin(2.0 * pi * (s - t));
     if (G->ana == 1) {
         V[0] = 2.0 + w;
         for (int a = 0; a < dim; ++a) V[1 + a] = dir[a];
@@ -623,10 +724,11 @@ int oracle_run_opt(int dim, const long n[3], const double dr[3], double gamma,
     if (rc) return rc;
     if ((order != 1 && order != 2) || (riemann != 0 && riemann != 1)) return ORC_EINVAL;
     for (int a = 0; a < dim; ++a)
-        if (bc[a] < 0 || bc[a] > 2 || (bc[a] == 2 && ana != 1 && ana != 2)) return ORC_EINVAL;
+        if (bc[a] < 0 || bc[a] > 2 || (bc[a] == 2 && (ana < 1 || ana > 3))) return ORC_EINVAL;
     G.ana = ana;
     G.ana_theta = ana_theta;
     G.ana_amp = ana_amp;
+    if (ana == 3) riemann_star(SOD_L, SOD_R, gamma, &G.ana_ps, &G.ana_us);
     set_threads(nthreads);
     work_t W;
     rc = alloc_work(&W, &G);

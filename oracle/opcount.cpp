@@ -50,6 +50,7 @@ static inline bool isfinite(counted a) { return std::isfinite(a.v); }  // a chec
 // boundary values of the analytic test solutions, not part of the per-cell method: not counted
 static inline counted sin(counted a) { return std::sin(a.v); }
 static inline counted cos(counted a) { return std::cos(a.v); }
+static inline counted pow(counted a, counted b) { return std::pow(a.v, b.v); }
 
 #define double counted
 extern "C" {

@@ -135,8 +135,10 @@ def oblique_wave(shape_xyz, kind: str, theta: float, t: float = 0.0, amp: float 
     travelling at angle theta from the x axis, at time t: with the coordinate along the wave
     s = (x - 1/2) cos theta + (y - 1/2) sin theta + 1/2 and w = sin(2 pi (s - t)),
     kind "entropy": rho = 2 + amp w, v = (cos theta, sin theta), p = 1;
-    kind "sound":   rho = gamma (1 + amp w), v = amp w (cos theta, sin theta), p = 1 + gamma amp w.
-    Unlike entropy_wave / sound_wave the grid need not be periodic along the wave."""
+    kind "sound":   rho = gamma (1 + amp w), v = amp w (cos theta, sin theta), p = 1 + gamma amp w;
+    kind "shock_tube" (t = 0 only): Sod's states (rho, v, p) = (1, 0, 1) where s < 1/2, else
+    (0.125, 0, 0.1).  Unlike entropy_wave / sound_wave the grid need not be periodic along the
+    wave."""
     dim = len(shape_xyz)
     X = _mesh(tuple(shape_xyz))
     x = X[0]
@@ -144,6 +146,14 @@ def oblique_wave(shape_xyz, kind: str, theta: float, t: float = 0.0, amp: float 
     d = (math.cos(theta), math.sin(theta))
     w = np.sin(2.0 * math.pi * ((x - 0.5) * d[0] + (y - 0.5) * d[1] + 0.5 - t))
     V = np.empty((dim + 2,) + tuple(reversed(shape_xyz)))
+    if kind == "shock_tube":
+        if t != 0.0:
+            raise ValueError("the shock tube's initial states only")
+        left = (x - 0.5) * d[0] + (y - 0.5) * d[1] < 0.0
+        V[0] = np.where(left, 1.0, 0.125)
+        V[1:dim + 1] = 0.0
+        V[dim + 1] = np.where(left, 1.0, 0.1)
+        return V
     if kind == "entropy":
         V[0] = 2.0 + amp * w
         for a in range(dim):
