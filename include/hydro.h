@@ -57,7 +57,13 @@ enum {
     HYDRO_EUNSUPPORTED = 5 /* valid request that this build has no kernel for */
 };
 
-typedef enum { HYDRO_BC_PERIODIC = 0, HYDRO_BC_OUTFLOW = 1 } hydro_bc_t;
+typedef enum { HYDRO_BC_PERIODIC = 0, HYDRO_BC_OUTFLOW = 1, HYDRO_BC_ANALYTIC = 2 } hydro_bc_t;
+/* Analytic solutions of HYDRO_BC_ANALYTIC (section 4.3 convergence tests; hydro_set_analytic). */
+typedef enum {
+    HYDRO_ANALYTIC_ENTROPY_WAVE = 1,
+    HYDRO_ANALYTIC_SOUND_WAVE = 2,
+    HYDRO_ANALYTIC_SHOCK_TUBE = 3
+} hydro_analytic_t;
 typedef enum { HYDRO_F64 = 0, HYDRO_F32 = 1 } hydro_prec_t;
 
 /* Grid: dim in {1,2,3}; n[a] >= 1 cells on active axes (n[a] is ignored and taken as 1 on
@@ -150,7 +156,12 @@ int hydro_workspace_bytes_variant(const hydro_grid_t *grid, int32_t prec,
  *   grid      grid and box (copied)
  *   gamma     ratio of specific heats, > 1
  *   bc        per-axis boundary condition (hydro_bc_t); entries >= dim ignored.  Periodic
- *             wraps; outflow copies the nearest interior cell into the two ghost layers
+ *             wraps; outflow copies the nearest interior cell into the two ghost layers;
+ *             analytic (dim 1 and 2 only, else HYDRO_EUNSUPPORTED) fills the two ghost layers
+ *             outside that axis's ends with the exact solution set by hydro_set_analytic at
+ *             the time of each RK stage.  Analytic boundaries run on one-plane tiles: with no
+ *             tile given a 2D context takes 32 x 8; a row tile (tile_y = 1) is
+ *             HYDRO_EUNSUPPORTED
  *   prec      HYDRO_F32 (whole stencil in FP32; dt, time and totals in FP64) or HYDRO_F64
  *   cfl       Courant number, 0 < cfl
  *   variant   kernel variant or NULL for the default
@@ -167,6 +178,23 @@ int hydro_create(const hydro_grid_t *grid, double gamma, const int32_t bc[3], in
 int hydro_get_variant(const hydro_ctx_t *ctx, hydro_variant_t *out);
 
 int hydro_destroy(hydro_ctx_t *ctx);
+
+/* The exact solution the analytic boundaries substitute (section 4.3: the tests' domain is
+ * the unit square and the solution is given outside it at every time).  With the coordinate
+ * along the wave s = (x - 1/2) cos(theta) + (y - 1/2) sin(theta) + 1/2 (dim 1: y = 1/2) and
+ * w = sin(2 pi (s - t)), at the ghost-cell centres x = lo + (i + 1/2) dr:
+ *   HYDRO_ANALYTIC_ENTROPY_WAVE: rho = 2 + w, v = (cos theta, sin theta), p = 1
+ *   HYDRO_ANALYTIC_SOUND_WAVE:   rho = gamma (1 + A w), v = A w (cos theta, sin theta),
+ *                                p = 1 + gamma A w   (A = amplitude)
+ *   HYDRO_ANALYTIC_SHOCK_TUBE:   Sod's problem, (rho, u, p) = (1, 0, 1) for s < 1/2 and
+ *                                (0.125, 0, 0.1) otherwise at t = 0, and its exact similarity
+ *                                solution in (s - 1/2) / t after, u the velocity along
+ *                                (cos theta, sin theta)
+ * evaluated in FP64, converted to conserved variables and rounded to the precision of the
+ * context.  Stage 1 of a step takes the solution at t, stage 2 at t + dt/2.  Until it is
+ * called, steps of a context with analytic boundaries return HYDRO_EINVAL.  Errors:
+ * HYDRO_EINVAL (no analytic axis, unknown kind, non-finite theta or amplitude). */
+int hydro_set_analytic(hydro_ctx_t *ctx, int32_t kind, double theta, double amplitude);
 
 /* Change the stream later calls are ordered on. */
 int hydro_set_stream(hydro_ctx_t *ctx, void *stream);

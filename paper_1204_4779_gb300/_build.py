@@ -37,6 +37,7 @@ UNITS = {
     "mlp.cu": [],
     "wave.cu": ["--fmad=false"],
     "diag.cu": [],
+    "analytic.cu": ["--fmad=false"],
 }
 HEADERS = ["hydro_device.cuh", "stage_kernel.cuh", "stage_launch.cuh", "hydro_internal.h",
            "batch_kernel.cuh"]

@@ -207,6 +207,7 @@ __global__ void __launch_bounds__(BX, (MinBlocks<T, BX, OCC>::value))
         V.inv_dr[0] = T(R.inv_dr[0]), V.inv_dr[1] = T(R.inv_dr[1]), V.inv_dr[2] = T(1);
         V.gas = A.gas;
         V.ctrl = ctrl;
+        V.ana = 0;  // the batch's grids are periodic or outflow
         __syncthreads();  // the previous item's last shared-memory reads are done
         T smax = T(0);
         bool bad = false;

@@ -1,5 +1,6 @@
 // C ABI of libhydro.so (declared in include/hydro.h): argument checking, the solver context,
 // the CUDA-graph cache of step chunks and the per-kernel event timing.
+#include <math.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -51,6 +52,7 @@ struct Layout {
     size_t v_off;            // manifest V: the primitive planes
     size_t f_off[3];         // manifest F: the face-flux planes of each axis
     size_t plane, fplane[3]; // bytes of one cell plane and of one face plane per axis
+    size_t frame_off, frame_plane;  // dim 1, 2: the ghost-cell ring of analytic boundaries
 };
 
 bool grid_ok(const hydro_grid_t *g, long long *ncell) {
@@ -66,8 +68,9 @@ bool grid_ok(const hydro_grid_t *g, long long *ncell) {
     return true;
 }
 
-// Workspace: control block, totals partials, the stage buffer U1, and for the manifest forms
-// (manifest: 1 none, 2 V, 3 F in the ABI's spelling) the V planes or the face-flux planes.
+// Workspace: control block, totals partials, the stage buffer U1, for the manifest forms
+// (manifest: 1 none, 2 V, 3 F in the ABI's spelling) the V planes or the face-flux planes, and
+// in dim 1 and 2 the ring of ghost cells analytic boundaries fill (O(nx + ny) per plane).
 Layout layout_for(int dim, const int64_t n[3], long long ncell, int prec, int manifest = 1) {
     Layout L;
     memset(&L, 0, sizeof L);
@@ -87,6 +90,11 @@ Layout layout_for(int dim, const int64_t n[3], long long ncell, int prec, int ma
             L.f_off[a] = L.total;
             L.total += L.fplane[a] * (size_t)(dim + 2);
         }
+    }
+    if (dim <= 2) {
+        L.frame_plane = align_up((size_t)hydro::frame_cells(dim, (int)n[0], dim >= 2 ? (int)n[1] : 1) * esz);
+        L.frame_off = L.total;
+        L.total += L.frame_plane * (size_t)(dim + 2);
     }
     return L;
 }
@@ -204,6 +212,11 @@ struct hydro_ctx {
     double dr[3] = {1, 1, 1};
     double gamma = 1.4, cfl = 0.4;
     int order = 2, riemann = 0;
+    int ana_axes = 0;        // bit a: axis a has analytic boundaries
+    int ana_kind = 0;        // their solution (hydro_set_analytic); 0 = not set yet
+    double ana_theta = 0.0, ana_amp = 0.0;
+    double lo[3] = {0, 0, 0};
+    void *frame[5] = {};
     hydro_variant_t var = {};
     Layout lay = {};
     unsigned char *ws = nullptr;
@@ -261,11 +274,30 @@ hydro::StageLaunch stage_args(const hydro_ctx *c, const hydro_state_t *s, int st
     L.riemann = c->riemann;
     L.gamma = c->gamma;
     L.ctrl = c->ctrl;
+    L.ana = c->ana_axes;
+    for (int k = 0; k < 5; ++k) L.frame[k] = c->frame[k];
     return L;
 }
 
 cudaError_t launch_stage(const hydro_ctx *c, const hydro::StageLaunch &L, cudaStream_t st,
                          bool prepare_only = false) {
+    if (c->ana_axes && !prepare_only) {  // the ghost ring at the stage's time first
+        hydro::AnalyticLaunch A;
+        memset(&A, 0, sizeof A);
+        A.prec = c->prec;
+        A.dim = c->dim;
+        A.nx = c->n[0];
+        A.ny = c->n[1];
+        A.kind = c->ana_kind;
+        for (int d = 0; d < 2; ++d) A.lo[d] = c->lo[d], A.dr[d] = c->dr[d];
+        A.gamma = c->gamma;
+        A.theta = c->ana_theta;
+        A.amp = c->ana_amp;
+        for (int k = 0; k < 5; ++k) A.frame[k] = c->frame[k];
+        A.ctrl = c->ctrl;
+        const cudaError_t e = hydro::launch_analytic_frame(A, L.stage, st);
+        if (e != cudaSuccess) return e;
+    }
     if (c->prec == HYDRO_F64) return hydro::stage_f64(c->dim, L, st, prepare_only);
     switch (c->dim) {
         case 1: return hydro::stage_f32_d1(L, st, prepare_only);
@@ -492,11 +524,26 @@ int hydro_create(const hydro_grid_t *grid, double gamma, const int32_t bc[3], in
     if (!grid_ok(grid, &ncell) || !bc || !workspace) return HYDRO_EINVAL;
     if (prec != HYDRO_F32 && prec != HYDRO_F64) return HYDRO_EINVAL;
     if (!(gamma > 1.0) || !(gamma < 1e300) || !(cfl > 0.0) || !(cfl < 1e300)) return HYDRO_EINVAL;
-    for (int a = 0; a < grid->dim; ++a)
-        if (bc[a] != HYDRO_BC_PERIODIC && bc[a] != HYDRO_BC_OUTFLOW) return HYDRO_EINVAL;
+    int ana_axes = 0;
+    for (int a = 0; a < grid->dim; ++a) {
+        if (bc[a] != HYDRO_BC_PERIODIC && bc[a] != HYDRO_BC_OUTFLOW && bc[a] != HYDRO_BC_ANALYTIC)
+            return HYDRO_EINVAL;
+        if (bc[a] == HYDRO_BC_ANALYTIC) ana_axes |= 1 << a;
+    }
     if (((uintptr_t)workspace) % kAlign) return HYDRO_EINVAL;
     hydro_variant_t var;
     if (!resolve_variant(prec, grid->dim, variant, &var)) return HYDRO_EUNSUPPORTED;
+    if (ana_axes) {  // one-plane tiles of dim 1 and 2 read the ghost ring
+        if (grid->dim == 3) return HYDRO_EUNSUPPORTED;
+        const bool tile_given = variant && (variant->tile_x || variant->tile_y);
+        if (grid->dim == 2 && !tile_given) {  // the default 2D FP32 tile marches: take 32 x 8
+            hydro_variant_t w = variant ? *variant : hydro_variant_t{};
+            w.tile_x = 32;
+            w.tile_y = 8;
+            if (!resolve_variant(prec, grid->dim, &w, &var)) return HYDRO_EUNSUPPORTED;
+        }
+        if (grid->dim == 2 && var.tile_y == 1) return HYDRO_EUNSUPPORTED;
+    }
     const Layout lay = layout_for(grid->dim, grid->n, ncell, prec, var.manifest);
     if (workspace_bytes < lay.total) return HYDRO_EINVAL;
     // grid-dimension limits of the stage launch
@@ -521,7 +568,9 @@ int hydro_create(const hydro_grid_t *grid, double gamma, const int32_t bc[3], in
         c->n[a] = act ? (int)grid->n[a] : 1;
         c->periodic[a] = act ? (bc[a] == HYDRO_BC_PERIODIC) : 1;
         c->dr[a] = act ? (grid->hi[a] - grid->lo[a]) / (double)grid->n[a] : 1.0;
+        c->lo[a] = act ? grid->lo[a] : 0.0;
     }
+    c->ana_axes = ana_axes;
     if (marching && var.march > c->n[c->dim - 1]) var.march = c->n[c->dim - 1];
     c->gamma = gamma;
     c->cfl = cfl;
@@ -538,6 +587,8 @@ int hydro_create(const hydro_grid_t *grid, double gamma, const int32_t bc[3], in
         for (int a = 0; a < c->dim; ++a)
             for (int k = 0; k < c->dim + 2; ++k)
                 c->flux[a][k] = c->ws + lay.f_off[a] + lay.fplane[a] * (size_t)k;
+    if (c->dim <= 2)
+        for (int k = 0; k < c->dim + 2; ++k) c->frame[k] = c->ws + lay.frame_off + lay.frame_plane * (size_t)k;
     c->stream = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->copy, cudaStreamNonBlocking);
@@ -595,6 +646,23 @@ int hydro_set_scheme(hydro_ctx_t *c, int32_t order, int32_t riemann) {
     return HYDRO_OK;
 }
 
+int hydro_set_analytic(hydro_ctx_t *c, int32_t kind, double theta, double amplitude) {
+    if (!c || kind < HYDRO_ANALYTIC_ENTROPY_WAVE || kind > HYDRO_ANALYTIC_SHOCK_TUBE) return HYDRO_EINVAL;
+    if (!(theta == theta) || !(fabs(theta) < 1e6) || !(fabs(amplitude) < 1e300)) return HYDRO_EINVAL;
+    if (!c->ana_axes) return HYDRO_EINVAL;
+    DeviceGuard dg(c->device);
+    for (auto &g : c->graphs)  // captured graphs hold the old fill arguments
+        if (g.exec) {
+            cudaGraphExecDestroy(g.exec);
+            g.exec = nullptr;
+            g.chunk = 0;
+        }
+    c->ana_kind = kind;
+    c->ana_theta = theta;
+    c->ana_amp = amplitude;
+    return HYDRO_OK;
+}
+
 int hydro_set_stream(hydro_ctx_t *c, void *stream) {
     if (!c) return HYDRO_EINVAL;
     c->stream = static_cast<cudaStream_t>(stream);
@@ -605,6 +673,7 @@ int hydro_step(hydro_ctx_t *c, const hydro_state_t *state, int32_t n_steps, doub
                double *t_inout, int32_t *steps_done) {
     if (!c || !state_ok(c, state) || n_steps < 0) return HYDRO_EINVAL;
     if (t_end != t_end) return HYDRO_EINVAL;
+    if (c->ana_axes && !c->ana_kind) return HYDRO_EINVAL;  // no analytic solution set
     DeviceGuard dg(c->device);
     const double t0 = t_inout ? *t_inout : 0.0;
     if (t0 != t0) return HYDRO_EINVAL;
@@ -660,6 +729,7 @@ int hydro_step_host(hydro_ctx_t *c, const hydro_state_t *dev, const void *const 
                     void *const host_out[5], int32_t n_steps, double t_end, double *t_inout,
                     int32_t *steps_done) {
     if (!c || !state_ok(c, dev) || !host_in || !host_out || n_steps < 0) return HYDRO_EINVAL;
+    if (c->ana_axes && !c->ana_kind) return HYDRO_EINVAL;
     for (int k = 0; k < c->dim + 2; ++k)
         if (!host_in[k] || !host_out[k]) return HYDRO_EINVAL;
     DeviceGuard dg(c->device);

@@ -30,6 +30,8 @@ struct StageLaunch {
     int manifest;       // dim 3: 0 nothing stored, 1 V stored by a pass, 2 face fluxes stored
     void *vbuf[5];      // manifest V: the primitive planes
     void *flux[3][5];   // manifest F: face-flux planes per axis
+    int ana;            // bit a: axis a takes analytic ghost cells from frame (one-plane tiles)
+    const void *frame[5];
     double dr[3];
     double gamma;
     void *ctrl;
@@ -72,6 +74,22 @@ cudaError_t launch_totals(const AuxArgs &A, double *partials, int nparts, double
 cudaError_t launch_convert(const AuxArgs &A, int to_cons, cudaStream_t st);
 
 constexpr int kTotalsParts = 1024;
+
+// Analytic-solution boundaries (analytic.cu).  The frame is the ring of two ghost layers
+// around an nx x ny grid (dim 1: ny = 1), frame_cells cells per plane in the order of
+// frame_index (stage_kernel.cuh); launch_analytic_frame fills it with the conserved form of the
+// solution `kind` (1 entropy wave, 2 sound wave of amplitude amp, 3 Sod's shock tube, each
+// travelling at angle theta from the x axis) at the time of RK stage `stage` of the step held
+// in ctrl.
+struct AnalyticLaunch {
+    int prec, dim, nx, ny, kind;
+    double lo[2], dr[2];
+    double gamma, theta, amp;
+    void *frame[5];
+    void *ctrl;
+};
+int frame_cells(int dim, int nx, int ny);
+cudaError_t launch_analytic_frame(const AnalyticLaunch &L, int stage, cudaStream_t st);
 
 // ---- batched 2D grids (batch_kernel.cuh) ----
 struct BatchItem {  // one tile of one grid

@@ -47,7 +47,21 @@ template <class T> struct StageArgs {
     Ctrl *ctrl;
     T *flux[3][5];      // manifest F: face-flux planes per axis (faces of the cells' low sides
                         // plus the grid's high boundary, x fastest, the face axis n_a + 1 long)
+    const T *frame[5];  // analytic boundaries: the ghost-cell ring (frame_index), U at the
+                        // stage's time
+    int ana;            // bit a set: axis a takes its ghost cells from the frame (one-plane
+                        // tiles of dim 1 and 2 only)
 };
+
+// Position of ghost cell (gx, gy) of an nx x ny grid (dim 1: ny = 1, gy = 0) in the frame ring
+// of two ghost layers: the two rows below the grid (x from -2 to nx + 1), the two rows above
+// it, then per grid row its four side cells (x = -2, -1, nx, nx + 1).  Size 4 (nx + 4) + 4 ny.
+__host__ __device__ __forceinline__ int frame_index(int gx, int gy, int nx, int ny) {
+    const int w = nx + 4;
+    if (gy < 0) return (gy + 2) * w + gx + 2;
+    if (gy >= ny) return (gy - ny + 2) * w + gx + 2;
+    return 4 * w + gy * 4 + (gx < 0 ? gx + 2 : gx - nx + 2);
+}
 
 // CFL signal of one cell's new state, sum_a (|v_a| + c_s) / dr_a, folded into the running
 // maximum smax (NaN propagates); bad: rho <= 0 or p <= 0 seen.
@@ -437,7 +451,23 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int x0, int y0
     const int pstride = nx * ny;                       // cells per plane
     const int x = x0 + tx, y = y0 + ty;
     const bool active = (x < nx) && (y < ny);
-    const int own_off = remap(y, ny, A.periodic[1]) * nx + remap(x, nx, A.periodic[0]);
+    // plane offset of the cell (gx, gy) at most two cells outside the grid: boundary remap, or
+    // for a cell outside on exactly one axis that takes analytic ghost cells, -(1 + its
+    // position in the frame ring)
+    auto cell_off = [&](int gx, int gy) -> int {
+        if constexpr (!MARCH) {
+            if (A.ana) {
+                const bool ox = gx < 0 || gx >= nx;
+                const bool oy = (IN >= 2) && (gy < 0 || gy >= ny);
+                if (ox != oy && gx >= -2 && gx < nx + 2 && gy >= -2 && gy < ny + 2 &&
+                    (A.ana & (ox ? 1 : 2)))
+                    return -1 - frame_index(gx, (IN >= 2) ? gy : 0, nx, ny);
+            }
+        }
+        const int yg = (IN >= 2) ? remap(gy, ny, A.periodic[1]) : 0;
+        return yg * nx + remap(gx, nx, A.periodic[0]);
+    };
+    const int own_off = cell_off(x, y);
     const int own_s = (IN >= 2) ? (ty + 2) * HX + (tx + 2) : (tx + 2);
 
     // halo cells of this thread: plane offset and shared index.  Halo work goes to the
@@ -448,9 +478,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int x0, int y0
     for (int j = 0; j < HPT; ++j) {
         int lx, ly;
         h_ok[j] = halo_task<IN, BX, BY>((NT - 1 - tid) + j * NT, lx, ly);
-        const int xg = remap(x0 + lx - 2, nx, A.periodic[0]);
-        const int yg = (IN >= 2) ? remap(y0 + ly - 2, ny, A.periodic[1]) : 0;
-        h_off[j] = yg * nx + xg;
+        h_off[j] = cell_off(x0 + lx - 2, y0 + ly - 2);
         h_s[j] = ly * HX + lx;
     }
 
@@ -463,6 +491,13 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int x0, int y0
     const int pz = MARCH ? A.periodic[MA] : 1;
 
     auto load_u = [&](T (&u)[NV], int zr, int off) {
+        if constexpr (!MARCH) {
+            if (off < 0) {  // analytic ghost cell
+#pragma unroll
+                for (int k = 0; k < NV; ++k) u[k] = __ldg(A.frame[k] + (-1 - off));
+                return;
+            }
+        }
         const int i = zr * pstride + off;
 #pragma unroll
         for (int k = 0; k < NV; ++k) u[k] = __ldg(A.uin[k] + i);

@@ -28,6 +28,8 @@ template <class T> static StageArgs<T> make_stage_args(const StageLaunch &L) {
     A.riemann = L.riemann;
     A.gas = make_gas<T>(L.gamma);
     A.ctrl = static_cast<Ctrl *>(L.ctrl);
+    A.ana = L.ana;
+    for (int k = 0; k < 5; ++k) A.frame[k] = static_cast<const T *>(L.frame[k]);
     return A;
 }
 

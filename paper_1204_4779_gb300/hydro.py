@@ -20,7 +20,9 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libhydro.so")
 
 HYDRO_OK, HYDRO_EINVAL, HYDRO_ECUDA, HYDRO_ENONFINITE, HYDRO_ETIMEOUT, HYDRO_EUNSUPPORTED = range(6)
-HYDRO_BC_PERIODIC, HYDRO_BC_OUTFLOW = 0, 1
+HYDRO_BC_PERIODIC, HYDRO_BC_OUTFLOW, HYDRO_BC_ANALYTIC = 0, 1, 2
+HYDRO_ANALYTIC_ENTROPY_WAVE, HYDRO_ANALYTIC_SOUND_WAVE, HYDRO_ANALYTIC_SHOCK_TUBE = 1, 2, 3
+ANALYTIC_KINDS = {"entropy": 1, "sound": 2, "shock_tube": 3}
 HYDRO_F64, HYDRO_F32 = 0, 1
 
 # every symbol include/hydro.h declares
@@ -29,7 +31,7 @@ EXPORTS = (
     "hydro_workspace_bytes", "hydro_workspace_bytes_variant", "hydro_create", "hydro_get_variant",
     "hydro_destroy", "hydro_set_stream",
     "hydro_step",
-    "hydro_step_host", "hydro_set_scheme", "hydro_cfl_dt", "hydro_totals", "hydro_status", "hydro_prim_to_cons",
+    "hydro_step_host", "hydro_set_scheme", "hydro_set_analytic", "hydro_cfl_dt", "hydro_totals", "hydro_status", "hydro_prim_to_cons",
     "hydro_cons_to_prim", "hydro_set_profiling", "hydro_kernel_times", "hydro_step_static",
     "hydro_batch_workspace_bytes", "hydro_batch_create", "hydro_batch_destroy",
     "hydro_batch_offsets", "hydro_batch_set_stream", "hydro_batch_step", "hydro_batch_totals",
@@ -97,6 +99,7 @@ def load_library(path: str = LIB_PATH, build_if_missing: bool = True):
             "hydro_get_variant": ([vp, P(Variant)], ctypes.c_int),
             "hydro_set_stream": ([vp, vp], ctypes.c_int),
             "hydro_set_scheme": ([vp, i32, i32], ctypes.c_int),
+            "hydro_set_analytic": ([vp, i32, dbl, dbl], ctypes.c_int),
             "hydro_step": ([vp, P(State), i32, dbl, P(dbl), P(i32)], ctypes.c_int),
             "hydro_step_host": ([vp, P(State), P(vp), P(vp), i32, dbl, P(dbl), P(i32)], ctypes.c_int),
             "hydro_cfl_dt": ([vp, P(State), P(dbl)], ctypes.c_int),
@@ -216,7 +219,9 @@ class Solver:
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         if isinstance(bc, (str, int)):
             bc = [bc] * self.dim
-        self.bc = [HYDRO_BC_PERIODIC if b in ("periodic", 0) else HYDRO_BC_OUTFLOW for b in bc]
+        names = {"periodic": HYDRO_BC_PERIODIC, "outflow": HYDRO_BC_OUTFLOW,
+                 "analytic": HYDRO_BC_ANALYTIC}
+        self.bc = [names[b] if isinstance(b, str) else int(b) for b in bc]
         g = Grid()
         g.dim = self.dim
         for a in range(3):
@@ -335,6 +340,13 @@ class Solver:
         """Reconstruction order (2 MinBee, 1 first order) and HLLC wave speeds (0 Davis, 1
         pressure-based) of later steps."""
         _check(self.lib.hydro_set_scheme(self.ctx, int(order), int(riemann)), "hydro_set_scheme")
+
+    def set_analytic(self, kind, theta: float = 0.0, amplitude: float = 1.0):
+        """Exact solution of the analytic boundaries (kind "entropy", "sound", "shock_tube" or
+        1-3), travelling at angle theta (radians) from the x axis; amplitude of the sound wave."""
+        k = ANALYTIC_KINDS[kind] if isinstance(kind, str) else int(kind)
+        _check(self.lib.hydro_set_analytic(self.ctx, k, float(theta), float(amplitude)),
+               "hydro_set_analytic")
 
     def kernel_times(self, reset: bool = False):
         """{kind: (total_ms, launches)} for kinds 'cfl', 'stage1', 'stage2'."""

@@ -1,0 +1,133 @@
+"""Analytic-solution boundaries on the GPU (section 4.3's convergence tests): parity with the
+FP64 oracle, which fills its ghost layers with the same exact solutions at each stage's time.
+
+FP64: max relative error <= 1e-10; FP32: L1 density error relative to the oracle <= 1e-4.  The
+grids are ragged for the tile (several tiles, partial last tiles on both axes), so the ghost
+ring is read both by halo loads and by the own-cell loads of the threads past the grid's end.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from _helpers import gpu_state, l1_rel, max_rel_err, shape_of
+from paper_1204_4779_gb300 import hydro, inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+F32, F64 = torch.float32, torch.float64
+G = 1.4
+TH60 = math.pi / 3
+KIND = {"entropy": oracle.ANALYTIC_ENTROPY_WAVE, "sound": oracle.ANALYTIC_SOUND_WAVE,
+        "shock_tube": oracle.ANALYTIC_SHOCK_TUBE}
+
+
+def _initial(shape, kind, theta, amp):
+    return inputs.oblique_wave(shape, kind, theta, amp=amp)
+
+
+def _gpu(V, bc, dtype, kind, theta, amp, n, t_end=0.0, variant=None, order=2):
+    U = gpu_state(V, G, dtype)
+    S = hydro.Solver(shape_of(V), G, bc=list(bc), dtype=dtype, cfl=0.4, variant=variant)
+    S.set_analytic(kind, theta, amp)
+    if order != 2:
+        S.set_scheme(order, 0)
+    t, steps = S.step(U, n, t_end=t_end)
+    var = S.variant()
+    S.close()
+    return U.to(F64).cpu().numpy(), t, steps, var
+
+
+def _oracle(V, bc, kind, theta, amp, n, t_end=0.0, order=2):
+    U = oracle.prim_to_cons(V, G)
+    return oracle.run(U, G, 0.4, n, bc=bc, t_end=t_end, threads=oracle.max_threads(),
+                      analytic=(KIND[kind], theta, amp), order=order)
+
+
+CASES64 = [
+    # shape, bc, kind, theta, amp, steps, t_end, variant
+    ((40, 36), (2, 2), "entropy", TH60, 1.0, 30, 0.0, None),
+    ((37, 29), (2, 2), "sound", TH60, 1e-2, 30, 0.0, None),
+    ((48, 48), (2, 2), "shock_tube", TH60, 0.0, 10 ** 6, 0.125, None),
+    ((45, 21), (2, 0), "entropy", 0.0, 1.0, 25, 0.0, None),       # x analytic, y periodic
+    ((33, 40), (1, 2), "sound", math.pi / 2, 1e-2, 25, 0.0, None),  # along y; x outflow
+    ((37, 29), (2, 2), "entropy", TH60, 1.0, 20, 0.0, {"tile": (16, 16)}),
+    ((37, 29), (2, 2), "shock_tube", TH60, 0.0, 20, 0.0, {"tile": (64, 4)}),
+    ((150,), (2,), "entropy", 0.0, 1.0, 60, 0.0, None),
+    ((300,), (2,), "shock_tube", 0.0, 0.0, 10 ** 6, 0.2, None),
+]
+
+
+@pytest.mark.parametrize("case", range(len(CASES64)))
+def test_fp64_parity_with_the_oracle(case):
+    shape, bc, kind, theta, amp, n, t_end, variant = CASES64[case]
+    V = _initial(shape, kind, theta, amp)
+    Gd, tg, sg, var = _gpu(V, bc, F64, kind, theta, amp, n, t_end, variant)
+    O, to, so, _ = _oracle(V, bc, kind, theta, amp, n, t_end)
+    assert sg == so and abs(tg - to) <= 1e-12 * max(1.0, to), (sg, so, tg, to)
+    err = max_rel_err(Gd, O)
+    assert err <= 1e-10, err
+    if len(shape) == 2:
+        assert var["tile"][1] > 1  # analytic boundaries run on one-plane tiles
+
+
+def test_fp64_order1_parity():
+    V = _initial((37, 29), "entropy", TH60, 1.0)
+    Gd, tg, sg, _ = _gpu(V, (2, 2), F64, "entropy", TH60, 1.0, 20, order=1)
+    O, to, so, _ = _oracle(V, (2, 2), "entropy", TH60, 1.0, 20, order=1)
+    assert sg == so
+    assert max_rel_err(Gd, O) <= 1e-10
+
+
+@pytest.mark.parametrize("kind,theta,amp,t_end", [("entropy", TH60, 1.0, 0.25),
+                                                  ("sound", TH60, 1e-3, 0.25),
+                                                  ("shock_tube", TH60, 0.0, 0.125)])
+def test_fp32_parity_with_the_oracle(kind, theta, amp, t_end):
+    V = _initial((64, 64), kind, theta, amp)
+    Gd, tg, sg, var = _gpu(V, (2, 2), F32, kind, theta, amp, 10 ** 6, t_end)
+    O, to, so, _ = _oracle(V, (2, 2), kind, theta, amp, 10 ** 6, t_end)
+    assert tg == to == t_end and abs(sg - so) <= 1
+    assert l1_rel(Gd[0], O[0]) <= 1e-4
+    if kind == "sound":  # the perturbation carries the signal: also relative to rho - gamma
+        e = float(np.sum(np.abs(Gd[0] - O[0])) / np.sum(np.abs(O[0] - G)))
+        assert e <= 5e-3, e
+    assert var["tile"] == (32, 8)  # the 2D FP32 default marches rows; analytic takes 32 x 8
+
+
+def test_fp32_converges_to_the_exact_solution():
+    """The paper's oblique entropy-wave test to t = 1 on 32^2 .. 256^2 in FP32."""
+    errs = []
+    for n in (32, 64, 128, 256):
+        V = _initial((n, n), "entropy", TH60, 1.0)
+        Gd, t, _, _ = _gpu(V, (2, 2), F32, "entropy", TH60, 1.0, 10 ** 6, 1.0)
+        assert t == 1.0
+        E = inputs.oblique_wave((n, n), "entropy", TH60, t=1.0)
+        errs.append(float(np.mean(np.abs(Gd[0] - E[0]))))
+    orders = [math.log2(a / b) for a, b in zip(errs, errs[1:])]
+    print("oblique entropy wave L1", errs, orders)
+    assert all(o > 1.4 for o in orders), orders
+
+
+def test_unsupported_and_unset_analytic_boundaries():
+    lib = hydro.load_library()
+    with pytest.raises(hydro.HydroError) as e:
+        hydro.Solver((8, 8, 8), G, bc="analytic", dtype=F32)
+    assert e.value.status == hydro.HYDRO_EUNSUPPORTED
+    with pytest.raises(hydro.HydroError) as e:
+        hydro.Solver((64, 64), G, bc="analytic", dtype=F32, variant={"tile": (256, 1)})
+    assert e.value.status == hydro.HYDRO_EUNSUPPORTED
+    S = hydro.Solver((16, 16), G, bc="analytic", dtype=F64)
+    U = gpu_state(_initial((16, 16), "entropy", 0.0, 1.0), G, F64)
+    with pytest.raises(hydro.HydroError) as e:
+        S.step(U, 1)  # no solution set yet
+    assert e.value.status == hydro.HYDRO_EINVAL
+    with pytest.raises(hydro.HydroError):
+        S.set_analytic(4)
+    assert lib.hydro_set_analytic(S.ctx, 1, float("nan"), 1.0) == hydro.HYDRO_EINVAL
+    S.set_analytic("entropy", 0.0)
+    t, steps = S.step(U, 3)
+    assert steps == 3
+    P = hydro.Solver((16, 16), G, bc="periodic", dtype=F64)
+    assert lib.hydro_set_analytic(P.ctx, 1, 0.0, 1.0) == hydro.HYDRO_EINVAL  # no analytic axis
