@@ -342,15 +342,19 @@ def run_ours(args):
         for _ in range(2):  # warm (copies + step)
             S.step_host(dev_state, host, host, 1)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        marks = [torch.cuda.Event(enable_timing=True) for _ in range(args.e2e_steps + 1)]
         barrier()
         torch.cuda.synchronize()
         e0.record()
-        for _ in range(args.e2e_steps):
+        marks[0].record()
+        for i in range(args.e2e_steps):
             S.step_host(dev_state, host, host, 1)
+            marks[i + 1].record()
         e1.record()
         torch.cuda.synchronize()
         barrier()
         e2e_value, _ = aggregate_replicas(e0.elapsed_time(e1), ncell * args.e2e_steps, device=dev)
+        per_call = sorted(a.elapsed_time(b) for a, b in zip(marks, marks[1:]))
         nbytes = nv * 4 * ncell
         # the CPU-GPU link alone: the same state copied each way (pinned memory, CUDA events)
         link = {}
@@ -369,6 +373,8 @@ def run_ours(args):
                "unit": "cell-updates/s", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
                "steps": args.e2e_steps,
                "call": "hydro_step_host: pinned host state in, 1 RK step, host state out",
+               "per_call_ms": {"min": per_call[0], "median": per_call[len(per_call) // 2],
+                               "max": per_call[-1]},
                "link": dict(link, note="plain copies of the state over the CPU-GPU link; the "
                                        "step's copies alone take nbytes/h2d + nbytes/d2h")}
 

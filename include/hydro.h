@@ -214,7 +214,11 @@ int hydro_set_scheme(hydro_ctx_t *ctx, int32_t order, int32_t riemann);
  *   steps_done out: steps actually taken (may be NULL)
  * dt is computed on the device from the state at the start of each step (the first from
  * `state` by a CFL pass, later ones in the epilogue of the previous step) and never leaves
- * the device inside the call.  The steps run as CUDA graphs of captured launches.
+ * the device inside the call.  The steps run as CUDA graphs of captured launches (chunks of up
+ * to 64 steps); once no further step is to be taken (t_end reached or a failed step) the steps
+ * left return at once on the device, and a synchronous call stops launching chunks after
+ * that (it reads dt back after each chunk, one chunk late, so n_steps may be a generous
+ * bound when t_end is what ends the run).
  * If both t_inout and steps_done are NULL the call is asynchronous and a device-side error
  * is reported by the next synchronising call; otherwise it synchronises and returns
  * HYDRO_ENONFINITE if a step failed. */

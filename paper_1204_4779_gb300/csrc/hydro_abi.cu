@@ -229,6 +229,8 @@ struct hydro_ctx {
     cudaStream_t cap = nullptr;  // private stream used only to capture graphs
     cudaStream_t copy = nullptr;  // private stream of hydro_step_host's copies back to the host
     std::vector<cudaEvent_t> slab_events;  // one per stage-2 slab of hydro_step_host
+    double *dt_probe = nullptr;            // pinned host: dt after a graph chunk (2 slots)
+    cudaEvent_t probe_ev[2] = {nullptr, nullptr};
     GraphEntry graphs[kGraphSlots];
     unsigned long long use_clock = 0;
     bool profiling = false;
@@ -432,10 +434,14 @@ int run_steps_profiled(hydro_ctx *c, const hydro_state_t *s, int n) {
     return HYDRO_OK;
 }
 
-int run_steps(hydro_ctx *c, const hydro_state_t *s, int n) {
+// stop_early: the caller synchronises at the end anyway, so after each graph chunk the dt of
+// the next step is copied to the host, and once it is 0 (t_end reached, or a failed step) the
+// remaining chunks are not launched.  The check lags one chunk, so the GPU never waits on it:
+// at most one chunk of steps that return at once is launched after the last real step.
+int run_steps(hydro_ctx *c, const hydro_state_t *s, int n, bool stop_early = false) {
     if (n <= 0) return HYDRO_OK;
     if (c->profiling) return run_steps_profiled(c, s, n);
-    int left = n;
+    int left = n, k = 0;
     while (left > 0) {
         int chunk = kMaxChunk;
         while (chunk > left) chunk >>= 1;
@@ -444,6 +450,17 @@ int run_steps(hydro_ctx *c, const hydro_state_t *s, int n) {
         if (rc) return rc;
         CK(cudaGraphLaunch(g, c->stream));
         left -= chunk;
+        if (stop_early && left > 0) {
+            const int slot = k & 1;
+            CK(cudaMemcpyAsync(&c->dt_probe[slot], &c->ctrl->dt, sizeof(double),
+                               cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaEventRecord(c->probe_ev[slot], c->stream));
+            if (k > 0) {  // the previous chunk's probe (the current chunk is already queued)
+                CK(cudaEventSynchronize(c->probe_ev[slot ^ 1]));
+                if (!(c->dt_probe[slot ^ 1] > 0.0)) break;
+            }
+            ++k;
+        }
     }
     return HYDRO_OK;
 }
@@ -592,10 +609,17 @@ int hydro_create(const hydro_grid_t *grid, double gamma, const int32_t bc[3], in
     c->stream = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->copy, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void **>(&c->dt_probe), 2 * sizeof(double), 0);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i)
+        e = cudaEventCreateWithFlags(&c->probe_ev[i], cudaEventDisableTiming);
     if (e != cudaSuccess) {
         if (c->cap) cudaStreamDestroy(c->cap);
+        if (c->copy) cudaStreamDestroy(c->copy);
+        if (c->dt_probe) cudaFreeHost(c->dt_probe);
+        for (auto ev : c->probe_ev)
+            if (ev) cudaEventDestroy(ev);
         delete c;
-        return cuda_fail(e, "cudaStreamCreateWithFlags");
+        return cuda_fail(e, "context streams and events");
     }
     hydro_state_t dummy;
     memset(&dummy, 0, sizeof dummy);
@@ -603,6 +627,8 @@ int hydro_create(const hydro_grid_t *grid, double gamma, const int32_t bc[3], in
     if (e != cudaSuccess) {
         cudaStreamDestroy(c->cap);
         cudaStreamDestroy(c->copy);
+        cudaFreeHost(c->dt_probe);
+        for (auto ev : c->probe_ev) cudaEventDestroy(ev);
         delete c;
         return cuda_fail(e, "stage kernel attributes");
     }
@@ -626,6 +652,9 @@ int hydro_destroy(hydro_ctx_t *c) {
     for (auto e : c->slab_events) cudaEventDestroy(e);
     if (c->cap) cudaStreamDestroy(c->cap);
     if (c->copy) cudaStreamDestroy(c->copy);
+    if (c->dt_probe) cudaFreeHost(c->dt_probe);
+    for (auto ev : c->probe_ev)
+        if (ev) cudaEventDestroy(ev);
     delete c;
     return HYDRO_OK;
 }
@@ -679,7 +708,7 @@ int hydro_step(hydro_ctx_t *c, const hydro_state_t *state, int32_t n_steps, doub
     if (t0 != t0) return HYDRO_EINVAL;
     int rc = begin_steps(c, state, t0, t_end);
     if (rc) return rc;
-    rc = run_steps(c, state, n_steps);
+    rc = run_steps(c, state, n_steps, /*stop_early=*/t_inout || steps_done);
     if (rc) return rc;
     return finish_steps(c, t_inout, steps_done);
 }
@@ -741,7 +770,7 @@ int hydro_step_host(hydro_ctx_t *c, const hydro_state_t *dev, const void *const 
     int rc = begin_steps(c, dev, t, t_end);
     // dim 3 outside profiling: the last step overlaps its copy back with its stage 2
     const bool overlap = c->dim == 3 && n_steps >= 1 && !c->profiling && c->var.manifest == 1;
-    if (!rc) rc = run_steps(c, dev, overlap ? n_steps - 1 : n_steps);
+    if (!rc) rc = run_steps(c, dev, overlap ? n_steps - 1 : n_steps, /*stop_early=*/true);
     if (!rc && overlap) rc = last_step_overlapped(c, dev, host_out);
     if (rc) return rc;
     if (!overlap)
