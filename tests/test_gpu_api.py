@@ -86,6 +86,26 @@ def test_time_clipping_matches_oracle():
     assert s3 == 0 and t3 == 0.05
 
 
+def test_generous_step_bound_stops_at_t_end():
+    """A synchronous call stops launching graph chunks once t_end is reached: a bound of 10^6
+    steps costs about as much as the steps actually taken (10^6 empty steps would take
+    seconds)."""
+    import time
+    V = inputs.sod_1d(256)
+    U = gpu_state(V, 1.4, F64)
+    S = hydro.Solver((256,), 1.4, bc="outflow", dtype=F64)
+    S.step(gpu_state(V, 1.4, F64), 64, t_end=0.01)  # graphs captured outside the timing
+    t0 = time.perf_counter()
+    t, steps = S.step(U, 10 ** 6, t_end=0.1)
+    wall = time.perf_counter() - t0
+    O, to, so, _ = oracle_run(V, 1.4, (1,), 0.4, 10 ** 6, t_end=0.1)
+    assert t == to == 0.1 and steps == so
+    assert wall < 1.0, wall
+    # and the state is the one of the exact step count
+    G, _, _ = gpu_run(V, 1.4, (1,), F64, 0.4, steps, t_end=0.1)
+    assert np.array_equal(U.cpu().numpy(), G)
+
+
 def test_nonfinite_and_nonpositive_are_reported():
     V = inputs.uniform((32,), rho=1.0, v=(0.0,), p=1.0)
     for bad in ("nan", "negrho"):
