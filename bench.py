@@ -159,6 +159,19 @@ def _gpu_index(local_rank: int) -> int:
     return local_rank
 
 
+def _cpu_model() -> str:
+    """The host CPU's model name (lscpu), else the machine type."""
+    try:
+        import subprocess
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return os.uname().machine
+
+
 def cpu_oracle_cups(budget_s: float = 12.0, n: int = 64, max_steps: int = 200, device=None):
     """The FP64 CPU oracle as it stands, on a bounded sample of the workload: the same blast
     at n^3 (radius 8 cells, periodic, CFL 0.4), all host cores, about `budget_s` of CPU work."""
@@ -174,7 +187,7 @@ def cpu_oracle_cups(budget_s: float = 12.0, n: int = 64, max_steps: int = 200, d
     Uo, _, done, _ = oracle.run(U, GAMMA, CFL, steps, bc=(0, 0, 0), threads=threads)
     el = time.perf_counter() - t0
     out = {"value": n ** 3 * done / el, "unit": "cell-updates/s", "cores": threads,
-           "kind": "oracle",
+           "kind": "oracle", "cpu_model": _cpu_model(),
            "sample": f"{n}^3 blast (radius {RADIUS:g} cells), {done} FP64 RK steps, "
                      f"{el:.1f} s, OpenMP threads={threads}, host={os.uname().machine}"}
     if device is not None:
@@ -232,7 +245,7 @@ def run_reference(args):
             "config": {"workload": WORKLOAD, "sample": f"{n}^3 blast per step on the host",
                        "l2": "n/a (CPU)"},
             "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": threads,
-                             "kind": "oracle",
+                             "kind": "oracle", "cpu_model": _cpu_model(),
                              "sample": f"{n}^3 blast (radius {RADIUS:g} cells), {done} RK steps"},
             "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
