@@ -37,6 +37,10 @@ CASES = [
     ((37, 21, 19), (1, 0, 1), torch.float32, {"march": 7, "split": 1, "staging": 2, "occupancy": 2}),
     ((33, 18, 11), (0, 0, 0), torch.float32, {"tile": (16, 16), "march": 4}),
     ((23, 29, 17), (0, 0, 1), torch.float64, {"march": 6, "split": 1}),
+    # analytic boundaries: the ghost ring in the workspace is written before every stage
+    ((45, 29), (2, 2), torch.float32, {}),
+    ((37, 21), (2, 1), torch.float64, {}),
+    ((150,), (2,), torch.float32, {}),
 ]
 
 
@@ -68,6 +72,8 @@ def test_no_writes_outside_state_and_workspace(case):
                           ctypes.byref(var) if var is not None else None, base, wbytes,
                           torch.cuda.current_stream().cuda_stream, ctypes.byref(ctx))
     assert rc == 0
+    if 2 in bc:
+        assert lib.hydro_set_analytic(ctx, hydro.HYDRO_ANALYTIC_SHOCK_TUBE, 0.9, 0.0) == 0
     st = hydro.state_struct(U, len(shape) + 2)
     t = ctypes.c_double(0.0)
     n = ctypes.c_int32()
