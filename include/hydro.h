@@ -196,6 +196,14 @@ int hydro_destroy(hydro_ctx_t *ctx);
  * HYDRO_EINVAL (no analytic axis, unknown kind, non-finite theta or amplitude). */
 int hydro_set_analytic(hydro_ctx_t *ctx, int32_t kind, double theta, double amplitude);
 
+/* The same exact solutions at every cell centre of a grid (dim 1 or 2) at time t: the conserved
+ * state written to the dim+2 planes of `out` (device, caller-owned, prec elements), e.g. the
+ * initial data and the reference of a convergence study.  Stream-ordered on `stream`, no
+ * synchronisation.  Errors: HYDRO_EINVAL (dim 3, unknown kind, t < 0, bad grid or pointers). */
+int hydro_analytic_state(const hydro_grid_t *grid, double gamma, int32_t prec, int32_t kind,
+                         double theta, double amplitude, double t, const hydro_state_t *out,
+                         void *stream);
+
 /* Change the stream later calls are ordered on. */
 int hydro_set_stream(hydro_ctx_t *ctx, void *stream);
 

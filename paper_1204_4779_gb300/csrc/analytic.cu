@@ -129,24 +129,11 @@ __device__ void riemann_sample(const FrameArgs &a, double xi, double *r, double 
     }
 }
 
+// The conserved state of the solution at the point (x, y) and time t (dim 1: y = 1/2), stored
+// at index i of the planes `out`.
 template <class T>
-__global__ void __launch_bounds__(kFrameThreads) frame_kernel(const FrameArgs a, int stage) {
-    const int i = blockIdx.x * kFrameThreads + threadIdx.x;
-    if (i >= a.cells) return;
-    // ring position -> ghost cell (gx, gy), the inverse of frame_index
-    const int w = a.nx + 4;
-    int gx, gy;
-    if (i < 2 * w) {
-        gy = i / w - 2, gx = i % w - 2;
-    } else if (i < 4 * w) {
-        gy = a.ny + (i - 2 * w) / w, gx = (i - 2 * w) % w - 2;
-    } else {
-        const int j = i - 4 * w, c = j % 4;
-        gy = j / 4, gx = c < 2 ? c - 2 : a.nx + c - 2;
-    }
-    const double t = stage == 2 ? a.ctrl->t + 0.5 * a.ctrl->dt : a.ctrl->t;
-    const double x = a.lo[0] + (gx + 0.5) * a.dr[0];
-    const double y = a.dim >= 2 ? a.lo[1] + (gy + 0.5) * a.dr[1] : 0.5;
+__device__ void store_solution(const FrameArgs &a, double x, double y, double t, void *const *out,
+                               long long i) {
     const double s = (x - 0.5) * a.cth + (y - 0.5) * a.sth + 0.5;
     double rho, un, p;
     if (a.kind == 3) {
@@ -168,17 +155,51 @@ __global__ void __launch_bounds__(kFrameThreads) frame_kernel(const FrameArgs a,
     const double v[2] = {un * a.cth, un * a.sth};
     double kin = 0.0;
     for (int d = 0; d < a.dim; ++d) kin += v[d] * v[d];
-    T *const *f = reinterpret_cast<T *const *>(a.frame);
+    T *const *f = reinterpret_cast<T *const *>(out);
     f[0][i] = T(rho);
     for (int d = 0; d < a.dim; ++d) f[1 + d][i] = T(rho * v[d]);
     f[a.dim + 1][i] = T(p / (a.gamma - 1.0) + 0.5 * rho * kin);
+}
+
+template <class T>
+__global__ void __launch_bounds__(kFrameThreads) frame_kernel(const FrameArgs a, int stage) {
+    const int i = blockIdx.x * kFrameThreads + threadIdx.x;
+    if (i >= a.cells) return;
+    // ring position -> ghost cell (gx, gy), the inverse of frame_index
+    const int w = a.nx + 4;
+    int gx, gy;
+    if (i < 2 * w) {
+        gy = i / w - 2, gx = i % w - 2;
+    } else if (i < 4 * w) {
+        gy = a.ny + (i - 2 * w) / w, gx = (i - 2 * w) % w - 2;
+    } else {
+        const int j = i - 4 * w, c = j % 4;
+        gy = j / 4, gx = c < 2 ? c - 2 : a.nx + c - 2;
+    }
+    const double t = stage == 2 ? a.ctrl->t + 0.5 * a.ctrl->dt : a.ctrl->t;
+    const double x = a.lo[0] + (gx + 0.5) * a.dr[0];
+    const double y = a.dim >= 2 ? a.lo[1] + (gy + 0.5) * a.dr[1] : 0.5;
+    store_solution<T>(a, x, y, t, a.frame, i);
+}
+
+// The solution at every cell centre of the grid at time t (grid-stride over the cells).
+template <class T>
+__global__ void __launch_bounds__(kFrameThreads) solution_kernel(const FrameArgs a, double t,
+                                                                 long long ncell) {
+    for (long long i = (long long)blockIdx.x * kFrameThreads + threadIdx.x; i < ncell;
+         i += (long long)gridDim.x * kFrameThreads) {
+        const long long gx = i % a.nx, gy = i / a.nx;
+        const double x = a.lo[0] + ((double)gx + 0.5) * a.dr[0];
+        const double y = a.dim >= 2 ? a.lo[1] + ((double)gy + 0.5) * a.dr[1] : 0.5;
+        store_solution<T>(a, x, y, t, a.frame, i);
+    }
 }
 
 }  // namespace
 
 int frame_cells(int dim, int nx, int ny) { return 4 * (nx + 4) + 4 * (dim >= 2 ? ny : 1); }
 
-cudaError_t launch_analytic_frame(const AnalyticLaunch &L, int stage, cudaStream_t st) {
+static FrameArgs frame_args(const AnalyticLaunch &L) {
     FrameArgs a;
     memset(&a, 0, sizeof a);
     a.dim = L.dim;
@@ -198,6 +219,11 @@ cudaError_t launch_analytic_frame(const AnalyticLaunch &L, int stage, cudaStream
     }
     for (int k = 0; k < 5; ++k) a.frame[k] = L.frame[k];
     a.ctrl = static_cast<const Ctrl *>(L.ctrl);
+    return a;
+}
+
+cudaError_t launch_analytic_frame(const AnalyticLaunch &L, int stage, cudaStream_t st) {
+    const FrameArgs a = frame_args(L);
     const unsigned blocks = (unsigned)((a.cells + kFrameThreads - 1) / kFrameThreads);
     if (L.prec == HYDRO_F32)
         frame_kernel<float><<<blocks, kFrameThreads, 0, st>>>(a, stage);
@@ -207,3 +233,47 @@ cudaError_t launch_analytic_frame(const AnalyticLaunch &L, int stage, cudaStream
 }
 
 }  // namespace hydro
+
+extern "C" int hydro_analytic_state(const hydro_grid_t *grid, double gamma, int32_t prec,
+                                    int32_t kind, double theta, double amplitude, double t,
+                                    const hydro_state_t *out, void *stream) {
+    if (!grid || !out || grid->dim < 1 || grid->dim > 2) return HYDRO_EINVAL;
+    if (prec != HYDRO_F32 && prec != HYDRO_F64) return HYDRO_EINVAL;
+    if (kind < HYDRO_ANALYTIC_ENTROPY_WAVE || kind > HYDRO_ANALYTIC_SHOCK_TUBE) return HYDRO_EINVAL;
+    if (!(gamma > 1.0) || !(gamma < 1e300) || !(t >= 0.0) || !(t < 1e300)) return HYDRO_EINVAL;
+    if (!(fabs(theta) < 1e6) || !(fabs(amplitude) < 1e300)) return HYDRO_EINVAL;
+    long long ncell = 1;
+    for (int d = 0; d < grid->dim; ++d) {
+        if (grid->n[d] < 1 || grid->n[d] > (1LL << 31) - 1 || !(grid->hi[d] > grid->lo[d]))
+            return HYDRO_EINVAL;
+        ncell *= grid->n[d];
+    }
+    if (ncell >= (1LL << 31)) return HYDRO_EINVAL;
+    for (int k = 0; k < grid->dim + 2; ++k)
+        if (!out->plane[k]) return HYDRO_EINVAL;
+    hydro::AnalyticLaunch L;
+    memset(&L, 0, sizeof L);
+    L.prec = prec;
+    L.dim = grid->dim;
+    L.nx = (int)grid->n[0];
+    L.ny = grid->dim >= 2 ? (int)grid->n[1] : 1;
+    L.kind = kind;
+    for (int d = 0; d < grid->dim; ++d) {
+        L.lo[d] = grid->lo[d];
+        L.dr[d] = (grid->hi[d] - grid->lo[d]) / (double)grid->n[d];
+    }
+    L.gamma = gamma;
+    L.theta = theta;
+    L.amp = amplitude;
+    for (int k = 0; k < grid->dim + 2; ++k) L.frame[k] = out->plane[k];
+    const hydro::FrameArgs a = hydro::frame_args(L);
+    const long long want = (ncell + hydro::kFrameThreads - 1) / hydro::kFrameThreads;
+    const unsigned blocks = (unsigned)(want < 152LL * 16 ? want : 152LL * 16);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (prec == HYDRO_F32)
+        hydro::solution_kernel<float><<<blocks, hydro::kFrameThreads, 0, st>>>(a, t, ncell);
+    else
+        hydro::solution_kernel<double><<<blocks, hydro::kFrameThreads, 0, st>>>(a, t, ncell);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? HYDRO_OK : hydro::record_cuda_error(e, "hydro_analytic_state");
+}

@@ -31,7 +31,7 @@ EXPORTS = (
     "hydro_workspace_bytes", "hydro_workspace_bytes_variant", "hydro_create", "hydro_get_variant",
     "hydro_destroy", "hydro_set_stream",
     "hydro_step",
-    "hydro_step_host", "hydro_set_scheme", "hydro_set_analytic", "hydro_cfl_dt", "hydro_totals", "hydro_status", "hydro_prim_to_cons",
+    "hydro_step_host", "hydro_set_scheme", "hydro_set_analytic", "hydro_analytic_state", "hydro_cfl_dt", "hydro_totals", "hydro_status", "hydro_prim_to_cons",
     "hydro_cons_to_prim", "hydro_set_profiling", "hydro_kernel_times", "hydro_step_static",
     "hydro_batch_workspace_bytes", "hydro_batch_create", "hydro_batch_destroy",
     "hydro_batch_offsets", "hydro_batch_set_stream", "hydro_batch_step", "hydro_batch_totals",
@@ -100,6 +100,8 @@ def load_library(path: str = LIB_PATH, build_if_missing: bool = True):
             "hydro_set_stream": ([vp, vp], ctypes.c_int),
             "hydro_set_scheme": ([vp, i32, i32], ctypes.c_int),
             "hydro_set_analytic": ([vp, i32, dbl, dbl], ctypes.c_int),
+            "hydro_analytic_state": ([P(Grid), dbl, i32, i32, dbl, dbl, dbl, P(State), vp],
+                                     ctypes.c_int),
             "hydro_step": ([vp, P(State), i32, dbl, P(dbl), P(i32)], ctypes.c_int),
             "hydro_step_host": ([vp, P(State), P(vp), P(vp), i32, dbl, P(dbl), P(i32)], ctypes.c_int),
             "hydro_cfl_dt": ([vp, P(State), P(dbl)], ctypes.c_int),
@@ -199,10 +201,33 @@ def cons_to_prim(U: torch.Tensor, gamma: float) -> torch.Tensor:
     return _convert(U.contiguous(), gamma, False)
 
 
+def analytic_state(shape, gamma: float, kind, theta: float = 0.0, amplitude: float = 1.0,
+                   t: float = 0.0, dtype=torch.float64, device=None) -> torch.Tensor:
+    """Conserved planes of an exact solution of the convergence tests (kind "entropy", "sound",
+    "shock_tube" or 1-3) at the cell centres of the unit box (dim 1 or 2) at time t."""
+    lib = load_library()
+    dim = len(shape)
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    U = torch.empty((dim + 2,) + tuple(reversed([int(n) for n in shape])), dtype=dtype, device=dev)
+    g = Grid()
+    g.dim = dim
+    for a in range(3):
+        g.n[a] = int(shape[a]) if a < dim else 1
+        g.lo[a], g.hi[a] = 0.0, 1.0
+    k = ANALYTIC_KINDS[kind] if isinstance(kind, str) else int(kind)
+    st = state_struct(U, dim + 2)
+    with torch.cuda.device(dev):
+        _check(lib.hydro_analytic_state(ctypes.byref(g), float(gamma), _prec(dtype), k,
+                                        float(theta), float(amplitude), float(t), ctypes.byref(st),
+                                        _stream_ptr(dev)), "hydro_analytic_state")
+    return U
+
+
 class Solver:
     """One context of libhydro.so on the current CUDA device.
 
-    shape: cells per axis (nx, [ny, [nz]]); bc: per-axis "periodic"/"outflow" (or 0/1);
+    shape: cells per axis (nx, [ny, [nz]]); bc: per-axis "periodic"/"outflow"/"analytic" (or
+    0/1/2; analytic boundaries take their solution from set_analytic);
     variant: dict(tile=(bx, by), march=m, split=0|1|2, staging=0|1|2, occupancy=0|2|3,
     manifest=0|1|2|3) or None for the default.
     """
