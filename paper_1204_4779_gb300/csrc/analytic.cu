@@ -197,7 +197,9 @@ __global__ void __launch_bounds__(kFrameThreads) solution_kernel(const FrameArgs
 
 }  // namespace
 
-int frame_cells(int dim, int nx, int ny) { return 4 * (nx + 4) + 4 * (dim >= 2 ? ny : 1); }
+long long frame_cells(int dim, long long nx, long long ny) {
+    return 4 * (nx + 4) + 4 * (dim >= 2 ? ny : 1);
+}
 
 static FrameArgs frame_args(const AnalyticLaunch &L) {
     FrameArgs a;
@@ -206,7 +208,7 @@ static FrameArgs frame_args(const AnalyticLaunch &L) {
     a.nx = L.nx;
     a.ny = L.dim >= 2 ? L.ny : 1;
     a.kind = L.kind;
-    a.cells = frame_cells(L.dim, L.nx, L.ny);
+    a.cells = (int)frame_cells(L.dim, L.nx, L.ny);  // below 2^31: checked at create
     for (int d = 0; d < 2; ++d) a.lo[d] = L.lo[d], a.dr[d] = L.dr[d];
     a.gamma = L.gamma;
     a.cth = cos(L.theta);

@@ -92,7 +92,7 @@ Layout layout_for(int dim, const int64_t n[3], long long ncell, int prec, int ma
         }
     }
     if (dim <= 2) {
-        L.frame_plane = align_up((size_t)hydro::frame_cells(dim, (int)n[0], dim >= 2 ? (int)n[1] : 1) * esz);
+        L.frame_plane = align_up((size_t)hydro::frame_cells(dim, n[0], dim >= 2 ? n[1] : 1) * esz);
         L.frame_off = L.total;
         L.total += L.frame_plane * (size_t)(dim + 2);
     }
@@ -560,6 +560,8 @@ int hydro_create(const hydro_grid_t *grid, double gamma, const int32_t bc[3], in
             if (!resolve_variant(prec, grid->dim, &w, &var)) return HYDRO_EUNSUPPORTED;
         }
         if (grid->dim == 2 && var.tile_y == 1) return HYDRO_EUNSUPPORTED;
+        if (hydro::frame_cells(grid->dim, grid->n[0], grid->dim >= 2 ? grid->n[1] : 1) >= (1LL << 31))
+            return HYDRO_EUNSUPPORTED;  // the ring's int indices
     }
     const Layout lay = layout_for(grid->dim, grid->n, ncell, prec, var.manifest);
     if (workspace_bytes < lay.total) return HYDRO_EINVAL;

@@ -88,7 +88,7 @@ struct AnalyticLaunch {
     void *frame[5];
     void *ctrl;
 };
-int frame_cells(int dim, int nx, int ny);
+long long frame_cells(int dim, long long nx, long long ny);
 cudaError_t launch_analytic_frame(const AnalyticLaunch &L, int stage, cudaStream_t st);
 
 // ---- batched 2D grids (batch_kernel.cuh) ----
