@@ -57,7 +57,12 @@ enum {
     HYDRO_EUNSUPPORTED = 5 /* valid request that this build has no kernel for */
 };
 
-typedef enum { HYDRO_BC_PERIODIC = 0, HYDRO_BC_OUTFLOW = 1, HYDRO_BC_ANALYTIC = 2 } hydro_bc_t;
+typedef enum {
+    HYDRO_BC_PERIODIC = 0,
+    HYDRO_BC_OUTFLOW = 1,
+    HYDRO_BC_ANALYTIC = 2,
+    HYDRO_BC_EXCHANGE = 3
+} hydro_bc_t;
 /* Analytic solutions of HYDRO_BC_ANALYTIC (section 4.3 convergence tests; hydro_set_analytic). */
 typedef enum {
     HYDRO_ANALYTIC_ENTROPY_WAVE = 1,
@@ -161,7 +166,12 @@ int hydro_workspace_bytes_variant(const hydro_grid_t *grid, int32_t prec,
  *             outside that axis's ends with the exact solution set by hydro_set_analytic at
  *             the time of each RK stage.  Analytic boundaries run on one-plane tiles: with no
  *             tile given a 2D context takes 32 x 8; a row tile (tile_y = 1) is
- *             HYDRO_EUNSUPPORTED
+ *             HYDRO_EUNSUPPORTED.  Exchange (dim 1 and 2, n >= 2 on the axis, one-plane
+ *             tiles likewise): before each RK stage the two boundary layers at each end are
+ *             packed into buffers and unpacked into the two ghost layers at the other end —
+ *             the periodic wrap through the pack/unpack kernels a domain decomposition over
+ *             several GPUs would put its transfers between; results equal HYDRO_BC_PERIODIC
+ *             bit for bit
  *   prec      HYDRO_F32 (whole stencil in FP32; dt, time and totals in FP64) or HYDRO_F64
  *   cfl       Courant number, 0 < cfl
  *   variant   kernel variant or NULL for the default

@@ -38,6 +38,7 @@ UNITS = {
     "wave.cu": ["--fmad=false"],
     "diag.cu": [],
     "analytic.cu": ["--fmad=false"],
+    "exchange.cu": [],
 }
 HEADERS = ["hydro_device.cuh", "stage_kernel.cuh", "stage_launch.cuh", "hydro_internal.h",
            "batch_kernel.cuh"]

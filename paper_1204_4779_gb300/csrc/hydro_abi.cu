@@ -53,6 +53,7 @@ struct Layout {
     size_t f_off[3];         // manifest F: the face-flux planes of each axis
     size_t plane, fplane[3]; // bytes of one cell plane and of one face plane per axis
     size_t frame_off, frame_plane;  // dim 1, 2: the ghost-cell ring of analytic boundaries
+    size_t ex_off[2][2];            // dim 1, 2: exchange buffers per axis and side
 };
 
 bool grid_ok(const hydro_grid_t *g, long long *ncell) {
@@ -70,7 +71,8 @@ bool grid_ok(const hydro_grid_t *g, long long *ncell) {
 
 // Workspace: control block, totals partials, the stage buffer U1, for the manifest forms
 // (manifest: 1 none, 2 V, 3 F in the ABI's spelling) the V planes or the face-flux planes, and
-// in dim 1 and 2 the ring of ghost cells analytic boundaries fill (O(nx + ny) per plane).
+// in dim 1 and 2 the ring of ghost cells analytic and exchange boundaries fill and the exchange
+// buffers (O(nx + ny) per plane).
 Layout layout_for(int dim, const int64_t n[3], long long ncell, int prec, int manifest = 1) {
     Layout L;
     memset(&L, 0, sizeof L);
@@ -95,6 +97,11 @@ Layout layout_for(int dim, const int64_t n[3], long long ncell, int prec, int ma
         L.frame_plane = align_up((size_t)hydro::frame_cells(dim, n[0], dim >= 2 ? n[1] : 1) * esz);
         L.frame_off = L.total;
         L.total += L.frame_plane * (size_t)(dim + 2);
+        for (int a = 0; a < dim; ++a)
+            for (int side = 0; side < 2; ++side) {
+                L.ex_off[a][side] = L.total;
+                L.total += align_up((size_t)hydro::exchange_buffer_cells(dim, n[0], dim >= 2 ? n[1] : 1, a) * esz);
+            }
     }
     return L;
 }
@@ -213,6 +220,8 @@ struct hydro_ctx {
     double gamma = 1.4, cfl = 0.4;
     int order = 2, riemann = 0;
     int ana_axes = 0;        // bit a: axis a has analytic boundaries
+    int ex_axes = 0;         // bit a: axis a has exchange boundaries
+    void *ex_buf[2][2] = {};
     int ana_kind = 0;        // their solution (hydro_set_analytic); 0 = not set yet
     double ana_theta = 0.0, ana_amp = 0.0;
     double lo[3] = {0, 0, 0};
@@ -276,7 +285,7 @@ hydro::StageLaunch stage_args(const hydro_ctx *c, const hydro_state_t *s, int st
     L.riemann = c->riemann;
     L.gamma = c->gamma;
     L.ctrl = c->ctrl;
-    L.ana = c->ana_axes;
+    L.ana = c->ana_axes | c->ex_axes;  // the axes whose ghost cells come from the ring
     for (int k = 0; k < 5; ++k) L.frame[k] = c->frame[k];
     return L;
 }
@@ -298,6 +307,20 @@ cudaError_t launch_stage(const hydro_ctx *c, const hydro::StageLaunch &L, cudaSt
         for (int k = 0; k < 5; ++k) A.frame[k] = c->frame[k];
         A.ctrl = c->ctrl;
         const cudaError_t e = hydro::launch_analytic_frame(A, L.stage, st);
+        if (e != cudaSuccess) return e;
+    }
+    if (c->ex_axes && !prepare_only) {  // then the exchanged layers of the stage's input
+        hydro::ExchangeLaunch X;
+        memset(&X, 0, sizeof X);
+        X.prec = c->prec;
+        X.dim = c->dim;
+        X.nx = c->n[0];
+        X.ny = c->n[1];
+        X.axes = c->ex_axes;
+        for (int k = 0; k < 5; ++k) X.uin[k] = L.uin[k], X.frame[k] = c->frame[k];
+        for (int a = 0; a < 2; ++a)
+            for (int side = 0; side < 2; ++side) X.buf[a][side] = c->ex_buf[a][side];
+        const cudaError_t e = hydro::launch_exchange(X, st);
         if (e != cudaSuccess) return e;
     }
     if (c->prec == HYDRO_F64) return hydro::stage_f64(c->dim, L, st, prepare_only);
@@ -541,16 +564,19 @@ int hydro_create(const hydro_grid_t *grid, double gamma, const int32_t bc[3], in
     if (!grid_ok(grid, &ncell) || !bc || !workspace) return HYDRO_EINVAL;
     if (prec != HYDRO_F32 && prec != HYDRO_F64) return HYDRO_EINVAL;
     if (!(gamma > 1.0) || !(gamma < 1e300) || !(cfl > 0.0) || !(cfl < 1e300)) return HYDRO_EINVAL;
-    int ana_axes = 0;
+    int ana_axes = 0, ex_axes = 0;
     for (int a = 0; a < grid->dim; ++a) {
-        if (bc[a] != HYDRO_BC_PERIODIC && bc[a] != HYDRO_BC_OUTFLOW && bc[a] != HYDRO_BC_ANALYTIC)
-            return HYDRO_EINVAL;
+        if (bc[a] < HYDRO_BC_PERIODIC || bc[a] > HYDRO_BC_EXCHANGE) return HYDRO_EINVAL;
         if (bc[a] == HYDRO_BC_ANALYTIC) ana_axes |= 1 << a;
+        if (bc[a] == HYDRO_BC_EXCHANGE) {
+            if (grid->n[a] < 2) return HYDRO_EUNSUPPORTED;  // two layers to exchange
+            ex_axes |= 1 << a;
+        }
     }
     if (((uintptr_t)workspace) % kAlign) return HYDRO_EINVAL;
     hydro_variant_t var;
     if (!resolve_variant(prec, grid->dim, variant, &var)) return HYDRO_EUNSUPPORTED;
-    if (ana_axes) {  // one-plane tiles of dim 1 and 2 read the ghost ring
+    if (ana_axes | ex_axes) {  // one-plane tiles of dim 1 and 2 read the ghost ring
         if (grid->dim == 3) return HYDRO_EUNSUPPORTED;
         const bool tile_given = variant && (variant->tile_x || variant->tile_y);
         if (grid->dim == 2 && !tile_given) {  // the default 2D FP32 tile marches: take 32 x 8
@@ -590,6 +616,7 @@ int hydro_create(const hydro_grid_t *grid, double gamma, const int32_t bc[3], in
         c->lo[a] = act ? grid->lo[a] : 0.0;
     }
     c->ana_axes = ana_axes;
+    c->ex_axes = ex_axes;
     if (marching && var.march > c->n[c->dim - 1]) var.march = c->n[c->dim - 1];
     c->gamma = gamma;
     c->cfl = cfl;
@@ -606,8 +633,11 @@ int hydro_create(const hydro_grid_t *grid, double gamma, const int32_t bc[3], in
         for (int a = 0; a < c->dim; ++a)
             for (int k = 0; k < c->dim + 2; ++k)
                 c->flux[a][k] = c->ws + lay.f_off[a] + lay.fplane[a] * (size_t)k;
-    if (c->dim <= 2)
+    if (c->dim <= 2) {
         for (int k = 0; k < c->dim + 2; ++k) c->frame[k] = c->ws + lay.frame_off + lay.frame_plane * (size_t)k;
+        for (int a = 0; a < c->dim; ++a)
+            for (int side = 0; side < 2; ++side) c->ex_buf[a][side] = c->ws + lay.ex_off[a][side];
+    }
     c->stream = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->copy, cudaStreamNonBlocking);

@@ -89,6 +89,18 @@ struct AnalyticLaunch {
     void *ctrl;
 };
 long long frame_cells(int dim, long long nx, long long ny);
+
+// Ghost exchange through buffers (exchange.cu): pack the two boundary layers at both ends of
+// each exchange axis (bit a of axes) from the stage input uin into buf[a][side], then unpack
+// each buffer into the ghost ring at the other end (the periodic wrap on one GPU).
+struct ExchangeLaunch {
+    int prec, dim, nx, ny, axes;
+    const void *uin[5];
+    void *buf[2][2];
+    void *frame[5];
+};
+long long exchange_buffer_cells(int dim, long long nx, long long ny, int axis);
+cudaError_t launch_exchange(const ExchangeLaunch &L, cudaStream_t st);
 cudaError_t launch_analytic_frame(const AnalyticLaunch &L, int stage, cudaStream_t st);
 
 // ---- batched 2D grids (batch_kernel.cuh) ----

@@ -20,7 +20,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libhydro.so")
 
 HYDRO_OK, HYDRO_EINVAL, HYDRO_ECUDA, HYDRO_ENONFINITE, HYDRO_ETIMEOUT, HYDRO_EUNSUPPORTED = range(6)
-HYDRO_BC_PERIODIC, HYDRO_BC_OUTFLOW, HYDRO_BC_ANALYTIC = 0, 1, 2
+HYDRO_BC_PERIODIC, HYDRO_BC_OUTFLOW, HYDRO_BC_ANALYTIC, HYDRO_BC_EXCHANGE = 0, 1, 2, 3
 HYDRO_ANALYTIC_ENTROPY_WAVE, HYDRO_ANALYTIC_SOUND_WAVE, HYDRO_ANALYTIC_SHOCK_TUBE = 1, 2, 3
 ANALYTIC_KINDS = {"entropy": 1, "sound": 2, "shock_tube": 3}
 HYDRO_F64, HYDRO_F32 = 0, 1
@@ -226,8 +226,9 @@ def analytic_state(shape, gamma: float, kind, theta: float = 0.0, amplitude: flo
 class Solver:
     """One context of libhydro.so on the current CUDA device.
 
-    shape: cells per axis (nx, [ny, [nz]]); bc: per-axis "periodic"/"outflow"/"analytic" (or
-    0/1/2; analytic boundaries take their solution from set_analytic);
+    shape: cells per axis (nx, [ny, [nz]]); bc: per-axis "periodic"/"outflow"/"analytic"/
+    "exchange" (or 0-3; analytic boundaries take their solution from set_analytic; exchange
+    boundaries wrap through the ghost pack/unpack kernels);
     variant: dict(tile=(bx, by), march=m, split=0|1|2, staging=0|1|2, occupancy=0|2|3,
     manifest=0|1|2|3) or None for the default.
     """
@@ -245,7 +246,7 @@ class Solver:
         if isinstance(bc, (str, int)):
             bc = [bc] * self.dim
         names = {"periodic": HYDRO_BC_PERIODIC, "outflow": HYDRO_BC_OUTFLOW,
-                 "analytic": HYDRO_BC_ANALYTIC}
+                 "analytic": HYDRO_BC_ANALYTIC, "exchange": HYDRO_BC_EXCHANGE}
         self.bc = [names[b] if isinstance(b, str) else int(b) for b in bc]
         g = Grid()
         g.dim = self.dim

@@ -41,6 +41,9 @@ CASES = [
     ((45, 29), (2, 2), torch.float32, {}),
     ((37, 21), (2, 1), torch.float64, {}),
     ((150,), (2,), torch.float32, {}),
+    # exchange boundaries: the pack buffers and the ring
+    ((45, 29), (3, 2), torch.float64, {}),
+    ((37, 21), (3, 3), torch.float32, {}),
 ]
 
 
