@@ -441,6 +441,15 @@ def run_ours(args):
                 "source": "operations counted in the FP64 oracle's own evaluation of one RK step "
                           "(profiles/oracle_opcounts.json); peak = hydro_fma_rate measured live"}
 
+    # the FP64 leg against the FP64 FMA rate, the same counted operations per cell-update (its
+    # divisions and square roots are correctly rounded, each many FP64 instructions, so this
+    # bound is generous too)
+    if fp64 is not None and opc is not None and fma64:
+        ach64 = opc * fp64["value"]
+        fp64["fp64_roofline"] = {"bound": "alu", "achieved": ach64, "peak": fma64,
+                                 "unit": "FP64 lane-operations/s", "frac": ach64 / fma64,
+                                 "ops_per_cell_update": opc}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_cups(device=dev)
