@@ -183,3 +183,25 @@ def test_convergence_module_runs_the_section_tests():
     assert all(x > 1.5 for x in o), o
     sod = [convergence.run("shock_tube", TH60, n, F64)["l1_rho"] for n in (32, 64)]
     assert sod[1] < sod[0] and sod[1] < 0.012, sod
+
+
+def test_analytic_boundaries_with_host_stepping_and_profiling():
+    """The ghost-ring fills also run on the host-buffer path and under per-kernel profiling,
+    with the same results as plain device stepping."""
+    V = _initial((40, 36), "shock_tube", TH60, 0.0)
+    ref, tr, sr, _ = _gpu(V, (2, 2), F64, "shock_tube", TH60, 0.0, 12)
+    S = hydro.Solver((40, 36), G, bc="analytic", dtype=F64)
+    S.set_analytic("shock_tube", TH60, 0.0)
+    host = torch.from_numpy(oracle.prim_to_cons(V, G)).pin_memory()
+    dev = torch.empty(host.shape, dtype=F64, device="cuda")
+    t, steps = S.step_host(dev, host, host, 12)
+    assert steps == sr == 12 and t == tr
+    assert np.array_equal(host.numpy(), ref)
+    P = hydro.Solver((40, 36), G, bc="analytic", dtype=F64)
+    P.set_analytic("shock_tube", TH60, 0.0)
+    P.set_profiling(True)
+    U = gpu_state(V, G, F64)
+    P.step(U, 12)
+    assert np.array_equal(U.cpu().numpy(), ref)
+    kt = P.kernel_times()
+    assert kt["stage1"][1] == 12 and kt["stage2"][1] == 12
