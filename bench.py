@@ -42,7 +42,8 @@ def _peaks():
 
 # the sources each committed ncu record depends on: a record whose digest differs was taken on
 # other kernel code and is not used
-STAGE_SOURCES = ("hydro_device.cuh", "stage_kernel.cuh", "stage_launch.cuh", "stage_f32_d3.cu")
+STAGE_SOURCES = ("hydro_device.cuh", "stage_kernel.cuh", "stage_launch.cuh", "stage_f32_d3.cu",
+                 "stage_f32_d3b.cu")
 BATCH_SOURCES = ("hydro_device.cuh", "stage_kernel.cuh", "batch_kernel.cuh", "batch_f32.cu")
 
 
