@@ -421,38 +421,48 @@ int get_graph(hydro_ctx *c, const hydro_state_t *s, int chunk, cudaGraphExec_t *
     return HYDRO_OK;
 }
 
+// Profiling: the steps launched one by one with CUDA events around each launch, in batches of
+// up to kMaxChunk steps (the events are reused); after each batch the times are collected and
+// the stepping stops once no further step is to be taken (dt = 0).
 int run_steps_profiled(hydro_ctx *c, const hydro_state_t *s, int n) {
     const hydro::StageLaunch L1 = stage_args(c, s, 1), L2 = stage_args(c, s, 2);
     const hydro::AuxArgs C = aux_args(c, s);
     const int per = c->var.split ? 3 : 2;  // launches per step
-    const size_t need = (size_t)per * n + 1;
+    const size_t need = (size_t)per * kMaxChunk + 1;
     while (c->events.size() < need) {
         cudaEvent_t e;
         CK(cudaEventCreate(&e));
         c->events.push_back(e);
     }
-    CK(cudaEventRecord(c->events[0], c->stream));
-    for (int i = 0; i < n; ++i) {
-        const int e0 = per * i;
-        CK(launch_stage(c, L1, c->stream));
-        CK(cudaEventRecord(c->events[e0 + 1], c->stream));
-        CK(launch_stage(c, L2, c->stream));
-        CK(cudaEventRecord(c->events[e0 + 2], c->stream));
-        if (c->var.split) {
-            CK(hydro::launch_cfl(C, c->stream, /*advance=*/true));
-            CK(cudaEventRecord(c->events[e0 + 3], c->stream));
+    for (int done = 0; done < n;) {
+        const int b = n - done < kMaxChunk ? n - done : kMaxChunk;
+        CK(cudaEventRecord(c->events[0], c->stream));
+        for (int i = 0; i < b; ++i) {
+            const int e0 = per * i;
+            CK(launch_stage(c, L1, c->stream));
+            CK(cudaEventRecord(c->events[e0 + 1], c->stream));
+            CK(launch_stage(c, L2, c->stream));
+            CK(cudaEventRecord(c->events[e0 + 2], c->stream));
+            if (c->var.split) {
+                CK(hydro::launch_cfl(C, c->stream, /*advance=*/true));
+                CK(cudaEventRecord(c->events[e0 + 3], c->stream));
+            }
         }
-    }
-    CK(cudaEventSynchronize(c->events[(size_t)per * n]));
-    for (int i = 0; i < n; ++i) {
-        const int e0 = per * i;
-        for (int k = 0; k < per; ++k) {
-            float m = 0;
-            CK(cudaEventElapsedTime(&m, c->events[e0 + k], c->events[e0 + k + 1]));
-            const int kind = k < 2 ? k + 1 : 0;  // stage 1, stage 2, then the CFL pass
-            c->kms[kind] += m;
-            c->klaunch[kind] += 1;
+        CK(cudaMemcpyAsync(&c->dt_probe[0], &c->ctrl->dt, sizeof(double), cudaMemcpyDeviceToHost,
+                           c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        for (int i = 0; i < b; ++i) {
+            const int e0 = per * i;
+            for (int k = 0; k < per; ++k) {
+                float m = 0;
+                CK(cudaEventElapsedTime(&m, c->events[e0 + k], c->events[e0 + k + 1]));
+                const int kind = k < 2 ? k + 1 : 0;  // stage 1, stage 2, then the CFL pass
+                c->kms[kind] += m;
+                c->klaunch[kind] += 1;
+            }
         }
+        done += b;
+        if (!(c->dt_probe[0] > 0.0)) break;
     }
     return HYDRO_OK;
 }
