@@ -106,6 +106,22 @@ def test_generous_step_bound_stops_at_t_end():
     assert np.array_equal(U.cpu().numpy(), G)
 
 
+def test_profiled_stepping_stops_at_t_end():
+    """Under profiling the steps run in batches of 64 with reused events, and the stepping stops
+    after the batch in which t_end is reached."""
+    V = inputs.sod_1d(256)
+    U = gpu_state(V, 1.4, F64)
+    S = hydro.Solver((256,), 1.4, bc="outflow", dtype=F64)
+    S.set_profiling(True)
+    t, steps = S.step(U, 10 ** 6, t_end=0.05)
+    O, to, so, _ = oracle_run(V, 1.4, (1,), 0.4, 10 ** 6, t_end=0.05)
+    assert t == to == 0.05 and steps == so
+    kt = S.kernel_times()
+    assert steps <= kt["stage1"][1] < steps + 64 and kt["stage2"][1] == kt["stage1"][1]
+    G, _, _ = gpu_run(V, 1.4, (1,), F64, 0.4, steps, t_end=0.05)
+    assert np.array_equal(U.cpu().numpy(), G)
+
+
 def test_nonfinite_and_nonpositive_are_reported():
     V = inputs.uniform((32,), rho=1.0, v=(0.0,), p=1.0)
     for bad in ("nan", "negrho"):
