@@ -487,17 +487,20 @@ def run_ours(args):
 
 def run_kh2d(args):
     """A 2D line: the shear layer (Kelvin-Helmholtz data, gamma 5/3, periodic, seed 1204477901) at
-    --size^2 (default 2048) in FP32 with the library's default 2D variant (row tiles), steps
-    timed with per-launch events like the main line."""
+    --size^2 (default 2048) in FP32 (or --dtype f64) with the library's default 2D variant (FP32:
+    row tiles; FP64: the 32 x 8 tile), steps timed with per-launch events like the main line."""
     import torch
 
     from paper_1204_4779_gb300 import hydro, inputs
     torch.cuda.set_device(0)
     n = args.size if args.size != N else 2048
     V = torch.from_numpy(inputs.kh_2d(n, seed=1204477901)).cuda()
-    U = hydro.prim_to_cons(V, 5.0 / 3.0).to(torch.float32).contiguous()
+    f64 = args.dtype == "f64"
+    dtype = torch.float64 if f64 else torch.float32
+    esz = 8 if f64 else 4
+    U = hydro.prim_to_cons(V, 5.0 / 3.0).to(dtype).contiguous()
     del V
-    S = hydro.Solver((n, n), 5.0 / 3.0, bc="periodic", dtype=torch.float32, cfl=CFL)
+    S = hydro.Solver((n, n), 5.0 / 3.0, bc="periodic", dtype=dtype, cfl=CFL)
     variant = S.variant()
     S.step(U, args.warmup)
     torch.cuda.synchronize()
@@ -514,17 +517,18 @@ def run_kh2d(args):
     kt = S.kernel_times(reset=True)
     ncell = n * n
     hbm, peak_kind = _peaks()
-    alg = {"stage1": 2 * 4 * 4 * ncell, "stage2": 3 * 4 * 4 * ncell}
+    alg = {"stage1": 2 * 4 * esz * ncell, "stage2": 3 * 4 * esz * ncell}
     dom = max(("stage1", "stage2"), key=lambda k: kt[k][0])
     avg_ms = kt[dom][0] / max(kt[dom][1], 1)
     achieved = alg[dom] / (avg_ms * 1e-3) / 1e9
-    line = {"metric": f"cell-updates/s per RK step, 2D shear layer {n}^2 (FP32)",
+    prec = "FP64" if f64 else "FP32"
+    line = {"metric": f"cell-updates/s per RK step, 2D shear layer {n}^2 ({prec})",
             "value": ncell * args.steps / (ms * 1e-3), "unit": "cell-updates/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic",
-            "config": {"workload": f"2D periodic {n}^2 shear layer, gamma 5/3, FP32",
-                       "l2": f"state {4 * 4 * ncell / 2**20:.0f} MiB vs 129 MB L2; no flush",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if f64 else "f32", "data": "synthetic",
+            "config": {"workload": f"2D periodic {n}^2 shear layer, gamma 5/3, {prec}",
+                       "l2": f"state {4 * esz * ncell / 2**20:.0f} MiB vs 129 MB L2; no flush",
                        "variant": {"tile": list(variant["tile"]), "march": variant["march"],
                                    "split": variant["split"], "occupancy": variant["occupancy"]}},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
@@ -605,6 +609,8 @@ def main():
     ap.add_argument("--config", choices=("blast512", "batched", "kh2d"), default="blast512",
                     help="blast512: the benchmark line; batched: the 4096-grid configuration; "
                          "kh2d: the 2D shear layer (--size, default 2048)")
+    ap.add_argument("--dtype", choices=("f32", "f64"), default="f32",
+                    help="precision of the kh2d line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=10,
                     help="timed FP64 steps of the same workload after the FP32 run (0: none)")
