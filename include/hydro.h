@@ -271,7 +271,9 @@ int hydro_cons_to_prim(int32_t dim, int64_t ncell, double gamma, int32_t prec,
                        const hydro_state_t *cons_in, const hydro_state_t *prim_out, void *stream);
 
 /* Per-kernel timing.  With profiling on, hydro_step launches its kernels directly (no graph)
- * with CUDA events recorded on the context's stream around each launch.
+ * with CUDA events recorded on the context's stream around each launch, in batches of up to 64
+ * steps (the call synchronises after each batch and stops once no further step is to be
+ * taken).  Stage times include the ghost-ring fills of analytic and exchange boundaries.
  * hydro_kernel_times fills, for each kernel kind k (0 = CFL pass, 1 = RK stage 1, 2 = RK
  * stage 2 with the fused dt reduction), ms_out[k] = summed device time and launches_out[k] =
  * launches since the last reset; it synchronises.  n = number of entries the arrays hold. */
