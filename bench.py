@@ -368,7 +368,8 @@ def run_ours(args):
         torch.cuda.synchronize()
         barrier()
         e2e_value, _ = aggregate_replicas(e0.elapsed_time(e1), ncell * args.e2e_steps, device=dev)
-        per_call = sorted(a.elapsed_time(b) for a, b in zip(marks, marks[1:]))
+        calls = [a.elapsed_time(b) for a, b in zip(marks, marks[1:])]
+        per_call = sorted(calls)
         nbytes = nv * 4 * ncell
         # the CPU-GPU link alone: the same state copied each way (pinned memory, CUDA events)
         link = {}
@@ -388,7 +389,7 @@ def run_ours(args):
                "steps": args.e2e_steps,
                "call": "hydro_step_host: pinned host state in, 1 RK step, host state out",
                "per_call_ms": {"min": per_call[0], "median": per_call[len(per_call) // 2],
-                               "max": per_call[-1]},
+                               "max": per_call[-1], "in_order": [round(c, 2) for c in calls]},
                "link": dict(link, note="plain copies of the state over the CPU-GPU link; the "
                                        "step's copies alone take nbytes/h2d + nbytes/d2h")}
 
