@@ -73,7 +73,7 @@ typedef enum { HYDRO_F64 = 0, HYDRO_F32 = 1 } hydro_prec_t;
 
 /* Grid: dim in {1,2,3}; n[a] >= 1 cells on active axes (n[a] is ignored and taken as 1 on
  * axes a >= dim); box [lo[a], hi[a]] with hi > lo, so dr_a = (hi[a] - lo[a]) / n[a].
- * n[0]*n[1]*n[2] must be below 2^31. */
+ * n[a] <= 2^31 - 1024 and n[0]*n[1]*n[2] < 2^31. */
 typedef struct {
     int32_t dim;
     int32_t reserved;

@@ -168,13 +168,15 @@ __global__ void __launch_bounds__(kFrameThreads) frame_kernel(const FrameArgs a,
     // ring position -> ghost cell (gx, gy), the inverse of frame_index
     const int w = a.nx + 4;
     int gx, gy;
-    if (i < 2 * w) {
-        gy = i / w - 2, gx = i % w - 2;
-    } else if (i < 4 * w) {
-        gy = a.ny + (i - 2 * w) / w, gx = (i - 2 * w) % w - 2;
+    if (i < 4 * a.ny) {
+        const int c = i % 4;
+        gy = i / 4, gx = c < 2 ? c - 2 : a.nx + c - 2;
+    } else if (i < 4 * a.ny + 2 * w) {
+        const int j = i - 4 * a.ny;
+        gy = j / w - 2, gx = j % w - 2;
     } else {
-        const int j = i - 4 * w, c = j % 4;
-        gy = j / 4, gx = c < 2 ? c - 2 : a.nx + c - 2;
+        const int j = i - 4 * a.ny - 2 * w;
+        gy = a.ny + j / w, gx = j % w - 2;
     }
     const double t = stage == 2 ? a.ctrl->t + 0.5 * a.ctrl->dt : a.ctrl->t;
     const double x = a.lo[0] + (gx + 0.5) * a.dr[0];
@@ -198,7 +200,7 @@ __global__ void __launch_bounds__(kFrameThreads) solution_kernel(const FrameArgs
 }  // namespace
 
 long long frame_cells(int dim, long long nx, long long ny) {
-    return 4 * (nx + 4) + 4 * (dim >= 2 ? ny : 1);
+    return dim >= 2 ? 4 * ny + 4 * (nx + 4) : 4;
 }
 
 static FrameArgs frame_args(const AnalyticLaunch &L) {
@@ -246,7 +248,7 @@ extern "C" int hydro_analytic_state(const hydro_grid_t *grid, double gamma, int3
     if (!(fabs(theta) < 1e6) || !(fabs(amplitude) < 1e300)) return HYDRO_EINVAL;
     long long ncell = 1;
     for (int d = 0; d < grid->dim; ++d) {
-        if (grid->n[d] < 1 || grid->n[d] > (1LL << 31) - 1 || !(grid->hi[d] > grid->lo[d]))
+        if (grid->n[d] < 1 || grid->n[d] > (1LL << 31) - 1024 || !(grid->hi[d] > grid->lo[d]))
             return HYDRO_EINVAL;
         ncell *= grid->n[d];
     }

@@ -60,7 +60,8 @@ bool grid_ok(const hydro_grid_t *g, long long *ncell) {
     if (!g || g->dim < 1 || g->dim > 3) return false;
     long long n = 1;
     for (int a = 0; a < g->dim; ++a) {
-        if (g->n[a] < 1 || g->n[a] > (1LL << 31) - 1) return false;
+        // (cell coordinates of a tile plus its halo stay below 2^31)
+        if (g->n[a] < 1 || g->n[a] > (1LL << 31) - 1024) return false;
         if (!(g->hi[a] > g->lo[a])) return false;
         n *= g->n[a];
         if (n >= (1LL << 31)) return false;

@@ -76,7 +76,8 @@ cudaError_t launch_convert(const AuxArgs &A, int to_cons, cudaStream_t st);
 constexpr int kTotalsParts = 1024;
 
 // Analytic-solution boundaries (analytic.cu).  The frame is the ring of two ghost layers
-// around an nx x ny grid (dim 1: ny = 1), frame_cells cells per plane in the order of
+// around an nx x ny grid (dim 1: the four cells beyond its ends), frame_cells cells per plane in
+// the order of
 // frame_index (stage_kernel.cuh); launch_analytic_frame fills it with the conserved form of the
 // solution `kind` (1 entropy wave, 2 sound wave of amplitude amp, 3 Sod's shock tube, each
 // travelling at angle theta from the x axis) at the time of RK stage `stage` of the step held

@@ -54,13 +54,14 @@ template <class T> struct StageArgs {
 };
 
 // Position of ghost cell (gx, gy) of an nx x ny grid (dim 1: ny = 1, gy = 0) in the frame ring
-// of two ghost layers: the two rows below the grid (x from -2 to nx + 1), the two rows above
-// it, then per grid row its four side cells (x = -2, -1, nx, nx + 1).  Size 4 (nx + 4) + 4 ny.
+// of two ghost layers: first per grid row its four side cells (x = -2, -1, nx, nx + 1), then
+// (dim 2) the two rows below the grid and the two above it, x from -2 to nx + 1.  Size
+// 4 ny + 4 (nx + 4) in dim 2, 4 in dim 1.
 __host__ __device__ __forceinline__ int frame_index(int gx, int gy, int nx, int ny) {
     const int w = nx + 4;
-    if (gy < 0) return (gy + 2) * w + gx + 2;
-    if (gy >= ny) return (gy - ny + 2) * w + gx + 2;
-    return 4 * w + gy * 4 + (gx < 0 ? gx + 2 : gx - nx + 2);
+    if (gy < 0) return 4 * ny + (gy + 2) * w + gx + 2;
+    if (gy >= ny) return 4 * ny + (gy - ny + 2) * w + gx + 2;
+    return gy * 4 + (gx < 0 ? gx + 2 : gx - nx + 2);
 }
 
 // CFL signal of one cell's new state, sum_a (|v_a| + c_s) / dr_a, folded into the running

@@ -76,7 +76,7 @@ extern "C" int hydro_step_static(const hydro_grid_t *grid, double gamma, const i
     int n[3] = {1, 1, 1}, periodic[3] = {1, 1, 1};
     double dr[3] = {1.0, 1.0, 1.0};
     for (int a = 0; a < dim; ++a) {
-        if (grid->n[a] < 1 || grid->n[a] > (1LL << 31) - 1 || !(grid->hi[a] > grid->lo[a]))
+        if (grid->n[a] < 1 || grid->n[a] > (1LL << 31) - 1024 || !(grid->hi[a] > grid->lo[a]))
             return HYDRO_EINVAL;
         if (bc[a] != HYDRO_BC_PERIODIC && bc[a] != HYDRO_BC_OUTFLOW) return HYDRO_EINVAL;
         n[a] = (int)grid->n[a];

@@ -56,6 +56,14 @@ def test_workspace_bytes_and_bad_grids():
     assert lib.hydro_workspace_bytes(ctypes.byref(_grid(1, (8,))), 7, ctypes.byref(b)) == \
         hydro.HYDRO_EINVAL
     assert lib.hydro_workspace_bytes(None, 0, ctypes.byref(b)) == hydro.HYDRO_EINVAL
+    # the per-axis limit: 2^31 - 1024 cells (a tile plus its halo stays below 2^31), and the
+    # 1D ghost ring of analytic and exchange boundaries is four cells, not a row
+    top = (1 << 31) - 1024
+    assert lib.hydro_workspace_bytes(ctypes.byref(_grid(1, (top + 1,))), hydro.HYDRO_F32,
+                                     ctypes.byref(b)) == hydro.HYDRO_EINVAL
+    assert lib.hydro_workspace_bytes(ctypes.byref(_grid(1, (top,))), hydro.HYDRO_F32,
+                                     ctypes.byref(b)) == 0
+    assert b.value < 3 * top * 4 + (1 << 20)  # the stage buffer U1 and a few small blocks
 
 
 def test_create_rejects_bad_arguments_before_touching_the_device():
