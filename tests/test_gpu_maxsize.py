@@ -30,9 +30,12 @@ def _uniform_with_bump(shape, bump_index):
     return U
 
 
-def _run(shape, bump_index, steps):
+def _run(shape, bump_index, steps, dx):
+    """Periodic run on a box of cell size dx on every axis (the same dx for the big and the small
+    grid, so that both take the same dt)."""
     U = _uniform_with_bump(shape, bump_index)
-    S = hydro.Solver(shape, G, bc="periodic", dtype=F32, cfl=0.4)
+    S = hydro.Solver(shape, G, bc="periodic", dtype=F32, cfl=0.4, lo=[0.0] * len(shape),
+                     hi=[n * dx for n in shape])
     t, n = S.step(U, steps)
     T = S.totals(U)
     S.close()
@@ -41,8 +44,8 @@ def _run(shape, bump_index, steps):
 
 def test_one_dimensional_grid_at_the_axis_limit():
     n = (1 << 31) - 1024
-    big, tb, nb, Tb = _run((n,), n - 1, 3)
-    small, ts, ns, _ = _run((64,), 63, 3)
+    big, tb, nb, Tb = _run((n,), n - 1, 3, 1.0 / 64)
+    small, ts, ns, _ = _run((64,), 63, 3, 1.0 / 64)
     assert nb == ns == 3 and tb == ts
     w = 12  # cells the bump can reach in 3 steps (two per stage and side)
     for k in range(big.shape[0]):
@@ -51,16 +54,16 @@ def test_one_dimensional_grid_at_the_axis_limit():
         assert torch.equal(b[:w], s[:w]), k
         mid = b[w:n - w]
         assert bool((mid == mid[0]).all()), k  # the rest is still the uniform state
-    # the FP64 totals of the uniform part are n-fold those of a cell, plus the bump region
-    assert abs(Tb[0] - (1.0 + 0.5 / n)) < 1e-6
+    # the FP64 mass: n cells of density 1 and the bump's extra 0.5, times dx
+    assert abs(Tb[0] - (n + 0.5) / 64) < 1e-6 * n / 64
 
 
 def test_three_dimensional_grid_just_below_2_31_cells():
     m = 1290  # 1290^3 = 2,146,689,000 < 2^31
     last = m ** 3 - 1
-    big, tb, nb, _ = _run((m, m, m), last, 2)
     s = 24
-    small, ts, ns, _ = _run((s, s, s), s ** 3 - 1, 2)
+    big, tb, nb, _ = _run((m, m, m), last, 2, 1.0 / s)
+    small, ts, ns, _ = _run((s, s, s), s ** 3 - 1, 2, 1.0 / s)
     assert nb == ns == 2 and tb == ts
     w = 8  # cells the bump can reach in 2 steps
     idx_b = np.r_[0:w, m - w:m]
