@@ -14,6 +14,7 @@ divided by the slowest rank's time.
 from __future__ import annotations
 
 import argparse
+import gc
 import hashlib
 import json
 import os
@@ -466,6 +467,7 @@ def run_ours(args):
                        "grid": [n, n, n], "gamma": GAMMA, "cfl": CFL,
                        "blast_radius_cells": RADIUS, "parallelism": f"replicas x{world}",
                        "l2": f"inputs larger than L2 ({5 * 4 * ncell / 2**30:.2f} GiB state vs 129 MB L2); no flush",
+                       "host": "Python cyclic GC off during the run",
                        "variant": variant},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": traffic, "kernel": dom,
@@ -620,6 +622,10 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    # Python's cyclic garbage collector off for the run (as timeit does): its pauses stall the
+    # host thread that issues the launches and copies, tens of milliseconds at a time
+    gc.collect()
+    gc.disable()
     if args.impl == "reference":
         run_reference(args)
     elif args.config == "batched":
