@@ -28,22 +28,22 @@ def _initial(shape, kind, theta, amp):
     return inputs.oblique_wave(shape, kind, theta, amp=amp)
 
 
-def _gpu(V, bc, dtype, kind, theta, amp, n, t_end=0.0, variant=None, order=2):
+def _gpu(V, bc, dtype, kind, theta, amp, n, t_end=0.0, variant=None, order=2, riemann=0):
     U = gpu_state(V, G, dtype)
     S = hydro.Solver(shape_of(V), G, bc=list(bc), dtype=dtype, cfl=0.4, variant=variant)
     S.set_analytic(kind, theta, amp)
-    if order != 2:
-        S.set_scheme(order, 0)
+    if order != 2 or riemann != 0:
+        S.set_scheme(order, riemann)
     t, steps = S.step(U, n, t_end=t_end)
     var = S.variant()
     S.close()
     return U.to(F64).cpu().numpy(), t, steps, var
 
 
-def _oracle(V, bc, kind, theta, amp, n, t_end=0.0, order=2):
+def _oracle(V, bc, kind, theta, amp, n, t_end=0.0, order=2, riemann=0):
     U = oracle.prim_to_cons(V, G)
     return oracle.run(U, G, 0.4, n, bc=bc, t_end=t_end, threads=oracle.max_threads(),
-                      analytic=(KIND[kind], theta, amp), order=order)
+                      analytic=(KIND[kind], theta, amp), order=order, riemann=riemann)
 
 
 CASES64 = [
@@ -71,6 +71,14 @@ def test_fp64_parity_with_the_oracle(case):
     assert err <= 1e-10, err
     if len(shape) == 2:
         assert var["tile"][1] > 1  # analytic boundaries run on one-plane tiles
+
+
+def test_fp64_pressure_based_speeds_parity():
+    V = _initial((37, 29), "shock_tube", TH60, 0.0)
+    Gd, tg, sg, _ = _gpu(V, (2, 2), F64, "shock_tube", TH60, 0.0, 10 ** 6, 0.1, riemann=1)
+    O, to, so, _ = _oracle(V, (2, 2), "shock_tube", TH60, 0.0, 10 ** 6, 0.1, riemann=1)
+    assert sg == so and tg == to == 0.1
+    assert max_rel_err(Gd, O) <= 1e-10
 
 
 def test_fp64_order1_parity():
