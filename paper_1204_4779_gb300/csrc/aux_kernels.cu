@@ -15,7 +15,8 @@ constexpr int kAuxThreads = 256;
 template <class T> struct AuxT {
     const T *u[5];
     T *out[5];
-    long long ncell;
+    long long ncell, first;
+    unsigned total_blocks;
     double dr[3];
     T inv_dr[3];
     Gas<T> gas;
@@ -29,6 +30,8 @@ template <class T> AuxT<T> make_aux(const AuxArgs &A) {
         a.out[k] = static_cast<T *>(A.out[k]);
     }
     a.ncell = A.ncell;
+    a.first = A.first;
+    a.total_blocks = A.total_blocks;
     for (int d = 0; d < 3; ++d) {
         a.dr[d] = A.dr[d];
         a.inv_dr[d] = T(1.0 / A.dr[d]);
@@ -39,7 +42,9 @@ template <class T> AuxT<T> make_aux(const AuxArgs &A) {
 }
 
 // Max over cells of sum_a (|v_a| + c_s) / dr_a, c_s = sqrt(gamma p / rho); flags rho <= 0 or
-// p <= 0; the last CTA turns the max into dt (cfl / max, clipped onto t_end).
+// p <= 0; the last CTA turns the max into dt (cfl / max, clipped onto t_end).  A pass may be
+// split into launches over consecutive cell ranges [first, first + ncell) whose CTAs add up to
+// total_blocks: the running maximum and the CTA count then span the launches.
 template <class T, int D, bool ADVANCE>
 __global__ void __launch_bounds__(kAuxThreads) cfl_kernel(const AuxT<T> A) {
     __shared__ T sred[2 * kAuxThreads / 32];
@@ -50,7 +55,9 @@ __global__ void __launch_bounds__(kAuxThreads) cfl_kernel(const AuxT<T> A) {
     T smax = T(0);
     bool bad = false;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < A.ncell; i += stride) {
+    const long long end = A.first + A.ncell;
+    for (long long i = A.first + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < end;
+         i += stride) {
         T u[NV], v[NV];
 #pragma unroll
         for (int k = 0; k < NV; ++k) u[k] = A.u[k][i];
@@ -68,7 +75,7 @@ __global__ void __launch_bounds__(kAuxThreads) cfl_kernel(const AuxT<T> A) {
         smax = (s > smax || s != s) ? s : smax;
         bad |= !(v[0] > T(0)) || !(v[NV - 1] > T(0));
     }
-    reduce_signal_and_finalize<T, kAuxThreads>(A.ctrl, smax, bad, ADVANCE, sred);
+    reduce_signal_and_finalize<T, kAuxThreads>(A.ctrl, smax, bad, ADVANCE, sred, A.total_blocks);
 }
 
 // Totals, level 1: CTA b sums the contiguous chunk [b*chunk, (b+1)*chunk) of each plane in
@@ -209,6 +216,8 @@ template <class T> cudaError_t convert_t(const AuxArgs &A, int to_cons, cudaStre
 }
 
 }  // namespace
+
+unsigned cfl_blocks(long long ncell) { return (unsigned)grid_for(ncell); }
 
 cudaError_t launch_cfl(const AuxArgs &A, cudaStream_t st, bool advance) {
     if (A.prec == 1) return advance ? cfl_t<float, true>(A, st) : cfl_t<float, false>(A, st);

@@ -345,8 +345,8 @@ hydro::AuxArgs aux_args(const hydro_ctx *c, const hydro_state_t *s) {
     return A;
 }
 
-// Reset the control block and run the CFL pass: dt of the first step from `s`.
-int begin_steps(hydro_ctx *c, const hydro_state_t *s, double t0, double t_end) {
+// Reset the control block for a call starting at t0.
+int init_ctrl(hydro_ctx *c, double t0, double t_end) {
     Ctrl init;
     memset(&init, 0, sizeof init);
     init.t = t0;
@@ -354,6 +354,13 @@ int begin_steps(hydro_ctx *c, const hydro_state_t *s, double t0, double t_end) {
     init.cfl = c->cfl;
     for (int a = 0; a < 3; ++a) init.dr[a] = c->dr[a];
     CK(cudaMemcpyAsync(c->ctrl, &init, sizeof init, cudaMemcpyHostToDevice, c->stream));
+    return HYDRO_OK;
+}
+
+// Reset the control block and run the CFL pass: dt of the first step from `s`.
+int begin_steps(hydro_ctx *c, const hydro_state_t *s, double t0, double t_end) {
+    const int rc = init_ctrl(c, t0, t_end);
+    if (rc) return rc;
     if (c->profiling) {
         while (c->events.size() < 2) {
             cudaEvent_t e;
@@ -797,6 +804,48 @@ static int last_step_overlapped(hydro_ctx *c, const hydro_state_t *s, void *cons
     return HYDRO_OK;
 }
 
+// The copy in of hydro_step_host in dim 3 with the CFL pass overlapped: the state comes in
+// z-slab by z-slab on the private copy stream, and each slab's part of the CFL pass runs on the
+// context's stream as soon as the slab has arrived, so only the last part follows the copy.
+// The parts share one running maximum; the last CTA of all of them sets dt.
+static int copy_in_overlapped(hydro_ctx *c, const hydro_state_t *dev,
+                              const void *const host_in[5], double t0, double t_end) {
+    const int nslabs = c->n[2] < 8 ? c->n[2] : 8;
+    while ((int)c->slab_events.size() < nslabs + 1) {
+        cudaEvent_t e;
+        CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        c->slab_events.push_back(e);
+    }
+    const int rc = init_ctrl(c, t0, t_end);
+    if (rc) return rc;
+    // the copies start after the stream's earlier work on the state
+    CK(cudaEventRecord(c->slab_events[(size_t)nslabs], c->stream));
+    CK(cudaStreamWaitEvent(c->copy, c->slab_events[(size_t)nslabs], 0));
+    const size_t esz = c->prec == HYDRO_F32 ? 4 : 8;
+    const long long plane = (long long)c->n[0] * c->n[1];
+    hydro::AuxArgs A = aux_args(c, dev);
+    unsigned total = 0;
+    for (int i = 0; i < nslabs; ++i) {
+        const long long z0 = (long long)c->n[2] * i / nslabs, z1 = (long long)c->n[2] * (i + 1) / nslabs;
+        total += hydro::cfl_blocks((z1 - z0) * plane);
+    }
+    A.total_blocks = total;
+    for (int i = 0; i < nslabs; ++i) {
+        const long long z0 = (long long)c->n[2] * i / nslabs, z1 = (long long)c->n[2] * (i + 1) / nslabs;
+        const size_t off = (size_t)(z0 * plane) * esz, bytes = (size_t)((z1 - z0) * plane) * esz;
+        for (int k = 0; k < c->dim + 2; ++k)
+            CK(cudaMemcpyAsync(static_cast<char *>(dev->plane[k]) + off,
+                               static_cast<const char *>(host_in[k]) + off, bytes,
+                               cudaMemcpyHostToDevice, c->copy));
+        CK(cudaEventRecord(c->slab_events[(size_t)i], c->copy));
+        CK(cudaStreamWaitEvent(c->stream, c->slab_events[(size_t)i], 0));
+        A.first = z0 * plane;
+        A.ncell = (z1 - z0) * plane;
+        CK(hydro::launch_cfl(A, c->stream));
+    }
+    return HYDRO_OK;
+}
+
 int hydro_step_host(hydro_ctx_t *c, const hydro_state_t *dev, const void *const host_in[5],
                     void *const host_out[5], int32_t n_steps, double t_end, double *t_inout,
                     int32_t *steps_done) {
@@ -806,13 +855,19 @@ int hydro_step_host(hydro_ctx_t *c, const hydro_state_t *dev, const void *const 
         if (!host_in[k] || !host_out[k]) return HYDRO_EINVAL;
     DeviceGuard dg(c->device);
     const size_t bytes = (size_t)c->ncell * (c->prec == HYDRO_F32 ? 4 : 8);
-    for (int k = 0; k < c->dim + 2; ++k)
-        CK(cudaMemcpyAsync(dev->plane[k], host_in[k], bytes, cudaMemcpyHostToDevice, c->stream));
     double t = t_inout ? *t_inout : 0.0;
     int32_t done = 0;
-    int rc = begin_steps(c, dev, t, t_end);
-    // dim 3 outside profiling: the last step overlaps its copy back with its stage 2
+    // dim 3 outside profiling: the copy in overlaps the CFL pass and the last step's stage 2
+    // overlaps the copy back
     const bool overlap = c->dim == 3 && n_steps >= 1 && !c->profiling && c->var.manifest == 1;
+    int rc;
+    if (overlap) {
+        rc = copy_in_overlapped(c, dev, host_in, t, t_end);
+    } else {
+        for (int k = 0; k < c->dim + 2; ++k)
+            CK(cudaMemcpyAsync(dev->plane[k], host_in[k], bytes, cudaMemcpyHostToDevice, c->stream));
+        rc = begin_steps(c, dev, t, t_end);
+    }
     if (!rc) rc = run_steps(c, dev, overlap ? n_steps - 1 : n_steps, /*stop_early=*/true);
     if (!rc && overlap) rc = last_step_overlapped(c, dev, host_out);
     if (rc) return rc;

@@ -56,7 +56,9 @@ extern const int kNumTiles;
 struct AuxArgs {
     int prec;
     int dim;
-    long long ncell;
+    long long ncell;        // cells the launch covers (the CFL pass: from cell `first`)
+    long long first;        // CFL pass over part of the grid: its first cell (0: all)
+    unsigned total_blocks;  // CFL pass in parts: CTAs of all the parts' launches (0: this one)
     const void *u[5];
     void *out[5];
     double dr[3];
@@ -67,6 +69,8 @@ struct AuxArgs {
 // a call (ctrl freshly initialised); true: after an RK step whose stage 2 left the reduction
 // to this pass (t advances by the step's dt first).
 cudaError_t launch_cfl(const AuxArgs &A, cudaStream_t st, bool advance = false);
+// CTAs a CFL-pass launch over `ncell` cells uses (to sum over the parts of a split pass).
+unsigned cfl_blocks(long long ncell);
 // Totals: per-CTA partials into `partials` (dim+2 x nparts doubles), then the fixed-order
 // final sum times the cell volume into ctrl->totals.
 cudaError_t launch_totals(const AuxArgs &A, double *partials, int nparts, double vol,
