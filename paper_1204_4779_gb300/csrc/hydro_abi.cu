@@ -763,12 +763,12 @@ int hydro_step(hydro_ctx_t *c, const hydro_state_t *state, int32_t n_steps, doub
     return finish_steps(c, t_inout, steps_done);
 }
 
-// The last step of hydro_step_host in dim 3, with the copy back overlapped: stage 1 over the
-// grid, then stage 2 slab by slab (groups of march chunks along z, the dt reduction left to a
-// CFL pass), each slab's finished planes copied to the host on the private copy stream while
-// the next slabs compute; the CFL pass (status, time, next dt) runs after the last slab.  A
-// slab's U is final when its stage-2 launch ends: stage 2 writes only its own cells and reads
-// other slabs' U1, not U.  Returns with the copy stream joined into the context's stream.
+// The last step of hydro_step_host in dim 3, with the copy back overlapped: stages 1 and 2
+// slab by slab (groups of march chunks along z, the dt reduction left to a CFL pass), each
+// slab's finished planes copied to the host on the private copy stream while the next slabs
+// compute; the CFL pass (status, time, next dt) runs after the last slab.  A slab's U is final
+// when its stage-2 launch ends: stage 2 writes only its own cells and reads other slabs' U1,
+// not U.  Returns with the copy stream joined into the context's stream.
 static int last_step_overlapped(hydro_ctx *c, const hydro_state_t *s, void *const host_out[5]) {
     const int march = c->var.march;
     const int nchunks = (c->n[2] + march - 1) / march;
@@ -780,12 +780,33 @@ static int last_step_overlapped(hydro_ctx *c, const hydro_state_t *s, void *cons
     }
     const size_t esz = c->prec == HYDRO_F32 ? 4 : 8;
     const size_t plane_cells = (size_t)c->n[0] * (size_t)c->n[1];
-    CK(launch_stage(c, stage_args(c, s, 1), c->stream));
+    auto chunk0 = [&](int i) { return (int)((long long)nchunks * i / nslabs); };
+    // Stage 1 runs by slabs too, interleaved so that slab i of stage 2 (which overwrites U0 in
+    // place) follows every stage-1 slab that reads U0 planes of slab i (its neighbours, the last
+    // slab through the periodic wrap): last, 0, 1, then stage 2 of slab i after stage 1 of slab
+    // i + 1.  The copy back of the first slab can then start after two stage-1 slabs instead of
+    // the whole of stage 1.
+    hydro::StageLaunch L1 = stage_args(c, s, 1);
+    auto stage1_slab = [&](int i) -> cudaError_t {
+        L1.zchunk0 = chunk0(i);
+        L1.zchunks = chunk0(i + 1) - chunk0(i);
+        return launch_stage(c, L1, c->stream);
+    };
+    // (every slab at least two planes thick, so that the U0 planes a stage-1 slab reads lie in
+    // its neighbouring slabs; otherwise stage 1 runs whole first)
+    const bool interleave = march >= 2 && c->n[2] - chunk0(nslabs - 1) * march >= 2;
+    if (interleave) {
+        CK(stage1_slab(nslabs - 1));
+        if (nslabs > 1) CK(stage1_slab(0));
+    } else {
+        CK(launch_stage(c, stage_args(c, s, 1), c->stream));
+    }
     hydro::StageLaunch L2 = stage_args(c, s, 2);
     L2.split = 1;
     for (int i = 0; i < nslabs; ++i) {
-        const int k0 = (int)((long long)nchunks * i / nslabs);
-        const int k1 = (int)((long long)nchunks * (i + 1) / nslabs);
+        if (interleave && i + 1 <= nslabs - 2) CK(stage1_slab(i + 1));
+        const int k0 = chunk0(i);
+        const int k1 = chunk0(i + 1);
         L2.zchunk0 = k0;
         L2.zchunks = k1 - k0;
         CK(launch_stage(c, L2, c->stream));

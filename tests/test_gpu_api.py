@@ -201,15 +201,21 @@ def test_single_cell_axes_and_tiny_grids():
         assert sg == so and np.allclose(G, O, rtol=1e-12, atol=1e-12)
 
 
-@pytest.mark.parametrize("n_steps,t_end", [(1, 0.0), (3, 0.0), (5, 0.002)])
-def test_host_stepping_3d_overlapped_copy_back(n_steps, t_end):
-    """In 3D the last step of hydro_step_host copies each z-slab back while later slabs compute
-    (13 march chunks of 8 planes, the last one ragged, in 8 slabs): the host result, time and
-    step count equal stepping on the device."""
-    V = inputs.blast_3d(shape=(40, 36, 100), radius_cells=6.0)
+@pytest.mark.parametrize("n_steps,t_end,shape,bc", [
+    (1, 0.0, (40, 36, 100), (0, 0, 0)), (3, 0.0, (40, 36, 100), (0, 0, 0)),
+    (5, 0.002, (40, 36, 100), (0, 0, 0)),
+    (1, 0.0, (40, 36, 100), (0, 1, 1)),   # outflow along z
+    (2, 0.0, (24, 20, 57), (0, 0, 0)),    # a last slab of one plane: stage 1 whole first
+    (1, 0.0, (24, 20, 11), (0, 0, 0))])   # fewer planes than slabs
+def test_host_stepping_3d_overlapped_copy_back(n_steps, t_end, shape, bc):
+    """In 3D hydro_step_host copies the state in by z-slabs with the first CFL pass split over
+    them, and runs the last step's two stages slab by slab, copying each slab back while later
+    slabs compute (e.g. 13 march chunks of 8 planes, the last one ragged, in 8 slabs): the host
+    result, time and step count equal stepping on the device."""
+    V = inputs.blast_3d(shape=shape, radius_cells=6.0)
     U = gpu_state(V, 1.4, F32)
     var = dict(march=8)
-    S = hydro.Solver((40, 36, 100), 1.4, dtype=F32, variant=var)
+    S = hydro.Solver(shape, 1.4, bc=list(bc), dtype=F32, variant=var)
     Ud = U.clone()
     td, nd = S.step(Ud, n_steps, t_end=t_end)
     host = U.cpu().pin_memory()
