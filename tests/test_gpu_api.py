@@ -206,7 +206,7 @@ def test_single_cell_axes_and_tiny_grids():
     (5, 0.002, (40, 36, 100), (0, 0, 0)),
     (1, 0.0, (40, 36, 100), (0, 1, 1)),   # outflow along z
     (2, 0.0, (24, 20, 57), (0, 0, 0)),    # a last slab of one plane: stage 1 whole first
-    (1, 0.0, (24, 20, 11), (0, 0, 0))])   # fewer planes than slabs
+    (1, 0.0, (24, 20, 11), (0, 0, 0))])   # two march chunks: two slabs
 def test_host_stepping_3d_overlapped_copy_back(n_steps, t_end, shape, bc):
     """In 3D hydro_step_host copies the state in by z-slabs with the first CFL pass split over
     them, and runs the last step's two stages slab by slab, copying each slab back while later
