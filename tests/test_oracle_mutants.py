@@ -46,6 +46,11 @@ MUTANTS = [
     ("sod_contact_side", "int right = xi > us;", "int right = xi > 0.0;"),
     ("sod_shock_density", "out[0] = K[0] * (r + m) / (m * r + 1.0)", "out[0] = K[0] * (r + m) / (r + 1.0)"),
     ("sod_rarefaction_tail", "double tail = us + q * astar;", "double tail = us + q * a;"),
+    ("outflow_second_cell", "src[a] = ia < 0 ? 0 : G->n[a] - 1;", "src[a] = ia < 0 ? 1 : G->n[a] - 2;"),
+    ("cons_energy_kinetic_factor", "V[dim + 1] / (gamma - 1.0) + 0.5 * rho * v2;",
+     "V[dim + 1] / (gamma - 1.0) + rho * v2;"),
+    ("clip_compares_t_end_with_dt", "if (t_end > 0.0 && dt >= t_end - t) {", "if (t_end > 0.0 && dt >= t_end) {"),
+    ("totals_volume_axis", "vol *= dr[a];", "vol *= dr[0];"),
 ]
 
 
@@ -161,7 +166,19 @@ def _battery():
         from test_oracle_analytic_bc import sod_sample_deviation
         return sod_sample_deviation() <= 1e-13
 
-    for name, fn in [("sod", sod), ("entropy", entropy), ("ywave", ywave), ("contact", contact),
+    def totals():
+        from test_oracle_pins import test_totals_closed_form
+        test_totals_closed_form()
+        return True
+
+    def bruteforce():
+        # one RK step on tiny outflow grids against the 50-digit evaluation of the definitions
+        from test_oracle_bruteforce import test_one_rk_step_matches_decimal_evaluation as t
+        t((7,), (1,))
+        t((3, 4), (1, 0))
+        return True
+
+    for name, fn in [("totals", totals), ("bruteforce", bruteforce), ("sod", sod), ("entropy", entropy), ("ywave", ywave), ("contact", contact),
                      ("consistency", consistency), ("moving_contact", moving_contact),
                      ("euler_def", euler_def), ("star_rh", star_rh), ("limiter", limiter), ("cfl", cfl), ("conservation", conservation),
                      ("analytic", analytic)]:
