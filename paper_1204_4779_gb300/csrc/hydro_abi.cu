@@ -763,6 +763,32 @@ int hydro_step(hydro_ctx_t *c, const hydro_state_t *state, int32_t n_steps, doub
     return finish_steps(c, t_inout, steps_done);
 }
 
+// Copy the byte range [off, off + bytes) of each of n planes (dst[k] <- src[k]).  When both
+// sides' planes are equally spaced (one tensor of planes), one strided copy moves all of them.
+static cudaError_t copy_planes(void *const dst[5], const void *const src[5], int n, size_t off,
+                               size_t bytes, cudaMemcpyKind kind, cudaStream_t st) {
+    bool even = n > 1;
+    const long long dp = n > 1 ? (long long)((const char *)dst[1] - (const char *)dst[0]) : 0;
+    const long long sp = n > 1 ? (long long)((const char *)src[1] - (const char *)src[0]) : 0;
+    for (int k = 2; k < n && even; ++k)
+        even = (const char *)dst[k] - (const char *)dst[k - 1] == dp &&
+               (const char *)src[k] - (const char *)src[k - 1] == sp;
+    // positive pitches of at least the row width and below 2 GiB (the pitch limit of copies)
+    even = even && dp >= (long long)bytes && sp >= (long long)bytes && dp < (1LL << 31) &&
+           sp < (1LL << 31);
+    if (even)
+        return cudaMemcpy2DAsync(static_cast<char *>(dst[0]) + off, (size_t)dp,
+                                 static_cast<const char *>(src[0]) + off, (size_t)sp, bytes,
+                                 (size_t)n, kind, st);
+    for (int k = 0; k < n; ++k) {
+        const cudaError_t e = cudaMemcpyAsync(static_cast<char *>(dst[k]) + off,
+                                              static_cast<const char *>(src[k]) + off, bytes,
+                                              kind, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 // The last step of hydro_step_host in dim 3, with the copy back overlapped: stages 1 and 2
 // slab by slab (groups of march chunks along z, the dt reduction left to a CFL pass), each
 // slab's finished planes copied to the host on the private copy stream while the next slabs
@@ -814,10 +840,7 @@ static int last_step_overlapped(hydro_ctx *c, const hydro_state_t *s, void *cons
         CK(cudaStreamWaitEvent(c->copy, c->slab_events[(size_t)i], 0));
         const int z0 = k0 * march, z1 = k1 * march < c->n[2] ? k1 * march : c->n[2];
         const size_t off = (size_t)z0 * plane_cells * esz, bytes = (size_t)(z1 - z0) * plane_cells * esz;
-        for (int k = 0; k < c->dim + 2; ++k)
-            CK(cudaMemcpyAsync(static_cast<char *>(host_out[k]) + off,
-                               static_cast<const char *>(s->plane[k]) + off, bytes,
-                               cudaMemcpyDeviceToHost, c->copy));
+        CK(copy_planes(host_out, s->plane, c->dim + 2, off, bytes, cudaMemcpyDeviceToHost, c->copy));
     }
     CK(hydro::launch_cfl(aux_args(c, s), c->stream, /*advance=*/true));
     CK(cudaEventRecord(c->slab_events[(size_t)nslabs], c->copy));
@@ -854,10 +877,7 @@ static int copy_in_overlapped(hydro_ctx *c, const hydro_state_t *dev,
     for (int i = 0; i < nslabs; ++i) {
         const long long z0 = (long long)c->n[2] * i / nslabs, z1 = (long long)c->n[2] * (i + 1) / nslabs;
         const size_t off = (size_t)(z0 * plane) * esz, bytes = (size_t)((z1 - z0) * plane) * esz;
-        for (int k = 0; k < c->dim + 2; ++k)
-            CK(cudaMemcpyAsync(static_cast<char *>(dev->plane[k]) + off,
-                               static_cast<const char *>(host_in[k]) + off, bytes,
-                               cudaMemcpyHostToDevice, c->copy));
+        CK(copy_planes(dev->plane, host_in, c->dim + 2, off, bytes, cudaMemcpyHostToDevice, c->copy));
         CK(cudaEventRecord(c->slab_events[(size_t)i], c->copy));
         CK(cudaStreamWaitEvent(c->stream, c->slab_events[(size_t)i], 0));
         A.first = z0 * plane;

@@ -228,6 +228,40 @@ def test_host_stepping_3d_overlapped_copy_back(n_steps, t_end, shape, bc):
     assert torch.equal(dev, Ud)
 
 
+def test_host_stepping_with_separate_host_planes():
+    """Host planes in separate allocations (not one tensor): the copies go plane by plane
+    instead of one strided copy per slab, with the same result."""
+    import ctypes
+    shape = (40, 36, 100)
+    V = inputs.blast_3d(shape=shape, radius_cells=6.0)
+    U = gpu_state(V, 1.4, F32)
+    S = hydro.Solver(shape, 1.4, dtype=F32, variant=dict(march=8))
+    Ud = U.clone()
+    td, nd = S.step(Ud, 2)
+    # planes at irregular offsets of pinned buffers, so that no single pitch fits them
+    N = U[0].numel()
+    offs = [k * N + 16 * k * k for k in range(5)]
+    hin = torch.empty(5 * N + 1024, dtype=F32).pin_memory()
+    hout = torch.full((5 * N + 1024,), float("nan"), dtype=F32).pin_memory()
+    planes, outs = [], []
+    for k in range(5):
+        planes.append(hin[offs[k]:offs[k] + N].view(U[k].shape))
+        planes[k].copy_(U[k].cpu())
+        outs.append(hout[offs[k]:offs[k] + N].view(U[k].shape))
+    dev = torch.empty_like(U)
+    st = hydro.state_struct(dev, 5)
+    pin = (ctypes.c_void_p * 5)(*[p.data_ptr() for p in planes])
+    pout = (ctypes.c_void_p * 5)(*[o.data_ptr() for o in outs])
+    t = ctypes.c_double(0.0)
+    n = ctypes.c_int32()
+    torch.cuda.synchronize()
+    assert S.lib.hydro_step_host(S.ctx, ctypes.byref(st), pin, pout, 2, 0.0, ctypes.byref(t),
+                                 ctypes.byref(n)) == 0
+    assert n.value == nd and t.value == td
+    for k in range(5):
+        assert torch.equal(outs[k], Ud[k].cpu()), k
+
+
 def test_resolved_default_variants():
     """hydro_get_variant: the library defaults per dimension and precision, and the defaults a
     variant that names another tile gets (that tile's march and register budget)."""
