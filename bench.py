@@ -606,7 +606,7 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--e2e-steps", type=int, default=20,
+    ap.add_argument("--e2e-steps", type=int, default=40,
                     help="timed hydro_step_host calls of one step each (mean over the calls)")
     ap.add_argument("--size", type=int, default=N, help="cube side (the benchmark config is 512)")
     ap.add_argument("--config", choices=("blast512", "batched", "kh2d"), default="blast512",
