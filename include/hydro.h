@@ -246,7 +246,10 @@ int hydro_step(hydro_ctx_t *ctx, const hydro_state_t *state, int32_t n_steps, do
 /* Same as hydro_step, but the state comes from and goes back to HOST memory: the dim+2
  * planes at host_in[k] are copied into the device planes of `dev_state`, stepped, and copied
  * out to host_out[k] (host_out may equal host_in).  Pinned host memory gives full copy
- * bandwidth.  Always synchronises. */
+ * bandwidth.  In dim 3 the copies overlap the work: the state comes in by z-slabs, each slab's
+ * part of the first CFL pass starting on arrival, and the last step runs both stages slab by
+ * slab, each finished slab going back while later slabs compute; planes that are equally
+ * spaced on both sides (one tensor) move as one strided copy per slab.  Always synchronises. */
 int hydro_step_host(hydro_ctx_t *ctx, const hydro_state_t *dev_state,
                     const void *const host_in[5], void *const host_out[5], int32_t n_steps,
                     double t_end, double *t_inout, int32_t *steps_done);
