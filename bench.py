@@ -488,6 +488,57 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_wave(args):
+    """The paper's linear-wave example (hydro_wave_run, f_t = g, g_t = c^2 f_xx on a periodic 1D
+    grid) at --size cells (default 2^27) in FP32 (or --dtype f64): steps timed with CUDA events
+    around the call, against the HBM roofline of its algorithmic traffic (read f and g, write
+    both: 16 B per cell-update in FP32)."""
+    import math
+
+    import torch
+
+    from paper_1204_4779_gb300 import hydro
+    torch.cuda.set_device(0)
+    n = args.size if args.size != N else 1 << 27
+    f64 = args.dtype == "f64"
+    dtype = torch.float64 if f64 else torch.float32
+    esz = 8 if f64 else 4
+    L, c = 2.0 * math.pi, 1.0
+    dt = 0.5 * (L / n) / c
+    x = torch.arange(n, dtype=torch.float64, device="cuda") * (L / n)
+    f = torch.sin(x).to(dtype)
+    g = torch.zeros(n, dtype=dtype, device="cuda")
+    del x
+    steps = args.steps + (args.steps & 1)  # even: the result ends in the caller's arrays
+    hydro.wave_run(f, g, c, L, dt, 2 * args.warmup)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(_gpu_index(0)) as clk:
+        torch.cuda.synchronize()
+        e0.record()
+        E = hydro.wave_run(f, g, c, L, dt, steps)
+        e1.record()
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    hbm, peak_kind = _peaks()
+    achieved = 4 * esz * n * steps / (ms * 1e-3) / 1e9
+    drift = max(abs(e - E[0]) for e in E) / abs(E[0])
+    line = {"metric": f"cell-updates/s per step, linear wave {n} cells ({'FP64' if f64 else 'FP32'})",
+            "value": n * steps / (ms * 1e-3), "unit": "cell-updates/s", "n_gpus": 1,
+            "steps": steps, "warmup": args.warmup, "ms_per_step": ms / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if f64 else "f32", "data": "synthetic",
+            "config": {"workload": f"1D periodic linear wave (the paper's section 2.3 example), {n} cells, "
+                                   "c = 1, dt = dx / 2, one sine period",
+                       "l2": f"state {2 * esz * n / 2**20:.0f} MiB vs 129 MB L2; no flush",
+                       "energy_drift": drift},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": None, "kernel": "wave_step_kernel",
+                         "bytes_per_cell_update": 4 * esz,
+                         "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"},
+            "gpu_launches": 2 * steps, "clocks": clk.summary(), "e2e": None, "cpu_baseline": None}
+    print(json.dumps(line), flush=True)
+
+
 def run_kh2d(args):
     """A 2D line: the shear layer (Kelvin-Helmholtz data, gamma 5/3, periodic, seed 1204477901) at
     --size^2 (default 2048) in FP32 (or --dtype f64) with the library's default 2D variant (FP32:
@@ -609,11 +660,12 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=40,
                     help="timed hydro_step_host calls of one step each (mean over the calls)")
     ap.add_argument("--size", type=int, default=N, help="cube side (the benchmark config is 512)")
-    ap.add_argument("--config", choices=("blast512", "batched", "kh2d"), default="blast512",
+    ap.add_argument("--config", choices=("blast512", "batched", "kh2d", "wave"), default="blast512",
                     help="blast512: the benchmark line; batched: the 4096-grid configuration; "
-                         "kh2d: the 2D shear layer (--size, default 2048)")
+                         "kh2d: the 2D shear layer (--size, default 2048); wave: the linear-wave "
+                         "example (--size, default 2^27)")
     ap.add_argument("--dtype", choices=("f32", "f64"), default="f32",
-                    help="precision of the kh2d line")
+                    help="precision of the kh2d and wave lines")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=10,
                     help="timed FP64 steps of the same workload after the FP32 run (0: none)")
@@ -632,6 +684,8 @@ def main():
         run_batched(args)
     elif args.config == "kh2d":
         run_kh2d(args)
+    elif args.config == "wave":
+        run_wave(args)
     else:
         run_ours(args)
 

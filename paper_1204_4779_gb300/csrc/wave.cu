@@ -7,9 +7,10 @@
 // audited in FP64 after every step (the form of the paper's listing, which the scheme conserves
 // to round-off).
 //
-// One launch per step: a CTA owns a tile of cells, recomputes f1 on its tile plus one halo cell
-// each side from f and g (no second pass over f1), updates g, and reduces its energy terms
-// into one FP64 partial with a fixed tree; a one-CTA kernel sums the partials in fixed order.
+// One launch per step: a CTA walks tiles of cells (tile b, b + G, ... for G CTAs), recomputes f1
+// on each tile plus one halo cell each side from f and g (no second pass over f1), updates g,
+// and reduces the tile's energy terms with a fixed tree, summing its tiles in order into one
+// FP64 partial; a one-CTA kernel sums the G partials in fixed order.
 // State ping-pongs between the caller's arrays and two workspace arrays.  FP64 is compiled with
 // --fmad=false (plain IEEE operations in the order of the formulas); FP32 runs the stencil in
 // FP32 and the energy in FP64.
@@ -25,41 +26,46 @@ constexpr int kWaveThreads = 256;
 template <class T>
 __global__ void __launch_bounds__(kWaveThreads)
     wave_step_kernel(const T *__restrict__ f, const T *__restrict__ g, T *__restrict__ fo,
-                     T *__restrict__ go, long long n, T dt, T k, double c2, double dx,
-                     double *partial) {
+                     T *__restrict__ go, long long n, long long ntiles, T dt, T k, double c2,
+                     double dx, double *partial) {
     __shared__ T s_f1[kWaveThreads + 2];
     __shared__ double s_e[kWaveThreads];
-    const long long base = (long long)blockIdx.x * kWaveThreads;
-    const long long i = base + threadIdx.x;
-    const bool active = i < n;
-    // f1 on the tile and its two halo cells (periodic)
-    if (active) s_f1[threadIdx.x + 1] = f[i] + dt * g[i];
-    if (threadIdx.x == 0) {
-        const long long l = base == 0 ? n - 1 : base - 1;
-        s_f1[0] = f[l] + dt * g[l];
-    }
-    if (threadIdx.x == kWaveThreads - 1 || i == n - 1) {
-        const long long r = i + 1 >= n ? 0 : i + 1;
-        s_f1[threadIdx.x + 2] = f[r] + dt * g[r];
-    }
-    __syncthreads();
-    double e = 0.0;
-    if (active) {
-        const T fm = s_f1[threadIdx.x], f1 = s_f1[threadIdx.x + 1], fp = s_f1[threadIdx.x + 2];
-        const T g1 = g[i] + k * (fp + fm - T(2) * f1);
-        fo[i] = f1;
-        go[i] = g1;
-        const double dfdx = ((double)fp - (double)fm) / (2.0 * dx);
-        const double gm = ((double)g[i] + (double)g1) / 2.0;
-        e = 0.5 * (c2 * dfdx * dfdx + gm * gm) * dx;
-    }
-    s_e[threadIdx.x] = e;
-    __syncthreads();
-    for (int w = kWaveThreads / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w) s_e[threadIdx.x] += s_e[threadIdx.x + w];
+    double acc = 0.0;  // this CTA's tiles, summed in tile order (thread 0)
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const long long base = tile * kWaveThreads;
+        const long long i = base + threadIdx.x;
+        const bool active = i < n;
+        // f1 on the tile and its two halo cells (periodic)
+        if (active) s_f1[threadIdx.x + 1] = f[i] + dt * g[i];
+        if (threadIdx.x == 0) {
+            const long long l = base == 0 ? n - 1 : base - 1;
+            s_f1[0] = f[l] + dt * g[l];
+        }
+        if (threadIdx.x == kWaveThreads - 1 || i == n - 1) {
+            const long long r = i + 1 >= n ? 0 : i + 1;
+            s_f1[threadIdx.x + 2] = f[r] + dt * g[r];
+        }
         __syncthreads();
+        double e = 0.0;
+        if (active) {
+            const T fm = s_f1[threadIdx.x], f1 = s_f1[threadIdx.x + 1], fp = s_f1[threadIdx.x + 2];
+            const T g1 = g[i] + k * (fp + fm - T(2) * f1);
+            fo[i] = f1;
+            go[i] = g1;
+            const double dfdx = ((double)fp - (double)fm) / (2.0 * dx);
+            const double gm = ((double)g[i] + (double)g1) / 2.0;
+            e = 0.5 * (c2 * dfdx * dfdx + gm * gm) * dx;
+        }
+        s_e[threadIdx.x] = e;
+        __syncthreads();
+        for (int w = kWaveThreads / 2; w > 0; w >>= 1) {
+            if (threadIdx.x < w) s_e[threadIdx.x] += s_e[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) acc += s_e[0];
+        __syncthreads();  // the next tile reuses s_f1 and s_e
     }
-    if (threadIdx.x == 0) partial[blockIdx.x] = s_e[0];
+    if (threadIdx.x == 0) partial[blockIdx.x] = acc;
 }
 
 __global__ void __launch_bounds__(kWaveThreads)
@@ -80,13 +86,17 @@ size_t align_up(size_t x) { return (x + 255) / 256 * 256; }
 
 struct WaveLayout {
     size_t f_off, g_off, part_off, e_off, total;
-    long long nblocks;
+    long long ntiles;   // tiles of kWaveThreads cells
+    long long nblocks;  // CTAs of the step kernel (each walks tiles b, b + nblocks, ...)
 };
 
 WaveLayout wave_layout(long long n, int prec, int n_steps) {
     WaveLayout L;
     const size_t esz = prec == HYDRO_F32 ? 4 : 8;
-    L.nblocks = (n + kWaveThreads - 1) / kWaveThreads;
+    L.ntiles = (n + kWaveThreads - 1) / kWaveThreads;
+    // enough CTAs to fill every SM several times; the energy partials stay few, so the final
+    // fixed-order sum of them is short
+    L.nblocks = L.ntiles < 152LL * 8 ? L.ntiles : 152LL * 8;
     L.f_off = 0;
     L.g_off = align_up((size_t)n * esz);
     L.part_off = L.g_off + align_up((size_t)n * esz);
@@ -105,8 +115,8 @@ int wave_run_t(long long n, double c, double length, double dt, T *f, T *g, int 
     const double dx = length / (double)n;
     const T k = T(c * c * dt / (dx * dx));
     for (int s = 0; s < n_steps; ++s) {
-        wave_step_kernel<T><<<(unsigned)L.nblocks, kWaveThreads, 0, st>>>(fa, ga, fb, gb, n, T(dt), k,
-                                                                          c * c, dx, part);
+        wave_step_kernel<T><<<(unsigned)L.nblocks, kWaveThreads, 0, st>>>(fa, ga, fb, gb, n, L.ntiles,
+                                                                          T(dt), k, c * c, dx, part);
         wave_energy_kernel<<<1, kWaveThreads, 0, st>>>(part, (int)L.nblocks, energy + s);
         T *t = fa;
         fa = fb;
