@@ -27,7 +27,7 @@ template <class T>
 __global__ void __launch_bounds__(kWaveThreads)
     wave_step_kernel(const T *__restrict__ f, const T *__restrict__ g, T *__restrict__ fo,
                      T *__restrict__ go, long long n, long long ntiles, T dt, T k, double c2,
-                     double dx, double *partial) {
+                     double dx, double inv_2dx, double *partial) {
     __shared__ T s_f1[kWaveThreads + 2];
     __shared__ double s_e[kWaveThreads];
     double acc = 0.0;  // this CTA's tiles, summed in tile order (thread 0)
@@ -52,8 +52,9 @@ __global__ void __launch_bounds__(kWaveThreads)
             const T g1 = g[i] + k * (fp + fm - T(2) * f1);
             fo[i] = f1;
             go[i] = g1;
-            const double dfdx = ((double)fp - (double)fm) / (2.0 * dx);
-            const double gm = ((double)g[i] + (double)g1) / 2.0;
+            // FP64 divisions are long instruction sequences: multiply by 1 / (2 dx) instead
+            const double dfdx = ((double)fp - (double)fm) * inv_2dx;
+            const double gm = ((double)g[i] + (double)g1) * 0.5;
             e = 0.5 * (c2 * dfdx * dfdx + gm * gm) * dx;
         }
         s_e[threadIdx.x] = e;
@@ -115,8 +116,8 @@ int wave_run_t(long long n, double c, double length, double dt, T *f, T *g, int 
     const double dx = length / (double)n;
     const T k = T(c * c * dt / (dx * dx));
     for (int s = 0; s < n_steps; ++s) {
-        wave_step_kernel<T><<<(unsigned)L.nblocks, kWaveThreads, 0, st>>>(fa, ga, fb, gb, n, L.ntiles,
-                                                                          T(dt), k, c * c, dx, part);
+        wave_step_kernel<T><<<(unsigned)L.nblocks, kWaveThreads, 0, st>>>(
+            fa, ga, fb, gb, n, L.ntiles, T(dt), k, c * c, dx, 1.0 / (2.0 * dx), part);
         wave_energy_kernel<<<1, kWaveThreads, 0, st>>>(part, (int)L.nblocks, energy + s);
         T *t = fa;
         fa = fb;
