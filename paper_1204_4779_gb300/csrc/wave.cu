@@ -57,13 +57,18 @@ __global__ void __launch_bounds__(kWaveThreads)
             const double gm = ((double)g[i] + (double)g1) * 0.5;
             e = 0.5 * (c2 * dfdx * dfdx + gm * gm) * dx;
         }
-        s_e[threadIdx.x] = e;
+        // fixed-order tree: a butterfly within each warp (lane 0's order), then the warp sums
+        // in warp order
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+        if ((threadIdx.x & 31) == 0) s_e[threadIdx.x >> 5] = e;
         __syncthreads();
-        for (int w = kWaveThreads / 2; w > 0; w >>= 1) {
-            if (threadIdx.x < w) s_e[threadIdx.x] += s_e[threadIdx.x + w];
-            __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+#pragma unroll
+            for (int w = 0; w < kWaveThreads / 32; ++w) t += s_e[w];
+            acc += t;
         }
-        if (threadIdx.x == 0) acc += s_e[0];
         __syncthreads();  // the next tile reuses s_f1 and s_e
     }
     if (threadIdx.x == 0) partial[blockIdx.x] = acc;
