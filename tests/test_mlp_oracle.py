@@ -64,3 +64,16 @@ def test_training_reduces_loss():
     for k in range(1, 301):
         p, m, v = M.adam_step(p, M.gradient(p, X, t, d, H), m, v, k, lr=1e-2)
     assert M.loss(p, X, t, d, H) < 0.2 * L0
+
+
+def test_adam_steps_with_a_constant_gradient_have_magnitude_lr():
+    """With the same gradient every step the bias-corrected moments are exactly g and g^2, so
+    every step (not only the first) moves each coordinate by lr (eps = 0)."""
+    p, X, t, d, H = _case(7)
+    g = M.gradient(p, X, t, d, H)
+    m = np.zeros_like(p)
+    v = np.zeros_like(p)
+    for k in range(1, 4):
+        p2, m, v = M.adam_step(p, g, m, v, k, lr=1e-2, eps=0.0)
+        assert np.allclose(np.abs(p2 - p)[g != 0], 1e-2, rtol=1e-10), k
+        p = p2
