@@ -76,6 +76,21 @@ def blast_3d(n: int = 512, radius_cells: float = 8.0, p_in: float = 10.0,
     return V
 
 
+def blast_3d_box(n: int, lo: int, m: int, radius_cells: float = 8.0, p_in: float = 10.0,
+                 p_out: float = 1e-3) -> np.ndarray:
+    """The cells [lo, lo + m) on every axis of the n^3 field of blast_3d, computed directly
+    (the same cell-centre coordinates, so the same values as slicing the full field)."""
+    c = (np.arange(lo, lo + m, dtype=np.float64) + 0.5) / n
+    z, y, x = np.meshgrid(c, c, c, indexing="ij")
+    h = 1.0 / n
+    r2 = (x - 0.5) ** 2 + (y - 0.5) ** 2 + (z - 0.5) ** 2
+    inside = r2 <= (radius_cells * h) ** 2
+    V = np.zeros((5, m, m, m))
+    V[0] = 1.0
+    V[4] = np.where(inside, p_in, p_out)
+    return V
+
+
 def smooth(shape_xyz, seed: int, rho=(0.5, 2.0), p=(0.5, 2.0), vmax: float = 0.2) -> np.ndarray:
     """Seeded smooth periodic data: each field is mid + amp * sin(2 pi (k . x) + phi) with
     integer wave numbers k in {1, 2}^dim and phi ~ U[0, 2pi).  rho and p stay inside the given

@@ -58,3 +58,45 @@ def max_rel_err(G, O):
 
 def l1_rel(g, o):
     return float(np.sum(np.abs(g - o)) / np.sum(np.abs(o)))
+
+
+def outer_layers_equal(U, bg, w):
+    """True if every cell within w cells of a face of the box holds exactly the values bg
+    (one value per field)."""
+    dim = U.ndim - 1
+    for ax in range(1, dim + 1):
+        for sl in (slice(0, w), slice(U.shape[ax] - w, U.shape[ax])):
+            idx = [slice(None)] * (dim + 1)
+            idx[ax] = sl
+            part = U[tuple(idx)]
+            if not np.all(part == bg.reshape((-1,) + (1,) * dim)):
+                return False
+    return True
+
+
+def blast_subbox_oracle(n, lo, m, steps, radius=8.0, gamma=1.4, cfl=0.4, threads=None):
+    """The oracle's result for the n^3 periodic blast after `steps` RK steps, restricted to the
+    cells [lo, lo + m)^3, computed on that sub-box alone (cell size 1/n, periodic wrap).
+
+    The wrap is exact while the disturbance stays away from the sub-box faces: if the four
+    outer cell layers hold the uniform background at the start of a step, stage 1 leaves the
+    two outer layers of U1 at the background (a uniform neighbourhood of two cells gives equal
+    fluxes), so every ghost cell of either stage reads background values, as on the full grid,
+    where everything outside the sub-box is still background; and dt, the maximum of the CFL
+    signal, is the same, because the background's signal is below the blast's.  The check is
+    made before every step and after the last one; a failure raises.  Returns (U, t)."""
+    from paper_1204_4779_gb300 import inputs
+    V = inputs.blast_3d_box(n, lo, m, radius)
+    U = oracle.prim_to_cons(V, gamma)
+    bg = U[:, 0, 0, 0].copy()
+    th = oracle.max_threads() if threads is None else threads
+    t = 0.0
+    for s in range(steps):
+        if not outer_layers_equal(U, bg, 4):
+            raise AssertionError(f"the disturbance reached the sub-box faces before step {s}")
+        U, t, done, _ = oracle.run(U, gamma, cfl, 1, bc=(0, 0, 0), t0=t, dr=[1.0 / n] * 3,
+                                   threads=th)
+        assert done == 1
+    if not outer_layers_equal(U, bg, 4):
+        raise AssertionError("the disturbance reached the sub-box faces")
+    return U, t

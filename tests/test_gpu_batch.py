@@ -143,7 +143,7 @@ def test_full_batched_config_fp32():
         worst = max(worst, e)
         assert e <= 1e-4, (g, shapes[g], e)
         assert abs(t[g] - to) <= 1e-5 * to
-    print(f"batched 4096 grids FP32: worst sampled L1(rho) rel = {worst:.3e}")
+    print(f"PARITY batched4096 fp32 worst_sampled_l1_rho={worst:.3e}")
 
 
 # ---- row tiles: a work item is a strip of x columns marching along y -----------------------
