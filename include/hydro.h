@@ -376,24 +376,31 @@ int hydro_mlp_train(float *params, float *m, float *v, int32_t d, int32_t hidden
 /* hydro_step for callers that cannot allocate device memory (no counterpart in the paper).
  *
  * Some callers cannot call cudaMalloc or give the library a workspace: code running inside
- * another runtime that owns every allocation (a framework with its own caching allocator,
- * or a stream capture in which allocating is forbidden), and embedded or real-time callers
- * that must not allocate after start-up.  This call takes the grid, gamma, bc, prec and cfl of
- * hydro_create plus the arguments of hydro_step, needs no context and no workspace, and
- * allocates nothing: the RK stage buffer U1 and the step control block live in one
- * file-scope device array of HYDRO_STATIC_SCRATCH_BYTES.  The caller still owns and passes the
- * state planes (device memory, layout as for hydro_step).  Default kernel variant, direct
- * launches (no graph).
+ * another runtime that owns every allocation (a framework with its own caching allocator),
+ * and embedded or real-time callers that must not allocate after start-up.  This call takes
+ * the grid, gamma, bc, prec and cfl of hydro_create plus the arguments of hydro_step, needs no
+ * context and no workspace, and allocates nothing: the RK stage buffer U1 and the step control
+ * block live in one file-scope device array of HYDRO_STATIC_SCRATCH_BYTES.  The caller still
+ * owns and passes the state planes (device memory on the caller's CURRENT device, where the
+ * call runs; layout as for hydro_step).
+ *   Kernels: one fixed variant, not hydro_create's tuned defaults: 32 x 8 tiles in 2D and 3D
+ *   (3D marching up to 64 planes), 128-cell rows in 1D, look-ahead staging, the two-CTA
+ *   register budget, the dt reduction fused into stage 2.  Direct launches (no graph): one
+ *   CFL pass, then 2 * n_steps stage kernels whatever t_end is (the stages after t_end return
+ *   at once, but each still costs a launch, so keep n_steps near the steps needed).
  *   Size limit: the control block (256 bytes) plus dim+2 planes of n[0]*n[1]*n[2] cells, each
  *   rounded up to 256 bytes, must fit in HYDRO_STATIC_SCRATCH_BYTES (for example a 1D grid of
  *   10^5 cells in FP64, or 59^3 cells in FP32); larger grids return HYDRO_EINVAL.
  *   Set-up: the first call on each device (that device current) looks up the array's device
  *   address with cudaGetSymbolAddress and sets kernel attributes; make that first call
  *   before any stream capture.
+ *   Time: *t_inout (NULL: 0) is read on the host when the call is made.  With t_inout or
+ *   steps_done non-NULL the call copies the control block back and synchronises the stream
+ *   (as hydro_step does); with both NULL it only enqueues work and returns.
  *   Sharing: every call uses the same array, which keeps the last call's contents; each call
  *   rewrites the control block before use.  Calls that overlap on the GPU race on the array:
  *   order them (one stream, or events).
- * Errors and synchronisation as for hydro_step (stream = cudaStream_t to issue on). */
+ * Errors as for hydro_step (stream = cudaStream_t to issue on). */
 int hydro_step_static(const hydro_grid_t *grid, double gamma, const int32_t bc[3], int32_t prec,
                       double cfl, const hydro_state_t *state, int32_t n_steps, double t_end,
                       double *t_inout, int32_t *steps_done, void *stream);

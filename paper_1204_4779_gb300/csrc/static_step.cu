@@ -2,17 +2,24 @@
 //
 // Some callers cannot call cudaMalloc or hand the library a workspace: code running inside
 // another runtime that owns every allocation (a host framework with its own caching
-// allocator, or a stream capture where allocating is forbidden), and small embedded or
-// real-time callers that must not allocate after start-up.  This entry point needs no
-// workspace: the RK stage buffer U1 and the step control block live in one file-scope
-// device array of fixed size, HYDRO_STATIC_SCRATCH_BYTES, which every GPU that loads the
-// library holds until the process exits.  The caller still passes the state planes.
+// allocator), and small embedded or real-time callers that must not allocate after start-up.
+// This entry point needs no workspace: the RK stage buffer U1 and the step control block live
+// in one file-scope device array of fixed size, HYDRO_STATIC_SCRATCH_BYTES, which every GPU
+// that loads the library holds until the process exits.  The caller still passes the state
+// planes, which must live on the caller's current device: the call runs there.
 //
 // Host code cannot use that array's name as a device address (in host code it names a host
 // stand-in), so the first call on each device, with that device current, looks the address
 // up once with cudaGetSymbolAddress and sets the stage kernels' shared-memory attributes;
 // later calls reuse it.  Because of that set-up, make the first call on a device before any
 // stream capture.
+//
+// The kernels are one fixed variant (not the tuned defaults of hydro_create): 32 x 8 tiles in
+// 2D and 3D (3D marching up to 64 planes), 128-cell rows in 1D, look-ahead staging, the
+// two-CTA register budget, the dt reduction fused into stage 2.  The call launches the CFL
+// pass and then 2 n_steps stage kernels whatever t_end is (stages after t_end return at
+// once), with no graph; it reads nothing back unless t_inout or steps_done asks for it, in
+// which case it copies the control block to the host and synchronises the stream.
 //
 // Every call shares the one array and it keeps the last call's contents: the control block
 // is rewritten at the start of each call and U1 is fully written by stage 1 before stage 2
@@ -100,6 +107,10 @@ extern "C" int hydro_step_static(const hydro_grid_t *grid, double gamma, const i
     L.march = dim == 3 ? (n[2] < 64 ? n[2] : 64) : 1;
     L.tile_x = dim == 1 ? 128 : 32;
     L.tile_y = dim == 1 ? 1 : 8;
+    // launch-grid limits of the stage kernels (y and z at most 65535 CTAs), checked here
+    // rather than left to the array's size cap
+    if (dim >= 2 && (n[1] + L.tile_y - 1) / L.tile_y > 65535) return HYDRO_EINVAL;
+    if (dim == 3 && (n[2] + L.march - 1) / L.march > 65535) return HYDRO_EINVAL;
     L.prefetch = 1;
     L.split = 0;
     L.occupancy = 2;

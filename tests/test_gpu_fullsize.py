@@ -2,8 +2,8 @@
 configuration bench.py times), checked through properties that hold at any size: the FP64
 totals are conserved on the periodic box, the state stays finite and positive, and the blast
 keeps the symmetries of its initial data (axis permutations and mirror images of the centred
-sphere).  Element-wise parity with the oracle is tested at sizes the oracle finishes quickly
-(test_gpu_parity.py); a 512^3 oracle run needs tens of minutes of CPU time."""
+sphere).  Element-wise parity with the oracle at this size is in test_gpu_config_parity.py
+(the oracle on the centred sub-box the disturbance stays in)."""
 import numpy as np
 import pytest
 
