@@ -174,9 +174,12 @@ def _cpu_model() -> str:
     return os.uname().machine
 
 
-def cpu_oracle_cups(budget_s: float = 12.0, n: int = 64, max_steps: int = 200, device=None):
+def cpu_oracle_cups(budget_s: float = 12.0, n: int = 256, max_steps: int = 200, device=None):
     """The FP64 CPU oracle as it stands, on a bounded sample of the workload: the same blast
-    at n^3 (radius 8 cells, periodic, CFL 0.4), all host cores, about `budget_s` of CPU work."""
+    at n^3 (radius 8 cells, periodic, CFL 0.4), all host cores, about `budget_s` of CPU work
+    after one untimed step.  At 256^3 the oracle's arrays (state, primitives, face states and
+    fluxes of every axis, about 520 bytes a cell) are 8.7 GB, far beyond the host's last-level
+    cache, as the 512^3 workload is."""
     import oracle
     from paper_1204_4779_gb300 import inputs
     U = oracle.prim_to_cons(inputs.blast_3d(n, radius_cells=RADIUS), GAMMA)
@@ -190,8 +193,10 @@ def cpu_oracle_cups(budget_s: float = 12.0, n: int = 64, max_steps: int = 200, d
     el = time.perf_counter() - t0
     out = {"value": n ** 3 * done / el, "unit": "cell-updates/s", "cores": threads,
            "kind": "oracle", "cpu_model": _cpu_model(),
-           "sample": f"{n}^3 blast (radius {RADIUS:g} cells), {done} FP64 RK steps, "
-                     f"{el:.1f} s, OpenMP threads={threads}, host={os.uname().machine}"}
+           "sample": f"{n}^3 blast (radius {RADIUS:g} cells), {done} FP64 RK steps after one "
+                     f"untimed step, {el:.1f} s, OpenMP threads={threads}, "
+                     f"host={os.uname().machine}; working set about {520 * n ** 3 / 1e9:.1f} GB "
+                     f"(beyond the last-level cache)"}
     if device is not None:
         out["gpu_error_vs_oracle"] = _gpu_error(n, 1 + done, Uo, device)
     return out
@@ -226,13 +231,14 @@ def _gpu_error(n, steps, Uo, device):
 
 def run_reference(args):
     """Reference arm: the FP64 CPU oracle on the host cores, each step one RK step of a bounded
-    64^3 sample of the blast workload."""
+    128^3 sample of the blast workload (about 1.1 GB of oracle arrays, beyond the host's
+    last-level cache)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     import oracle
     from paper_1204_4779_gb300 import inputs
-    n = 64
+    n = args.ref_size
     U = oracle.prim_to_cons(inputs.blast_3d(n, radius_cells=RADIUS), GAMMA)
     threads = oracle.max_threads()
     U, *_ = oracle.run(U, GAMMA, CFL, args.warmup, bc=(0, 0, 0), threads=threads)
@@ -667,6 +673,8 @@ def main():
     ap.add_argument("--dtype", choices=("f32", "f64"), default="f32",
                     help="precision of the kh2d and wave lines")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-size", type=int, default=128,
+                    help="cube side of the reference arm's per-step sample (the oracle on the host)")
     ap.add_argument("--fp64-steps", type=int, default=10,
                     help="timed FP64 steps of the same workload after the FP32 run (0: none)")
     ap.add_argument("--repeats", type=int, default=30,
