@@ -56,17 +56,6 @@ def _kernel_digest(sources=STAGE_SOURCES) -> str:
     return h.hexdigest()[:16]
 
 
-def _oracle_opcounts():
-    """Floating-point operations per cell-update of one RK step, as counted in the oracle's
-    evaluation of the benchmark's blast (profiles/oracle_opcounts.json, written by
-    oracle/count_ops.py); None if the file is missing."""
-    try:
-        with open(os.path.join(ROOT, "profiles", "oracle_opcounts.json")) as f:
-            return float(json.load(f)["per_cell_update"]["total"])
-    except Exception:
-        return None
-
-
 def _ncu_record(field: str, kernel: str, name: str = "ncu_counters.json", sources=STAGE_SOURCES):
     """Per-launch figure (`per_launch_bytes` or `per_launch_warp_instructions`) of `kernel` in
     the benchmark's workload from a committed ncu summary (profiles/<name>), if it was taken on
@@ -347,6 +336,7 @@ def run_ours(args):
     hbm, peak_kind = _peaks()
     nv = 5
     alg = {"stage1": 2 * nv * 4 * ncell, "stage2": 3 * nv * 4 * ncell}  # bytes per launch
+    step_bytes = alg["stage1"] + alg["stage2"]
     dom = max(("stage1", "stage2"), key=lambda k: kt[k][0])
     avg_ms = kt[dom][0] / max(kt[dom][1], 1)
     achieved = alg[dom] / (avg_ms * 1e-3) / 1e9
@@ -436,28 +426,21 @@ def run_ours(args):
         S64.close()
         del U64, S64
 
-    # FP32 roofline of the whole step: the oracle's counted operations per cell-update times
-    # the cell-updates per second, against the measured FMA rate (one operation per lane per
-    # instruction; divisions and square roots take several instructions on the GPU, so this
-    # bound is generous to the kernel)
+    # FP32 roofline of the whole step: the FP32 lane operations the two stage kernels execute
+    # per cell (FADD, FMUL, FFMA and the packed f32x2 forms counted twice, from the committed ncu
+    # capture of the current kernels) times the cell-updates per second, against the FMA rate
+    # measured live (one lane operation per lane per clock)
     fp32 = None
-    opc = _oracle_opcounts()
-    if opc is not None:
-        ach = opc * ncell * args.steps / (ms_max * 1e-3)
-        fp32 = {"bound": "alu", "scope": "whole RK step", "achieved": ach, "peak": fma32,
-                "unit": "FP32 lane-operations/s", "frac": ach / fma32,
-                "ops_per_cell_update": opc, "fma_rate_f64": fma64,
-                "source": "operations counted in the FP64 oracle's own evaluation of one RK step "
-                          "(profiles/oracle_opcounts.json); peak = hydro_fma_rate measured live"}
-
-    # the FP64 leg against the FP64 FMA rate, the same counted operations per cell-update (its
-    # divisions and square roots are correctly rounded, each many FP64 instructions, so this
-    # bound is generous too)
-    if fp64 is not None and opc is not None and fma64:
-        ach64 = opc * fp64["value"]
-        fp64["fp64_roofline"] = {"bound": "alu", "achieved": ach64, "peak": fma64,
-                                 "unit": "FP64 lane-operations/s", "frac": ach64 / fma64,
-                                 "ops_per_cell_update": opc}
+    lane = _ncu_record("fp32_lane_ops_per_cell", "stage1"), _ncu_record("fp32_lane_ops_per_cell", "stage2")
+    if None not in lane:
+        ops = lane[0] + lane[1]
+        ach = ops * ncell * args.steps / (ms_max * 1e-3)
+        fp32 = {"bound": "alu", "scope": "whole RK step (both stage kernels)", "achieved": ach,
+                "peak": fma32, "unit": "FP32 lane-operations/s", "frac": ach / fma32,
+                "ops_per_cell_update": ops, "fma_rate_f64": fma64,
+                "source": "ncu-counted FP32 add/multiply/FMA lane operations of the stage kernels "
+                          "per cell (profiles/ncu_counters.json fp32_lane_ops_per_cell, f32x2 "
+                          "counted twice); peak = hydro_fma_rate measured live"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -477,7 +460,10 @@ def run_ours(args):
                        "variant": variant},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": traffic, "kernel": dom,
-                         "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"},
+                         "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                         "step_frac": step_bytes / (ms_max / args.steps * 1e-3) / 1e9 / hbm,
+                         "step_frac_note": "the whole RK step time-weighted: 100 B per cell "
+                                           "(stage 1 40 B, stage 2 60 B) over the step time"},
             "kernels": kernels,
             "gpu_launches": int(sum(v[1] for v in kt.values())),
             "clocks": clocks,
@@ -538,7 +524,9 @@ def run_wave(args):
                        "l2": f"state {2 * esz * n / 2**20:.0f} MiB vs 129 MB L2; no flush",
                        "energy_drift": drift},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": None, "kernel": "wave_step_kernel",
+                         "frac": achieved / hbm, "traffic": None,
+                         "kernel": "wave_step_kernel" if f64 else "wave_step_kernel_f32",
+                         "scope": "whole call (step kernels and the per-step energy sums)",
                          "bytes_per_cell_update": 4 * esz,
                          "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"},
             "gpu_launches": 2 * steps, "clocks": clk.summary(), "e2e": None, "cpu_baseline": None}

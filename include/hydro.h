@@ -348,8 +348,9 @@ int hydro_wave_run(int32_t prec, int64_t n, double c, double length, double dt, 
  * are device memory owned by the caller: params (hydro_mlp_sizes' param_count floats, layout
  * W1 (H x d, row-major), b1, W2 (H x H), b2, W3 (1 x H), b3), Adam moments m and v (same
  * size), inputs X (n x d, row-major), targets t (n), and a workspace of workspace_bytes for
- * n samples.  Loss: mean squared error over the n samples.  Calls are ordered on `stream`
- * and do not synchronise.  Deterministic (fixed reduction order, no atomics). */
+ * n samples (1 <= n <= 65535 * 128, 1 <= d, H <= 4096; otherwise HYDRO_EINVAL).  Loss: mean
+ * squared error over the n samples.  Calls are ordered on `stream` and do not synchronise.
+ * Deterministic (fixed reduction order, no atomics). */
 int hydro_mlp_sizes(int32_t d, int32_t hidden, int64_t n, int64_t *param_count,
                     size_t *workspace_bytes);
 /* y_out[s] = network(X[s]) for s < n. */

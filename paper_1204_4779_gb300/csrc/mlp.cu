@@ -3,11 +3,12 @@
 //
 // The network is small (input ~30 features, width 64, a few thousand samples), so each
 // kernel gives one thread one output element and loops over the reduction index in a fixed
-// order: deterministic results, no atomics.
+// order: deterministic results, no atomics.  The weight gradients sum over the samples in two
+// fixed-order levels: chunks of kChunk samples in parallel, then the chunk partials in order.
 //
 // Flat parameter layout: W1 (H x d, row-major), b1 (H), W2 (H x H), b2 (H), W3 (1 x H), b3 (1).
 // Workspace for n samples (floats): h1 (n H), h2 (n H), y (n), dy (n), dz2 (n H), dz1 (n H),
-// grad (P), loss (1).
+// grad (P), loss (1), the weight-gradient chunk partials (ceil(n / kChunk) x H x (max(d, H) + 1)).
 #include <math.h>
 #include <string.h>
 
@@ -17,9 +18,10 @@
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kChunk = 128;  // samples per partial sum of the weight gradients
 
 struct Sizes {
-    long long P, h1, h2, y, dy, dz2, dz1, grad, loss, total;  // float offsets / count
+    long long P, h1, h2, y, dy, dz2, dz1, grad, loss, part, total;  // float offsets / count
 };
 
 Sizes sizes(int d, int H, long long n) {
@@ -34,6 +36,7 @@ Sizes sizes(int d, int H, long long n) {
     S.dz1 = o; o += n * H;
     S.grad = o; o += S.P;
     S.loss = o; o += 1;
+    S.part = o; o += (n + kChunk - 1) / kChunk * (long long)H * ((d > H ? d : H) + 1);
     S.total = o;
     return S;
 }
@@ -85,22 +88,41 @@ __global__ void __launch_bounds__(kThreads) dense_backward(const float *delta, i
     dz[idx] = acc * (1.0f - hv * hv);
 }
 
-// gW[j][i] = sum_s delta[s][j] in[s][i]; gb[j] = sum_s delta[s][j]  (thread (j, i), i = din: gb)
-__global__ void __launch_bounds__(kThreads) dense_wgrad(const float *delta, int dout,
-                                                        const float *in, int din, long long n,
-                                                        float *gW, float *gb) {
+// Chunk partials of the weight gradient: part[c][j][i] = sum over samples s of chunk c of
+// delta[s][j] in[s][i] (i = din: delta[s][j] alone, the bias), s in increasing order.
+__global__ void __launch_bounds__(kThreads) dense_wgrad_part(const float *delta, int dout,
+                                                             const float *in, int din, long long n,
+                                                             float *part) {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (long long)dout * (din + 1)) return;
+    const long long per = (long long)dout * (din + 1);
+    if (idx >= per) return;
     const int j = (int)(idx / (din + 1));
     const int i = (int)(idx % (din + 1));
+    const long long s0 = (long long)blockIdx.y * kChunk;
+    const long long s1 = s0 + kChunk < n ? s0 + kChunk : n;
     float acc = 0.0f;
     if (i < din) {
-        for (long long s = 0; s < n; ++s) acc = fmaf(delta[s * dout + j], in[s * din + i], acc);
-        gW[(long long)j * din + i] = acc;
+        for (long long s = s0; s < s1; ++s) acc = fmaf(delta[s * dout + j], in[s * din + i], acc);
     } else {
-        for (long long s = 0; s < n; ++s) acc += delta[s * dout + j];
-        gb[j] = acc;
+        for (long long s = s0; s < s1; ++s) acc += delta[s * dout + j];
     }
+    part[blockIdx.y * per + idx] = acc;
+}
+
+// gW[j][i] = sum_c part[c][j][i] in chunk order; gb[j] = the same for i = din
+__global__ void __launch_bounds__(kThreads) dense_wgrad_sum(const float *part, int dout, int din,
+                                                            int nchunks, float *gW, float *gb) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long per = (long long)dout * (din + 1);
+    if (idx >= per) return;
+    float acc = 0.0f;
+    for (int c = 0; c < nchunks; ++c) acc += part[c * per + idx];
+    const int j = (int)(idx / (din + 1));
+    const int i = (int)(idx % (din + 1));
+    if (i < din)
+        gW[(long long)j * din + i] = acc;
+    else
+        gb[j] = acc;
 }
 
 __global__ void __launch_bounds__(kThreads) adam_kernel(float *p, float *m, float *v, const float *g,
@@ -117,6 +139,16 @@ __global__ void __launch_bounds__(kThreads) adam_kernel(float *p, float *m, floa
 }
 
 unsigned blocks(long long work) { return (unsigned)((work + kThreads - 1) / kThreads); }
+
+// gW, gb of a dense layer (delta: n x dout, in: n x din) through the chunk partials
+void dense_wgrad(const float *delta, int dout, const float *in, int din, long long n, float *part,
+                 float *gW, float *gb, cudaStream_t st) {
+    const int nchunks = (int)((n + kChunk - 1) / kChunk);
+    const long long per = (long long)dout * (din + 1);
+    dense_wgrad_part<<<dim3(blocks(per), (unsigned)nchunks), kThreads, 0, st>>>(delta, dout, in,
+                                                                                din, n, part);
+    dense_wgrad_sum<<<blocks(per), kThreads, 0, st>>>(part, dout, din, nchunks, gW, gb);
+}
 
 cudaError_t forward_all(const float *p, int d, int H, const float *X, long long n, float *ws,
                         const Sizes &S, cudaStream_t st) {
@@ -138,15 +170,18 @@ cudaError_t gradient_all(const float *p, int d, int H, const float *X, const flo
     float *gW3 = gb2 + H, *gb3 = gW3 + H;
     mse_kernel<<<1, kThreads, 0, st>>>(ws + S.y, t, n, ws + S.dy, ws + S.loss);
     // output layer (linear): delta = dy
-    dense_wgrad<<<blocks((long long)1 * (H + 1)), kThreads, 0, st>>>(ws + S.dy, 1, ws + S.h2, H, n, gW3, gb3);
+    float *part = ws + S.part;
+    dense_wgrad(ws + S.dy, 1, ws + S.h2, H, n, part, gW3, gb3, st);
     dense_backward<<<blocks(n * H), kThreads, 0, st>>>(ws + S.dy, 1, W3, ws + S.h2, H, n, ws + S.dz2);
-    dense_wgrad<<<blocks((long long)H * (H + 1)), kThreads, 0, st>>>(ws + S.dz2, H, ws + S.h1, H, n, gW2, gb2);
+    dense_wgrad(ws + S.dz2, H, ws + S.h1, H, n, part, gW2, gb2, st);
     dense_backward<<<blocks(n * H), kThreads, 0, st>>>(ws + S.dz2, H, W2, ws + S.h1, H, n, ws + S.dz1);
-    dense_wgrad<<<blocks((long long)H * (d + 1)), kThreads, 0, st>>>(ws + S.dz1, H, X, d, n, gW1, gb1);
+    dense_wgrad(ws + S.dz1, H, X, d, n, part, gW1, gb1, st);
     return cudaGetLastError();
 }
 
-bool dims_ok(int d, int H, long long n) { return d >= 1 && d <= 4096 && H >= 1 && H <= 4096 && n >= 1; }
+bool dims_ok(int d, int H, long long n) {
+    return d >= 1 && d <= 4096 && H >= 1 && H <= 4096 && n >= 1 && n <= 65535LL * kChunk;
+}
 
 }  // namespace
 

@@ -4,16 +4,31 @@
 //     g1[i] = g[i] + (c^2 dt / dx^2) (f1[i+1] + f1[i-1] - 2 f1[i]),
 // with the discrete energy
 //     E = sum_i (1/2) (c^2 ((f1[i+1] - f1[i-1]) / (2 dx))^2 + ((g[i] + g1[i]) / 2)^2) dx
-// audited in FP64 after every step (the form of the paper's listing, which the scheme conserves
-// to round-off).
+// audited after every step (the form of the paper's listing, which the scheme conserves to
+// round-off).
 //
-// One launch per step: a CTA walks tiles of cells (tile b, b + G, ... for G CTAs), recomputes f1
-// on each tile plus one halo cell each side from f and g (no second pass over f1), updates g,
-// and reduces the tile's energy terms with a fixed tree, summing its tiles in order into one
-// FP64 partial; a one-CTA kernel sums the G partials in fixed order.
-// State ping-pongs between the caller's arrays and two workspace arrays.  FP64 is compiled with
-// --fmad=false (plain IEEE operations in the order of the formulas); FP32 runs the stencil in
-// FP32 and the energy in FP64.
+// One launch per step: a CTA walks tiles of cells (tile b, b + G, ... for G CTAs); a one-CTA
+// kernel sums the G energy partials in fixed order.  State ping-pongs between the caller's
+// arrays and two workspace arrays.  The translation unit is compiled with --fmad=false: every
+// product and sum of the update formulas is its own IEEE operation, in the formulas' order.
+//
+// FP64: a tile's f1 (plus one halo cell each side) goes through shared memory; each cell's
+// energy term is evaluated in FP64 (the centred difference multiplied by a precomputed
+// 1 / (2 dx) rather than divided by 2 dx, which changes its rounding by at most an ulp, well
+// inside the 1e-13 relative agreement the tests require with the oracle's division), the tile's
+// terms reduced by a fixed tree and summed in tile order into the CTA's partial.
+//
+// FP32: the stencil runs in FP32 and the energy keeps FP64 accuracy without per-cell FP64
+// arithmetic (GB300's FP64 pipe runs at 1/62 of the FP32 rate).  Each cell recomputes f1 at
+// i-1, i, i+1 from f and g (one FP32 operation each, the neighbours' loads hitting cache), so
+// the tile loop has no barrier.  With D = f1[i+1] - f1[i-1] and G = g[i] + g1[i], the energy is
+// K1 sum D^2 + K2 sum G^2, K1 = c^2 dx / (8 dx^2), K2 = dx / 8.  D and G are formed exactly as
+// FP32 pairs (hi + lo) by Knuth's TwoSum, their squares as pairs by the FMA form of Dekker's
+// TwoProduct (dropping lo^2, 2^-48 of the square), and each thread adds them to two running
+// double-float sums (TwoSum of the high parts, the low parts added, renormalised; Dekker's and
+// Knuth's algorithms as used in double-double arithmetic).  Once per CTA the running sums go to
+// FP64, are scaled by K1 and K2 and reduced by the same fixed tree.  The result agrees with an
+// FP64 evaluation of the FP32 state's energy to about 2^-48 times the cells a thread visits.
 #include <string.h>
 
 #include "../../include/hydro.h"
@@ -22,6 +37,72 @@
 namespace {
 
 constexpr int kWaveThreads = 256;
+
+// ---- double-float (pairs of FP32 values hi + lo) building blocks --------------------------
+
+struct DF {
+    float hi, lo;
+};
+// a + b exactly as hi + lo (Knuth's TwoSum, six operations, any magnitudes)
+__device__ __forceinline__ DF two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    const float e = (a - (s - bb)) + (b - bb);
+    return {s, e};
+}
+// (hi + lo)^2 as a pair: hi^2 exactly by TwoProduct with an FMA, plus 2 hi lo (lo^2 dropped)
+__device__ __forceinline__ DF square(DF x) {
+    const float p = x.hi * x.hi;
+    float e = fmaf(x.hi, x.hi, -p);
+    e = fmaf(x.hi + x.hi, x.lo, e);
+    return {p, e};
+}
+// running sum s += x: TwoSum of the high parts, low parts added, then renormalised so that
+// |lo| <= ulp(hi) / 2 (Fast2Sum)
+__device__ __forceinline__ void acc_add(DF &s, DF x) {
+    const DF t = two_sum(s.hi, x.hi);
+    const float e = t.lo + (s.lo + x.lo);
+    const float h = t.hi + e;
+    s.lo = e - (h - t.hi);
+    s.hi = h;
+}
+
+// FP32 step with the double-float energy audit (see the file comment).  k1, k2: K1 and K2.
+__global__ void __launch_bounds__(kWaveThreads)
+    wave_step_kernel_f32(const float *__restrict__ f, const float *__restrict__ g,
+                         float *__restrict__ fo, float *__restrict__ go, long long n,
+                         long long ntiles, float dt, float k, double k1, double k2,
+                         double *partial) {
+    __shared__ double s_e[kWaveThreads / 32];
+    DF sd = {0.0f, 0.0f}, sg = {0.0f, 0.0f};  // this thread's sums of D^2 and G^2, cell order
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const long long i = tile * kWaveThreads + threadIdx.x;
+        if (i >= n) continue;
+        const long long l = i == 0 ? n - 1 : i - 1;
+        const long long r = i == n - 1 ? 0 : i + 1;
+        const float gi = g[i];
+        const float fm = f[l] + dt * g[l];
+        const float f1 = f[i] + dt * gi;
+        const float fp = f[r] + dt * g[r];
+        const float g1 = gi + k * (fp + fm - 2.0f * f1);
+        fo[i] = f1;
+        go[i] = g1;
+        acc_add(sd, square(two_sum(fp, -fm)));
+        acc_add(sg, square(two_sum(gi, g1)));
+    }
+    double e = k1 * ((double)sd.hi + (double)sd.lo) + k2 * ((double)sg.hi + (double)sg.lo);
+    // fixed-order tree: a butterfly within each warp, then the warp sums in warp order
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+    if ((threadIdx.x & 31) == 0) s_e[threadIdx.x >> 5] = e;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < kWaveThreads / 32; ++w) t += s_e[w];
+        partial[blockIdx.x] = t;
+    }
+}
 
 template <class T>
 __global__ void __launch_bounds__(kWaveThreads)
@@ -120,9 +201,15 @@ int wave_run_t(long long n, double c, double length, double dt, T *f, T *g, int 
     double *energy = reinterpret_cast<double *>(ws + L.e_off);
     const double dx = length / (double)n;
     const T k = T(c * c * dt / (dx * dx));
+    // the FP32 energy's factors: (1/2) c^2 (D / (2 dx))^2 dx = K1 D^2, (1/2) (G / 2)^2 dx = K2 G^2
+    const double k1 = c * c * dx / (8.0 * dx * dx), k2 = dx / 8.0;
     for (int s = 0; s < n_steps; ++s) {
-        wave_step_kernel<T><<<(unsigned)L.nblocks, kWaveThreads, 0, st>>>(
-            fa, ga, fb, gb, n, L.ntiles, T(dt), k, c * c, dx, 1.0 / (2.0 * dx), part);
+        if constexpr (sizeof(T) == 4)
+            wave_step_kernel_f32<<<(unsigned)L.nblocks, kWaveThreads, 0, st>>>(
+                fa, ga, fb, gb, n, L.ntiles, T(dt), k, k1, k2, part);
+        else
+            wave_step_kernel<T><<<(unsigned)L.nblocks, kWaveThreads, 0, st>>>(
+                fa, ga, fb, gb, n, L.ntiles, T(dt), k, c * c, dx, 1.0 / (2.0 * dx), part);
         wave_energy_kernel<<<1, kWaveThreads, 0, st>>>(part, (int)L.nblocks, energy + s);
         T *t = fa;
         fa = fb;
