@@ -365,14 +365,14 @@ def time_to_best(done, t_marks):
 
 
 def evolve(space, evaluate, rng, budget_evals=None, budget_seconds=None, initial=None, db=None,
-           marks=None):
+           marks=None, clock=time.perf_counter):
     """Plain evolutionary search; returns (best Record, list of Records, seconds spent).
-    `marks`, if a list, receives the wall-clock after each benchmark."""
+    `marks`, if a list, receives the wall-clock after each benchmark; `clock` reads it."""
     ev = Evolution(space, rng)
-    done, t0 = [], time.perf_counter()
+    done, t0 = [], clock()
     queue = list(initial or [space.default_genome()])
     while True:
-        spent = time.perf_counter() - t0
+        spent = clock() - t0
         if _over_budget(done, spent, budget_evals, budget_seconds):
             break
         g = queue.pop(0) if queue else ev.birth()
@@ -384,11 +384,11 @@ def evolve(space, evaluate, rng, budget_evals=None, budget_seconds=None, initial
         ev.add(r)
         done.append(r)
         if marks is not None:
-            marks.append(time.perf_counter() - t0)
+            marks.append(clock() - t0)
         if db is not None:
             db.add(r)
     best = max(done, key=lambda r: r.mu)
-    return best, done, time.perf_counter() - t0
+    return best, done, clock() - t0
 
 
 # ------------------------------------------------------------ learned cost model ----------
@@ -432,30 +432,39 @@ def spearman(a, b) -> float:
 
 def model_guided(space, shape, evaluate, model: CostModel, records, rng, budget_evals=None,
                  budget_seconds=None, retrain_every: int = 4, min_records: int = 20, db=None,
-                 pretrained: bool = False, marks=None):
+                 pretrained: bool = False, marks=None, clock=time.perf_counter):
     """Benchmark candidates in the order of the model's predicted time, retraining on the
     records as they arrive; evolutionary births when the model has too few records.
     `pretrained`: the model was already fitted on `records` (offline, before the target was
     known); otherwise the first fit counts against the budget.
     Returns (best Record, list of Records, seconds spent including any training)."""
-    t0 = time.perf_counter()
+    t0 = clock()
     pool = list(records)
     ev = Evolution(space, rng)
     done = []
     cands = space.all_genomes()
     Xc = np.array([features(space, g, shape) for g in cands])
     trained = pretrained
+    per_epoch = None  # measured seconds per training epoch
     while True:
-        spent = time.perf_counter() - t0
+        spent = clock() - t0
         if _over_budget(done, spent, budget_evals, budget_seconds):
             break
-        if not trained or (len(done) % retrain_every == 0 and len(done) > 0):
+        retrain = trained and len(done) > 0 and len(done) % retrain_every == 0
+        if retrain and budget_seconds is not None and per_epoch is not None:
+            # skip a retraining that would leave no time for the next benchmark
+            epochs = max(100, model.epochs // 4)
+            if spent + per_epoch * epochs + np.mean([r.seconds for r in done]) > budget_seconds:
+                retrain = False
+        if not trained or retrain:
             X, y = training_set(pool)
             if len(y) >= min_records:
-                model.fit(X, y, epochs=None if not trained else max(100, model.epochs // 4),
-                          warm=trained)
+                epochs = model.epochs if not trained else max(100, model.epochs // 4)
+                t1 = clock()
+                model.fit(X, y, epochs=epochs, warm=trained)
+                per_epoch = (clock() - t1) / epochs
                 trained = True
-            if _over_budget(done, time.perf_counter() - t0, budget_evals, budget_seconds):
+            if _over_budget(done, clock() - t0, budget_evals, budget_seconds):
                 break
         if trained:
             pred = model.predict(Xc)
@@ -470,11 +479,14 @@ def model_guided(space, shape, evaluate, model: CostModel, records, rng, budget_
         done.append(r)
         pool.append(r)
         if marks is not None:
-            marks.append(time.perf_counter() - t0)
+            marks.append(clock() - t0)
         if db is not None:
             db.add(r)
+    if not done:  # the budget ran out during the first training: nothing benchmarked
+        best = Record(space.dim, tuple(shape), tuple(space.default_genome()), 0.0, 0.0, False, 0.0)
+        return best, [best], clock() - t0
     best = max(done, key=lambda r: r.mu)
-    return best, done, time.perf_counter() - t0
+    return best, done, clock() - t0
 
 
 def gpu_mlp_factory(hidden: int = 64, seed: int = 0):
@@ -562,6 +574,69 @@ def compare(db: DB, target, ga_evals: int, rng_seed: int, reps: int = 10, steps:
     return out
 
 
+def study(db: DB, target, seeds: int, ga_evals: int, reps: int = 10, steps: int = 2,
+          hidden: int = 64, frac: float = 0.25, log=print, bench=None, mlp_factory=None,
+          clock=time.perf_counter):
+    """Several seeds of three searches on `target`:
+
+      plain_W      the plain evolutionary search with `ga_evals` benchmarks; its wall-clock
+                   is that seed's W;
+      plain_frac   the plain search with frac * W of wall-clock;
+      model_frac   the model-guided search with frac * W of wall-clock, its clock INCLUDING
+                   training the cost model from scratch (on the other grids' records, before
+                   its first benchmark) and every retraining.
+
+    Every search starts from the same seeded random variant.  A seed's model search 'matches'
+    when its best is within sigma_W + sigma of the plain_W best.  Returns per-seed records and,
+    per arm, the mean and standard deviation of the best rate and of the time to best.
+    `bench` (an evaluator with a .space), `mlp_factory(seed)` and `clock` replace the GPU
+    benchmark, the GPU MLP and the wall-clock (tests)."""
+    bench = bench if bench is not None else Benchmark(target, reps=reps, steps=steps)
+    mlp_factory = mlp_factory or (lambda seed: gpu_mlp_factory(hidden, seed=seed))
+    space = bench.space
+    others = [r for r in db.records if tuple(r.shape) != tuple(target)]
+    runs = []
+    for s in range(seeds):
+        start = [space.random_genome(np.random.default_rng(1000 + s))]
+        mk = []
+        ga_best, ga_done, W = evolve(space, bench, np.random.default_rng(s), budget_evals=ga_evals,
+                                     marks=mk, initial=start, clock=clock)
+        rec = {"seed": s, "W": W,
+               "plain_W": {"evals": len(ga_done), "seconds": W, "best": ga_best.mu,
+                           "sigma": ga_best.sigma, "time_to_best": time_to_best(ga_done, mk),
+                           "variant": space.variant(ga_best.genome)}}
+        mk = []
+        nb, nd, ns = evolve(space, bench, np.random.default_rng(10_000 + s),
+                            budget_seconds=frac * W, marks=mk, initial=start, clock=clock)
+        rec["plain_frac"] = {"evals": len(nd), "seconds": ns, "best": nb.mu, "sigma": nb.sigma,
+                             "time_to_best": time_to_best(nd, mk),
+                             "variant": space.variant(nb.genome)}
+        mk = []
+        cm = CostModel(mlp_factory(s))
+        mb, md, ms = model_guided(space, target, bench, cm, others, np.random.default_rng(s),
+                                  budget_seconds=frac * W, pretrained=False, marks=mk,
+                                  clock=clock)
+        rec["model_frac"] = {"evals": len(md), "seconds": ms, "best": mb.mu, "sigma": mb.sigma,
+                             "time_to_best": time_to_best(md, mk),
+                             "variant": space.variant(mb.genome),
+                             "matches_plain_W": bool(mb.mu >= ga_best.mu - (ga_best.sigma + mb.sigma))}
+        runs.append(rec)
+        log(f"{target} seed {s}: W {W:.2f} s  plain_W {ga_best.mu / 1e9:.3f} G  "
+            f"plain_frac {nb.mu / 1e9:.3f} G  model_frac {mb.mu / 1e9:.3f} G "
+            f"({len(md)} benchmarks, {ms:.2f} s)")
+    summary = {}
+    for arm in ("plain_W", "plain_frac", "model_frac"):
+        b = np.array([r[arm]["best"] for r in runs])
+        t = np.array([r[arm]["time_to_best"] for r in runs])
+        summary[arm] = {"best_mean": float(b.mean()), "best_sd": float(b.std(ddof=1)) if len(b) > 1 else 0.0,
+                        "ttb_mean": float(t.mean()), "ttb_sd": float(t.std(ddof=1)) if len(t) > 1 else 0.0}
+    summary["model_matches"] = int(sum(r["model_frac"]["matches_plain_W"] for r in runs))
+    summary["seeds"] = len(runs)
+    summary["W_mean"] = float(np.mean([r["W"] for r in runs]))
+    return {"target": list(target), "frac": frac, "ga_evals": ga_evals, "reps": reps,
+            "steps": steps, "records_used": len(others), "summary": summary, "runs": runs}
+
+
 BATCH_VARIANTS = ([((32, 8), 0), ((16, 16), 0)] +
                   [(t, m) for t in ((32, 1), (64, 1), (128, 1)) for m in (8, 16, 32, 64)])
 
@@ -610,7 +685,7 @@ def sweep(shape, reps: int = 5, steps: int = 20):
 def main(argv=None):
     import argparse
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
-    ap.add_argument("command", choices=("collect", "compare", "sweep"))
+    ap.add_argument("command", choices=("collect", "compare", "study", "sweep"))
     ap.add_argument("--db", default=None)
     ap.add_argument("--shape", type=int, nargs="+", default=None,
                     help="sweep: the grid (nx [ny [nz]]); omitted: the batched configuration")
@@ -620,6 +695,7 @@ def main(argv=None):
     ap.add_argument("--reps", type=int, default=10)
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--out", default=None)
+    ap.add_argument("--seeds", type=int, default=5, help="study: seeds per target")
     a = ap.parse_args(argv)
     if a.command == "sweep":
         res = sweep(tuple(a.shape), a.reps, a.steps) if a.shape else sweep_batched(a.reps, a.steps)
@@ -634,6 +710,14 @@ def main(argv=None):
     db = DB(a.db)
     if a.command == "collect":
         collect(db, TRAIN_SHAPES, a.per_shape, np.random.default_rng(a.seed), a.reps, a.steps)
+        return
+    if a.command == "study":
+        results = [study(db, t, a.seeds, a.ga_evals, a.reps, a.steps) for t in TARGETS]
+        text = json.dumps({"records_in_db": len(db.records), "results": results}, indent=1)
+        print(text)
+        if a.out:
+            with open(a.out, "w") as f:
+                f.write(text + "\n")
         return
     results = [compare(db, t, a.ga_evals, a.seed, a.reps, a.steps) for t in TARGETS]
     text = json.dumps({"records_in_db": len(db.records), "results": results}, indent=1)

@@ -168,3 +168,59 @@ def test_model_guided_search_gains_over_search_without_the_model():
         plain_best.append(b2.mu / truth)
     assert min(model_best) >= 0.97
     assert np.mean(model_best) > np.mean(plain_best)
+
+
+class _VirtualClock:
+    """Simulated wall-clock: each benchmark costs 0.1 s and the model's training 0.3 s per 800
+    epochs."""
+
+    def __init__(self):
+        self.t = 0.0
+
+    def __call__(self):
+        return self.t
+
+
+def test_study_arms_budgets_and_summary():
+    """The multi-seed study on a synthetic landscape with a simulated clock: per seed the plain
+    search's W, the plain and model-guided searches within a quarter of it (the model's training
+    counted in its clock), and the per-arm means."""
+    space = T.Space(3)
+    clock = _VirtualClock()
+    db = T.DB(None)
+    rng = np.random.default_rng(7)
+    for sh in [(n, n, n) for n in (32, 64, 96, 160, 256)]:
+        ev = _evaluator(space, sh, 11)
+        for g in rng.permutation(len(space.all_genomes()))[:60]:
+            db.add(ev(space.all_genomes()[g]))
+    target = (512, 512, 512)
+    base = _evaluator(space, target, 5)
+
+    class Bench:
+        def __init__(self):
+            self.space = space
+
+        def __call__(self, g):
+            clock.t += 0.1
+            return base(g)
+
+    class TimedMLP(NumpyMLP):
+        def train(self, X, t, epochs, lr):
+            clock.t += 0.3 * epochs / 800
+            return super().train(X, t, min(epochs, 200), lr)
+
+    out = T.study(db, target, seeds=3, ga_evals=60, bench=Bench(),
+                  mlp_factory=lambda s: (lambda d: TimedMLP(d, 16, s)), clock=clock,
+                  log=lambda *_: None)
+    assert out["summary"]["seeds"] == 3 and len(out["runs"]) == 3
+    for r in out["runs"]:
+        assert r["plain_W"]["evals"] == 60 and abs(r["W"] - 6.0) < 1e-9
+        for arm in ("plain_frac", "model_frac"):
+            assert r[arm]["seconds"] <= 0.25 * r["W"] + 1e-9, (arm, r[arm]["seconds"])
+        # the model arm paid for its training: fewer benchmarks than the plain one
+        assert r["model_frac"]["evals"] < r["plain_frac"]["evals"]
+    s = out["summary"]
+    for arm in ("plain_W", "plain_frac", "model_frac"):
+        assert s[arm]["best_mean"] > 0 and s[arm]["best_sd"] >= 0
+    truth = max(synthetic_cups(space, g, target) for g in space.all_genomes())
+    assert s["model_frac"]["best_mean"] >= 0.97 * truth
