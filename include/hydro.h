@@ -50,10 +50,11 @@ enum {
                              workspace too small or misaligned */
     HYDRO_ECUDA = 2,      /* a CUDA runtime call failed (hydro_last_cuda_error tells which) */
     HYDRO_ENONFINITE = 3, /* non-finite value, rho <= 0 or p <= 0 seen on the device */
-    HYDRO_ETIMEOUT = 4,   /* reserved for a bounded device-side wait that gives up; no kernel
-                             of this library waits on another CTA (the dt reductions use a
-                             last-CTA counter or per-item slots and a finaliser kernel), so
-                             no call returns it */
+    HYDRO_ETIMEOUT = 4,   /* a bounded device-side wait gave up: a TMA-staged stage kernel
+                             (variant staging 3) did not see its plane's copy complete on its
+                             mbarrier within the bound; the step's result is void.  No kernel
+                             waits on another CTA (the dt reductions use a last-CTA counter or
+                             per-item slots and a finaliser kernel) */
     HYDRO_EUNSUPPORTED = 5 /* valid request that this build has no kernel for */
 };
 
@@ -101,7 +102,13 @@ typedef struct {
  *                   the next dt reduced in the epilogue of stage 2 (fused).
  *   staging:        staging depth, marching tiles only.  0 = default (1); 1 = the next
  *                   plane's loads are issued one plane ahead of their use; 2 = each plane is
- *                   loaded when it is staged (no look-ahead, fewer registers).
+ *                   loaded when it is staged (no look-ahead, fewer registers); 3 = the planes
+ *                   of the stage's input come into shared memory by TMA (bulk tensor copies of
+ *                   the tile plus its halo, completion on an mbarrier, two planes in flight;
+ *                   dim 3 FP32, tile 16 x 8, nothing stored between a stage's parts).  Grids
+ *                   whose x extent is not a multiple of 4, or planes not 16-byte aligned, run
+ *                   the staging-1 kernels instead.  A TMA wait that does not complete within
+ *                   its bound makes the call return HYDRO_ETIMEOUT.
  *   occupancy:      FP32 marching tiles only: resident 256-thread CTAs' worth of warps per SM
  *                   the register budget of the stage kernels targets.  0 = library default
  *                   (3 for the default FP32 marching tiles, else 2); 2 (about 128 registers a
@@ -365,7 +372,9 @@ int hydro_mlp_gradient(const float *params, int32_t d, int32_t hidden, const flo
 int hydro_mlp_adam(float *params, float *m, float *v, const float *grad, int64_t count,
                    int32_t step, float lr, float beta1, float beta2, float eps, void *stream);
 /* `epochs` full-batch Adam steps (numbered step0+1 ...); loss_out[k] (device, may be NULL)
- * receives the loss before step k. */
+ * receives the loss before step k.  The step number is kept in the workspace and advanced on
+ * the device, so the epochs are captured once into a CUDA graph (on a private stream) and
+ * replayed on `stream`; the Adam bias corrections are computed on the device. */
 int hydro_mlp_train(float *params, float *m, float *v, int32_t d, int32_t hidden, const float *X,
                     const float *t, int64_t n, int32_t epochs, int32_t step0, float lr,
                     void *workspace, float *loss_out, void *stream);

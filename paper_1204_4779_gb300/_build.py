@@ -39,9 +39,10 @@ UNITS = {
     "diag.cu": [],
     "analytic.cu": ["--fmad=false"],
     "exchange.cu": [],
+    "tma_host.cu": [],
 }
 HEADERS = ["hydro_device.cuh", "stage_kernel.cuh", "stage_launch.cuh", "hydro_internal.h",
-           "batch_kernel.cuh"]
+           "batch_kernel.cuh", "tma.cuh"]
 
 
 def nvcc() -> str:

@@ -125,6 +125,22 @@ int tile_compiled_manifest(int prec, int dim, int bx, int by) {
     return 0;
 }
 
+// Status code of a control block's status bits: a timed-out device wait first (the step's
+// result is void), then a non-finite or non-positive state.
+int status_code(unsigned int status) {
+    if (status & hydro::STATUS_TIMEOUT) return HYDRO_ETIMEOUT;
+    return (status & hydro::STATUS_NONFINITE) ? HYDRO_ENONFINITE : HYDRO_OK;
+}
+
+// 1 if the tile is also compiled with TMA plane staging.
+int tile_compiled_tma(int prec, int dim, int bx, int by) {
+    for (int i = 0; i < hydro::kNumTiles; ++i) {
+        const hydro::TileShape &t = hydro::kTiles[i];
+        if (t.prec == prec && t.dim == dim && t.bx == bx && t.by == by) return t.tma;
+    }
+    return 0;
+}
+
 // Defaults chosen by measurements on GB300.  dim 3: marching 64 planes; FP32 tile 16 x 8 with
 // the three-CTA register budget (the variant tuner's best: 23.03 against 22.82 G
 // cell-updates/s for 32 x 8 at 512^3), FP64 tile 32 x 8 (its one compiled 3D tile).  dim 2, FP32: row tiles of 256
@@ -189,7 +205,11 @@ bool resolve_variant(int prec, int dim, const hydro_variant_t *in, hydro_variant
         if (dim != 3 || !tm || out->staging != 1 || out->occupancy != occ) return false;
     }
     if (in && (in->split < 0 || in->split > 2)) return false;
-    if (out->staging != 1 && out->staging != 2) return false;
+    if (out->staging < 1 || out->staging > 3) return false;
+    // TMA plane staging: 3D FP32 tiles compiled with it, nothing stored between the stage's parts
+    if (out->staging == 3 && (dim != 3 || prec != HYDRO_F32 || out->manifest != 1 ||
+                              !tile_compiled_tma(prec, dim, out->tile_x, out->tile_y)))
+        return false;
     if (out->occupancy != 2 && out->occupancy != 3) return false;
     // marching tiles: dim 3, and the row tiles of dim 2 (tile_y = 1), which march along y
     const bool marching = dim == 3 || (dim == 2 && out->tile_y == 1);
@@ -275,7 +295,7 @@ hydro::StageLaunch stage_args(const hydro_ctx *c, const hydro_state_t *s, int st
     L.march = c->var.march;
     L.tile_x = c->var.tile_x;
     L.tile_y = c->var.tile_y;
-    L.prefetch = c->var.staging == 2 ? 0 : 1;
+    L.prefetch = c->var.staging == 2 ? 0 : (c->var.staging == 3 ? 2 : 1);
     L.split = c->var.split;
     L.occupancy = c->var.occupancy;
     L.manifest = c->var.manifest == 2 ? 1 : (c->var.manifest == 3 ? 2 : 0);
@@ -513,7 +533,7 @@ int finish_steps(hydro_ctx *c, double *t_inout, int32_t *steps_done) {
     CK(cudaStreamSynchronize(c->stream));
     if (t_inout) *t_inout = h.t;
     if (steps_done) *steps_done = h.steps;
-    return (h.status & hydro::STATUS_NONFINITE) ? HYDRO_ENONFINITE : HYDRO_OK;
+    return status_code(h.status);
 }
 
 struct DeviceGuard {
@@ -930,7 +950,7 @@ int hydro_cfl_dt(hydro_ctx_t *c, const hydro_state_t *state, double *dt_out) {
     CK(cudaMemcpyAsync(&h, c->ctrl, sizeof h, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     *dt_out = h.dt;
-    return (h.status & hydro::STATUS_NONFINITE) ? HYDRO_ENONFINITE : HYDRO_OK;
+    return status_code(h.status);
 }
 
 int hydro_totals(hydro_ctx_t *c, const hydro_state_t *state, double out[5]) {
@@ -951,7 +971,7 @@ int hydro_status(hydro_ctx_t *c) {
     unsigned int st = 0;
     CK(cudaMemcpyAsync(&st, &c->ctrl->status, sizeof st, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    return (st & hydro::STATUS_NONFINITE) ? HYDRO_ENONFINITE : HYDRO_OK;
+    return status_code(st);
 }
 
 static int convert(int32_t dim, int64_t ncell, double gamma, int32_t prec, const hydro_state_t *in,

@@ -39,7 +39,10 @@ struct Ctrl {
     double coef[2][3];      // (dt/2)/dr_a and dt/dr_a of the next step, for RK stages 1 and 2
 };
 
-enum : unsigned int { STATUS_NONFINITE = 1u };
+enum : unsigned int {
+    STATUS_NONFINITE = 1u,  // non-finite, rho <= 0 or p <= 0 seen
+    STATUS_TIMEOUT = 2u,    // a bounded wait on an mbarrier gave up
+};
 
 // ------------------------------------------------------------------- arithmetic -----------
 

@@ -20,7 +20,8 @@ struct StageLaunch {
     int periodic[3];
     int march;
     int tile_x, tile_y;
-    int prefetch;       // dim 3: 1 = next plane's loads one plane ahead, 0 = at staging
+    int prefetch;       // dim 3: 1 = next plane's loads one plane ahead, 0 = at staging,
+                        // 2 = planes staged by TMA (FP32 tiles compiled with it)
     int split;          // stage 2: 0 = dt reduction fused, 1 = left to a separate CFL pass
     int occupancy;      // dim 3 FP32: resident CTAs per SM the register budget targets (2 or 3)
     int order;          // reconstruction order (2 MinBee, 1 first order); 0 = 2
@@ -48,6 +49,7 @@ cudaError_t stage_f64(int dim, const StageLaunch &L, cudaStream_t st, bool prepa
 struct TileShape {
     int prec, dim, bx, by, both_pf;
     int manifest;  // also compiled in the manifest forms (V and F)
+    int tma;       // also compiled with TMA plane staging
 };
 extern const TileShape kTiles[];
 extern const int kNumTiles;

@@ -21,7 +21,7 @@ const TileShape kTiles[] = {
     {1, 2, 32, 8, 0},  {1, 2, 64, 4, 0},  {1, 2, 16, 16, 0}, {1, 2, 32, 16, 0},
     {1, 2, 64, 1, 1},  {1, 2, 128, 1, 1}, {1, 2, 256, 1, 1},
     {1, 3, 32, 8, 1, 1}, {1, 3, 32, 4, 1},  {1, 3, 64, 4, 1},  {1, 3, 16, 16, 1, 1},
-    {1, 3, 32, 16, 1}, {1, 3, 16, 8, 1, 1},
+    {1, 3, 32, 16, 1}, {1, 3, 16, 8, 1, 1, 1},
     {0, 1, 128, 1, 0}, {0, 2, 32, 8, 0},  {0, 2, 128, 1, 0}, {0, 3, 32, 8, 0, 1},
 };
 const int kNumTiles = sizeof(kTiles) / sizeof(kTiles[0]);

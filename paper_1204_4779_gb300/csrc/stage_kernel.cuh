@@ -28,6 +28,7 @@
 #include <type_traits>
 
 #include "hydro_device.cuh"
+#include "tma.cuh"
 
 namespace hydro {
 
@@ -416,10 +417,15 @@ template <class T, int NT, int OCC = 2> struct MinBlocks {
 // MAN (dim 3 only): 0 = nothing stored in HBM between the parts of a stage; 1 = manifest V:
 // A.uin holds primitive planes (a pass stored V(U_in)), so loaded cells need no recovery;
 // 2 = manifest F: store every face flux in A.flux instead of updating (a pass applies them).
+// PF = 2 (dim 3, FP32): the planes of U_in come into shared memory by TMA (tma.cuh): one box
+// per plane (tile plus halo) in a ring of TmaBox::slots slots, the box of plane p issued once
+// the box of plane p - slots has been read; the own cell of plane z + 2 and the halo of plane
+// z + 1 are read from their boxes, cells outside the grid by plain loads with the boundary
+// remap.  M: the tensor maps of U_in's fields (a __grid_constant__ kernel parameter).
 template <class T, int D, int BX, int BY, int STAGE, int PF, bool CFL, int MAN = 0>
 __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int x0, int y0, int zb, int ze,
                                            unsigned char *smem_raw, T cx, T cy, T cz, T &smax,
-                                           bool &bad) {
+                                           bool &bad, const TmaMaps *M = nullptr) {
     static_assert(MAN == 0 || D == 3, "the manifest forms are compiled for 3D grids");
     using S = StageShape<T, D, BX, BY>;
     using GM = Geom<D, BY>;
@@ -434,6 +440,10 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int x0, int y0
     T *const sF1 = sF0 + NV * NF;
     const Gas<T> G = A.gas;
     const bool order2 = A.order == 2;
+    constexpr bool TMA = PF == 2;
+    static_assert(!TMA || (D == 3 && std::is_same<T, float>::value && MAN == 0),
+                  "TMA staging is compiled for the 3D FP32 tiles");
+    using TB = TmaBox<BX, BY>;
     // V of a loaded cell: recovered from U, or already V (manifest V)
     auto recover = [&](const T (&u)[NV], T (&v)[NV]) {
         if constexpr (MAN == 1) {
@@ -473,15 +483,22 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int x0, int y0
 
     // halo cells of this thread: plane offset and shared index.  Halo work goes to the
     // highest threads, the tile's extra row/column of faces to the lowest.
-    int h_off[HPT], h_s[HPT];
-    bool h_ok[HPT];
+    int h_off[HPT], h_s[HPT], h_b[HPT];
+    bool h_ok[HPT], h_in[HPT];
 #pragma unroll
     for (int j = 0; j < HPT; ++j) {
         int lx, ly;
         h_ok[j] = halo_task<IN, BX, BY>((NT - 1 - tid) + j * NT, lx, ly);
         h_off[j] = cell_off(x0 + lx - 2, y0 + ly - 2);
         h_s[j] = ly * HX + lx;
+        // TMA: the cell's place in the plane's box, and whether the box holds it (inside the
+        // grid; outside, the box holds zeros and the boundary remap applies)
+        h_b[j] = ly * TB::W + lx + 2;
+        const int gx = x0 + lx - 2, gy = y0 + ly - 2;
+        h_in[j] = gx >= 0 && gx < nx && gy >= 0 && gy < ny;
     }
+    const int own_b = (ty + 2) * TB::W + tx + 4;
+    const bool own_in = active;
 
     // in-plane face tasks of this thread
     int f_o[FPT], f_s[FPT], f_a[FPT], f_id[FPT];
@@ -490,6 +507,50 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int x0, int y0
     for (int j = 0; j < FPT; ++j) f_ok[j] = face_task<IN, BX, BY>(tid, j, f_o[j], f_s[j], f_a[j], f_id[j]);
 
     const int pz = MARCH ? A.periodic[MA] : 1;
+
+    // TMA ring: TB::slots slots of one plane's box each, an mbarrier per slot.  Box of plane p:
+    // slot q % slots and use q / slots of that slot, q = p - (zb + 1); boxes zb + 1 (if the
+    // chunk has two planes or more: the halo of plane zb + 1) to ze + 1 (the own cell of plane
+    // ze - 1 + 2) are issued, and every issued box is waited for.
+    constexpr int NSL = TB::slots;
+    float *sBox = nullptr;
+    uint32_t bar0 = 0;
+    if constexpr (TMA) {
+        const uintptr_t a = (reinterpret_cast<uintptr_t>(smem_raw) + S::smem_bytes + 127) &
+                            ~static_cast<uintptr_t>(127);
+        sBox = reinterpret_cast<float *>(a);
+        bar0 = smem_u32(sBox + NSL * 5 * TB::cells);
+    }
+    auto issue_box = [&](int p) {  // one thread
+        const int q = p - (zb + 1);
+        const uint32_t bar = bar0 + 8u * (q % NSL);
+        const uint32_t dst = smem_u32(sBox + (q % NSL) * 5 * TB::cells);
+        const int zr = remap(p, nz, pz);
+        mbar_arrive_expect_tx(bar, TB::bytes);
+#pragma unroll
+        for (int k = 0; k < 5; ++k)
+            tma_load_3d(dst + 4u * k * TB::cells, &M->map[k], x0 - 4, y0 - 2, zr, bar);
+    };
+    bool tma_dead = false;  // a wait of this thread timed out: wait no more
+    auto wait_box = [&](int p) -> const float * {
+        const int q = p - (zb + 1);
+        if (!tma_dead && !mbar_wait(bar0 + 8u * (q % NSL), (q / NSL) & 1, &A.ctrl->status)) {
+            atomicOr(&A.ctrl->status, STATUS_TIMEOUT);
+            tma_dead = true;
+        }
+        return sBox + (q % NSL) * 5 * TB::cells;
+    };
+    if constexpr (TMA) {
+        if (tid == 0) {
+#pragma unroll
+            for (int k = 0; k < NSL; ++k) mbar_init(bar0 + 8u * k, 1);
+            mbar_init_fence();
+            if (zb + 1 < ze) issue_box(zb + 1);
+#pragma unroll
+            for (int k = 2; k <= NSL; ++k)
+                if (zb + k <= ze + 1) issue_box(zb + k);
+        }
+    }
 
     auto load_u = [&](T (&u)[NV], int zr, int off) {
         if constexpr (!MARCH) {
@@ -568,7 +629,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int x0, int y0
             for (int k = 0; k < NV; ++k) base[k] = active ? A.ubase[k][i] : T(0);
         }
         T Vnn[NV];
-        if constexpr (MARCH) {
+        if constexpr (MARCH && !TMA) {
             if constexpr (PF == 0) load_u(pown, remap(z + 2, nz, pz), own_off);
             recover(pown, Vnn);  // V(z+2)
             if constexpr (PF == 1) {
@@ -585,6 +646,17 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int x0, int y0
         // march-axis face above this column
         T Fzp[NV], dzn[NV];
         if constexpr (MARCH) {
+            if constexpr (TMA) {  // V(z+2) of the own cell from its box (issued a plane ago)
+                const float *b = wait_box(z + 2);
+                T u[NV];
+                if (own_in) {
+#pragma unroll
+                    for (int k = 0; k < NV; ++k) u[k] = b[k * TB::cells + own_b];
+                } else {
+                    load_u(u, remap(z + 2, nz, pz), own_off);
+                }
+                recover(u, Vnn);
+            }
             minbee_slopes<T, NV>(Vc, Vn, Vnn, order2, dzn);
             march_face<T, D>(Vc, dzc, Vn, dzn, G, Fzp, A.riemann);
             // stage plane z+1 into the other buffer, prefetch the halo of plane z+2
@@ -593,6 +665,19 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int x0, int y0
 #pragma unroll
                     for (int j = 0; j < HPT; ++j)
                         if (h_ok[j]) load_u(phalo[j], remap(z + 1, nz, pz), h_off[j]);
+                }
+                if constexpr (TMA) {  // the halo of plane z+1 from its box
+                    const float *b = wait_box(z + 1);
+#pragma unroll
+                    for (int j = 0; j < HPT; ++j) {
+                        if (!h_ok[j]) continue;
+                        if (h_in[j]) {
+#pragma unroll
+                            for (int k = 0; k < NV; ++k) phalo[j][k] = b[k * TB::cells + h_b[j]];
+                        } else {
+                            load_u(phalo[j], remap(z + 1, nz, pz), h_off[j]);
+                        }
+                    }
                 }
                 stage_plane(sVn, Vn, phalo);
                 if (PF == 1 && z + 2 < ze) {
@@ -603,6 +688,13 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int x0, int y0
             }
         }
         __syncthreads();
+        // TMA: every thread is done with the box of plane z+1; its slot takes plane z+1+slots
+        if constexpr (TMA) {
+            if (tid == 0 && z + 1 + NSL <= ze + 1) {
+                fence_proxy_async_smem();
+                issue_box(z + 1 + NSL);
+            }
+        }
 
         if (active) {
             const int fxl = ty * (BX + 1) + tx;
@@ -686,6 +778,36 @@ __global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY, OCC>::value))
     bool bad = false;
     constexpr bool CFL = STAGE == 2 && FUSED && MAN != 2;
     stage_tile<T, D, BX, BY, STAGE, PF, CFL, MAN>(A, x0, y0, zb, ze, smem_raw, cx, cy, cz, smax, bad);
+    if constexpr (CFL) reduce_signal_and_finalize<T, S::NT>(ctrl, smax, bad, true, sRed);
+}
+
+// The same stage with the planes of U_in staged by TMA (PF = 2; 3D FP32).  Dynamic shared
+// memory: StageShape::smem_bytes + TmaBox::smem_bytes.
+template <class T, int D, int BX, int BY, int STAGE, bool FUSED = true, int OCC = 2>
+__global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY, OCC>::value))
+    stage_kernel_tma(const __grid_constant__ StageArgs<T> A, const __grid_constant__ TmaMaps M) {
+    using S = StageShape<T, D, BX, BY>;
+    using GM = Geom<D, BY>;
+    static_assert(D == 3, "TMA staging marches along z");
+    static_assert(TmaBox<BX, BY>::aligned, "TMA boxes of this tile would not stay aligned");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *const sRed = reinterpret_cast<T *>(smem_raw) + 2 * S::NV * S::PL + 2 * S::NV * S::NF;
+
+    Ctrl *ctrl = A.ctrl;
+    const double dt = __ldcg(&ctrl->dt);
+    if (!(dt > 0.0)) return;  // uniform over the grid: no step to take
+    const T cx = T(__ldcg(&ctrl->coef[STAGE - 1][0]));
+    const T cy = T(__ldcg(&ctrl->coef[STAGE - 1][1]));
+    const T cz = T(__ldcg(&ctrl->coef[STAGE - 1][2]));
+    const int x0 = blockIdx.x * BX;
+    const int y0 = blockIdx.y * BY;
+    const int zb = ((int)blockIdx.z + A.zchunk0) * A.march;
+    const int ze = min(zb + A.march, A.n[GM::MA]);
+    T smax = T(0);
+    bool bad = false;
+    constexpr bool CFL = STAGE == 2 && FUSED;
+    stage_tile<T, D, BX, BY, STAGE, 2, CFL, 0>(A, x0, y0, zb, ze, smem_raw, cx, cy, cz, smax, bad,
+                                               &M);
     if constexpr (CFL) reduce_signal_and_finalize<T, S::NT>(ctrl, smax, bad, true, sRed);
 }
 

@@ -112,12 +112,54 @@ static cudaError_t run_or_prepare(const StageLaunch &L, cudaStream_t st, bool pr
     return launch_stage_pf<T, D, BX, BY, PF, OCC, MAN>(L, make_stage_args<T>(L), st);
 }
 
+// TMA-staged kernels (3D FP32): the planes of U_in come in by bulk tensor copies.  Where the
+// maps cannot be made (a row pitch that is not a multiple of 16 bytes, planes not 16-byte
+// aligned) the launch falls back to the look-ahead kernels of the same tile and budget.
+template <class T, int D, int BX, int BY, int OCC> struct TmaKernels {
+    static constexpr auto s1 = stage_kernel_tma<T, D, BX, BY, 1, true, OCC>;
+    static constexpr auto s2 = stage_kernel_tma<T, D, BX, BY, 2, true, OCC>;
+    static constexpr auto s2_split = stage_kernel_tma<T, D, BX, BY, 2, false, OCC>;
+    static constexpr size_t smem = StageShape<T, D, BX, BY>::smem_bytes + TmaBox<BX, BY>::smem_bytes;
+};
+
+template <class T, int D, int BX, int BY, int OCC>
+static cudaError_t run_or_prepare_tma(const StageLaunch &L, cudaStream_t st, bool prepare_only) {
+    using K = TmaKernels<T, D, BX, BY, OCC>;
+    if (prepare_only) {
+        cudaError_t e = cudaFuncSetAttribute(K::s1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K::smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(K::s2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K::smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(K::s2_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K::smem);
+        if (e == cudaSuccess) e = prepare_stage_pf<T, D, BX, BY, 1, OCC>();  // the fallback
+        return e;
+    }
+    const StageArgs<T> A = make_stage_args<T>(L);
+    TmaMaps M;
+    if (encode_plane_maps(&M, L.uin, L.n, TmaBox<BX, BY>::W, TmaBox<BX, BY>::H) != cudaSuccess)
+        return launch_stage_pf<T, D, BX, BY, 1, OCC>(L, A, st);
+    const dim3 grid((unsigned)((A.n[0] + BX - 1) / BX), (unsigned)((A.n[1] + BY - 1) / BY),
+                    (unsigned)(L.zchunks > 0 ? L.zchunks : (A.n[2] + A.march - 1) / A.march - L.zchunk0));
+    if (L.stage == 1)
+        K::s1<<<grid, BX * BY, K::smem, st>>>(A, M);
+    else if (L.split)
+        K::s2_split<<<grid, BX * BY, K::smem, st>>>(A, M);
+    else
+        K::s2<<<grid, BX * BY, K::smem, st>>>(A, M);
+    return cudaGetLastError();
+}
+
 // Both staging depths and both occupancy targets exist only for marching tiles (dim 3, and the
 // row tiles of dim 2); one-plane tiles have nothing to look ahead to and small register needs.
 // The manifest forms (3D tiles compiled with them) exist for the look-ahead staging and the
 // default budget of the precision.
-template <class T, int D, int BX, int BY, bool BOTH_PF, bool MANIFEST = false>
+template <class T, int D, int BX, int BY, bool BOTH_PF, bool MANIFEST = false, bool TMA = false>
 static cudaError_t dispatch_tile(const StageLaunch &L, cudaStream_t st, bool prepare_only) {
+    if constexpr (TMA && D == 3) {
+        if (L.prefetch == 2)
+            return L.occupancy == 3 ? run_or_prepare_tma<T, D, BX, BY, 3>(L, st, prepare_only)
+                                    : run_or_prepare_tma<T, D, BX, BY, 2>(L, st, prepare_only);
+    }
     if constexpr (MANIFEST && D == 3) {
         constexpr int OCC = sizeof(T) == 4 ? 3 : 2;
         if (L.manifest == 1) return run_or_prepare<T, D, BX, BY, 1, OCC, 1>(L, st, prepare_only);
@@ -142,3 +184,6 @@ static cudaError_t dispatch_tile(const StageLaunch &L, cudaStream_t st, bool pre
 // The same with the manifest forms compiled too (dim 3).
 #define HYDRO_STAGE_CASE_M(T, D, BX, BY, PF2) \
     if (L.tile_x == BX && L.tile_y == BY) return dispatch_tile<T, D, BX, BY, PF2, true>(L, st, prepare_only);
+// The same with the TMA-staged kernels compiled too (dim 3 FP32).
+#define HYDRO_STAGE_CASE_MT(T, D, BX, BY, PF2) \
+    if (L.tile_x == BX && L.tile_y == BY) return dispatch_tile<T, D, BX, BY, PF2, true, true>(L, st, prepare_only);

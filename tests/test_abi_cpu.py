@@ -139,6 +139,14 @@ def test_variant_table():
     assert not hydro.variant_supported(torch.float32, 3, (16, 8), staging=2, manifest=3)
     assert not hydro.variant_supported(torch.float32, 3, (16, 8), occupancy=2, manifest=2)
     assert not hydro.variant_supported(torch.float32, 3, (16, 8), manifest=4)
+    # TMA plane staging: 3D FP32 16 x 8, either budget, nothing stored between the parts
+    assert hydro.variant_supported(torch.float32, 3, (16, 8), staging=3)
+    assert hydro.variant_supported(torch.float32, 3, (16, 8), 32, split=1, staging=3, occupancy=2)
+    assert not hydro.variant_supported(torch.float32, 3, (32, 8), staging=3)
+    assert not hydro.variant_supported(torch.float64, 3, (32, 8), staging=3)
+    assert not hydro.variant_supported(torch.float32, 2, (256, 1), staging=3)
+    assert not hydro.variant_supported(torch.float32, 3, (16, 8), staging=3, manifest=2)
+    assert not hydro.variant_supported(torch.float32, 3, (16, 8), staging=4)
 
 
 def test_workspace_bytes_of_the_manifest_forms():

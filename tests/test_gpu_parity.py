@@ -247,3 +247,33 @@ def test_manifest_forms_are_the_same_step(dtype, tile, split, manifest):
 def test_manifest_forms_fp64_match_oracle(manifest):
     V = inputs.smooth((21, 18, 19), seed=24)
     _compare64(V, 1.4, (1, 0, 1), 0.4, 10, variant=dict(march=5, manifest=manifest))
+
+
+# ---- TMA plane staging (staging 3, 3D FP32 16 x 8) ------------------------------------------
+
+@pytest.mark.parametrize("occupancy", [2, 3])
+@pytest.mark.parametrize("shape,bc,march", [
+    ((44, 38, 21), (0, 0, 0), 8),    # ragged x (44 = 2 x 16 + 12), y and z chunks
+    ((44, 38, 21), (1, 0, 1), 64),   # outflow x and z, one z chunk
+    ((48, 17, 9), (0, 1, 0), 4),     # ragged y, chunks of four planes (the last of one)
+    ((16, 8, 1), (0, 0, 0), 64),     # one plane, one tile
+    ((40, 24, 2), (1, 1, 1), 1),     # chunks of one plane (only the own box in flight)
+    ((45, 38, 21), (0, 0, 0), 8),    # x extent not a multiple of 4: the look-ahead kernels run
+])
+def test_tma_staging_equals_look_ahead_staging(shape, bc, march, occupancy):
+    """The planes come into shared memory by bulk tensor copies instead of per-thread loads;
+    the arithmetic and its operands are the same, so the step is the same bit for bit."""
+    V = inputs.smooth(shape, seed=31)
+    base = dict(tile=(16, 8), march=march, split=2, occupancy=occupancy)
+    G1, t1, s1 = gpu_run(V, 1.4, bc, F32, 0.4, 12, variant=dict(base, staging=1))
+    G3, t3, s3 = gpu_run(V, 1.4, bc, F32, 0.4, 12, variant=dict(base, staging=3))
+    assert s1 == s3 == 12 and t1 == t3
+    assert np.array_equal(G1, G3)
+
+
+def test_tma_staging_blast_fp32_vs_oracle():
+    V = inputs.blast_3d(64, radius_cells=8.0)
+    G, tg, sg = gpu_run(V, 1.4, (0, 0, 0), F32, 0.4, 100, variant=dict(staging=3))
+    O, to, so, _ = oracle_run(V, 1.4, (0, 0, 0), 0.4, 100)
+    assert sg == so == 100 and abs(tg - to) <= 1e-5 * to
+    assert l1_rel(G[0], O[0]) <= 1e-4
