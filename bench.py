@@ -273,11 +273,12 @@ def run_ours(args):
     U = hydro.prim_to_cons(V, GAMMA).to(torch.float32).contiguous()
     U_init = U.clone()
     del V
-    S = hydro.Solver((n, n, n), GAMMA, bc="periodic", dtype=torch.float32, cfl=CFL)
+    S = hydro.Solver((n, n, n), GAMMA, bc="periodic", dtype=torch.float32, cfl=CFL,
+                     variant=dict(staging=args.staging) if args.staging else None)
     variant = S.variant()
     variant = {"tile": list(variant["tile"]), "march": variant["march"],
                "split": "fused dt reduction" if variant["split"] == 2 else "separate CFL pass",
-               "staging": "look-ahead" if variant["staging"] == 1 else "at use",
+               "staging": {1: "look-ahead", 2: "at use", 3: "TMA"}[variant["staging"]],
                "occupancy": variant["occupancy"]}
     # measured FMA throughput of this GPU (the FP32 roofline's denominator), before the warm-up
     fma32 = hydro.fma_rate(torch.float32, dev)
@@ -645,6 +646,88 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def run_aux(args):
+    """The two reductions of the step on their own, on the blast state (--size^3, FP32): the
+    CFL pass (hydro_cfl_dt: max of the CFL signal over U, then dt; 20 B per cell read) and the
+    FP64 totals audit (hydro_totals: fixed-order partial sums per CTA, then the final sum; 20 B
+    per cell read).  Each call synchronises (its result comes back to the host); CUDA events
+    around --steps calls after --warmup calls."""
+    import torch
+
+    from paper_1204_4779_gb300 import hydro, inputs
+    torch.cuda.set_device(0)
+    n = args.size
+    V = inputs.blast_3d_torch(n, RADIUS, device="cuda")
+    U = hydro.prim_to_cons(V, GAMMA).to(torch.float32).contiguous()
+    del V
+    S = hydro.Solver((n, n, n), GAMMA, bc="periodic", dtype=torch.float32, cfl=CFL)
+    hbm, peak_kind = _peaks()
+    nbytes = 5 * 4 * n ** 3
+    out = {}
+    with ClockSampler(_gpu_index(0)) as clk:
+        for name, call in (("cfl_pass", lambda: S.cfl_dt(U)), ("totals", lambda: S.totals(U))):
+            for _ in range(args.warmup):
+                call()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(args.steps):
+                call()
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+            out[name] = {"ms_per_call": ms, "achieved_gbs": nbytes / (ms * 1e-3) / 1e9,
+                         "frac": nbytes / (ms * 1e-3) / 1e9 / hbm}
+    S.close()
+    line = {"metric": f"HBM throughput of the CFL pass and the totals audit, {n}^3 FP32 blast",
+            "value": out["cfl_pass"]["achieved_gbs"], "unit": "GB/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{n}^3 blast state, FP32 (20 B per cell read by each call)",
+                       "l2": f"state {nbytes / 2**30:.2f} GiB vs 129 MB L2; no flush",
+                       "timing": "CUDA events around whole calls (kernels, the 8-byte result "
+                                 "copy and the synchronisation)"},
+            "roofline": {"bound": "hbm", "peak": hbm, "unit": "GB/s",
+                         "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)", **out},
+            "clocks": clk.summary(), "e2e": None, "cpu_baseline": None}
+    print(json.dumps(line), flush=True)
+
+
+def run_mlp(args):
+    """The cost model's training (hydro_mlp_train: forward, loss, back-propagation and Adam of
+    the 3-layer width-64 MLP on every record, epochs replayed from a CUDA graph) on a seeded
+    synthetic record set of the tuner's size: --size records (default 4200) of the 3D feature
+    width; epochs per second over --steps epochs after --warmup."""
+    import numpy as np
+    import torch
+
+    from paper_1204_4779_gb300 import costmodel, tuner
+    torch.cuda.set_device(0)
+    n = args.size if args.size != N else 4200
+    space = tuner.Space(3)
+    d = len(tuner.features(space, space.default_genome(), (64, 64, 64)))
+    rng = np.random.default_rng(1204477905)
+    X = rng.normal(0.0, 1.0, (n, d)).astype(np.float32)
+    t = rng.normal(0.0, 1.0, n).astype(np.float32)
+    net = costmodel.MLP(d, 64, seed=0)
+    net.train(X, t, max(args.warmup, 1))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    losses = net.train(X, t, args.steps)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    line = {"metric": f"cost-model training epochs/s ({n} records, width 64)",
+            "value": args.steps / (ms * 1e-3), "unit": "epochs/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": f"{n} seeded records x {d} features",
+                                            "loss_first_last": [float(losses[0]), float(losses[-1])]},
+            "e2e": None, "cpu_baseline": None}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -654,13 +737,18 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=40,
                     help="timed hydro_step_host calls of one step each (mean over the calls)")
     ap.add_argument("--size", type=int, default=N, help="cube side (the benchmark config is 512)")
-    ap.add_argument("--config", choices=("blast512", "batched", "kh2d", "wave"), default="blast512",
+    ap.add_argument("--config", choices=("blast512", "batched", "kh2d", "wave", "aux", "mlp"),
+                    default="blast512",
                     help="blast512: the benchmark line; batched: the 4096-grid configuration; "
                          "kh2d: the 2D shear layer (--size, default 2048); wave: the linear-wave "
-                         "example (--size, default 2^27)")
+                         "example (--size, default 2^27); aux: the CFL pass and the totals audit "
+                         "alone (--size^3); mlp: the cost model's training (--size records)")
     ap.add_argument("--dtype", choices=("f32", "f64"), default="f32",
                     help="precision of the kh2d and wave lines")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--staging", type=int, default=0, choices=(0, 1, 2, 3),
+                    help="blast512: the stage kernels' staging (0 library default, 1 look-ahead "
+                         "loads, 2 loads at use, 3 TMA)")
     ap.add_argument("--ref-size", type=int, default=128,
                     help="cube side of the reference arm's per-step sample (the oracle on the host)")
     ap.add_argument("--fp64-steps", type=int, default=10,
@@ -682,6 +770,10 @@ def main():
         run_kh2d(args)
     elif args.config == "wave":
         run_wave(args)
+    elif args.config == "aux":
+        run_aux(args)
+    elif args.config == "mlp":
+        run_mlp(args)
     else:
         run_ours(args)
 

@@ -8,7 +8,12 @@
 //
 // Flat parameter layout: W1 (H x d, row-major), b1 (H), W2 (H x H), b2 (H), W3 (1 x H), b3 (1).
 // Workspace for n samples (floats): h1 (n H), h2 (n H), y (n), dy (n), dz2 (n H), dz1 (n H),
-// grad (P), loss (1), the weight-gradient chunk partials (ceil(n / kChunk) x H x (max(d, H) + 1)).
+// grad (P), loss (1), the Adam step counter (one int), the weight-gradient chunk partials
+// (ceil(n / kChunk) x H x (max(d, H) + 1)).
+//
+// Training replays captured epochs: the Adam step number lives in the workspace (the loss
+// kernel advances it, the Adam kernel derives its bias corrections from it), so one epoch's
+// launches are the same every epoch and a CUDA graph of kEpochsPerGraph epochs is replayed.
 #include <math.h>
 #include <string.h>
 
@@ -20,8 +25,10 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kChunk = 128;  // samples per partial sum of the weight gradients
 
+constexpr int kEpochsPerGraph = 16;
+
 struct Sizes {
-    long long P, h1, h2, y, dy, dz2, dz1, grad, loss, part, total;  // float offsets / count
+    long long P, h1, h2, y, dy, dz2, dz1, grad, loss, stepc, part, total;  // float offsets / count
 };
 
 Sizes sizes(int d, int H, long long n) {
@@ -36,6 +43,7 @@ Sizes sizes(int d, int H, long long n) {
     S.dz1 = o; o += n * H;
     S.grad = o; o += S.P;
     S.loss = o; o += 1;
+    S.stepc = o; o += 1;
     S.part = o; o += (n + kChunk - 1) / kChunk * (long long)H * ((d > H ? d : H) + 1);
     S.total = o;
     return S;
@@ -55,9 +63,12 @@ __global__ void __launch_bounds__(kThreads) dense_forward(const float *in, int d
     out[idx] = TANH ? tanhf(acc) : acc;
 }
 
-// dy[s] = 2 (y[s] - t[s]) / n; loss = (1/n) sum_s (y[s] - t[s])^2 (one CTA, fixed order)
+// dy[s] = 2 (y[s] - t[s]) / n; loss = (1/n) sum_s (y[s] - t[s])^2 (one CTA, fixed order).
+// Training (stepc non-null): also record the loss in hist[*stepc - step0] and advance the Adam
+// step counter *stepc, which the Adam kernel of the same epoch reads.
 __global__ void __launch_bounds__(kThreads) mse_kernel(const float *y, const float *t, long long n,
-                                                       float *dy, float *loss) {
+                                                       float *dy, float *loss, int *stepc = nullptr,
+                                                       int step0 = 0, float *hist = nullptr) {
     __shared__ float s[kThreads];
     float acc = 0.0f;
     for (long long i = threadIdx.x; i < n; i += kThreads) {
@@ -71,7 +82,13 @@ __global__ void __launch_bounds__(kThreads) mse_kernel(const float *y, const flo
         if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
         __syncthreads();
     }
-    if (threadIdx.x == 0) *loss = s[0] / (float)n;
+    if (threadIdx.x == 0) {
+        *loss = s[0] / (float)n;
+        if (stepc) {
+            if (hist) hist[*stepc - step0] = s[0] / (float)n;
+            *stepc += 1;
+        }
+    }
 }
 
 // dz[s][i] = (sum_j delta[s][j] W[j][i]) (1 - h[s][i]^2): back through a dense layer and tanh
@@ -125,6 +142,25 @@ __global__ void __launch_bounds__(kThreads) dense_wgrad_sum(const float *part, i
         gb[j] = acc;
 }
 
+// Adam with the step number t = *stepc read on the device (bias corrections 1 - b^t)
+__global__ void __launch_bounds__(kThreads) adam_kernel_dev(float *p, float *m, float *v,
+                                                            const float *g, long long count,
+                                                            float lr, float b1, float b2, float eps,
+                                                            const int *stepc) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const float t = (float)*stepc;
+    const float c1 = 1.0f - powf(b1, t), c2 = 1.0f - powf(b2, t);
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+__global__ void set_step_kernel(int *stepc, int value) { *stepc = value; }
+
 __global__ void __launch_bounds__(kThreads) adam_kernel(float *p, float *m, float *v, const float *g,
                                                         long long count, float lr, float b1,
                                                         float b2, float eps, float c1, float c2) {
@@ -160,15 +196,18 @@ cudaError_t forward_all(const float *p, int d, int H, const float *X, long long 
     return cudaGetLastError();
 }
 
+// Forward, loss and back-propagation into ws + S.grad.  Training: stepc/step0/hist as in
+// mse_kernel.
 cudaError_t gradient_all(const float *p, int d, int H, const float *X, const float *t, long long n,
-                         float *ws, const Sizes &S, cudaStream_t st) {
+                         float *ws, const Sizes &S, cudaStream_t st, int *stepc = nullptr,
+                         int step0 = 0, float *hist = nullptr) {
     cudaError_t e = forward_all(p, d, H, X, n, ws, S, st);
     if (e != cudaSuccess) return e;
     const float *W2 = p + (long long)H * d + H, *W3 = W2 + (long long)H * H + H;
     float *g = ws + S.grad;
     float *gW1 = g, *gb1 = gW1 + (long long)H * d, *gW2 = gb1 + H, *gb2 = gW2 + (long long)H * H;
     float *gW3 = gb2 + H, *gb3 = gW3 + H;
-    mse_kernel<<<1, kThreads, 0, st>>>(ws + S.y, t, n, ws + S.dy, ws + S.loss);
+    mse_kernel<<<1, kThreads, 0, st>>>(ws + S.y, t, n, ws + S.dy, ws + S.loss, stepc, step0, hist);
     // output layer (linear): delta = dy
     float *part = ws + S.part;
     dense_wgrad(ws + S.dy, 1, ws + S.h2, H, n, part, gW3, gb3, st);
@@ -243,17 +282,43 @@ int hydro_mlp_train(float *params, float *m, float *v, int32_t d, int32_t hidden
         return HYDRO_EINVAL;
     const Sizes S = sizes(d, hidden, n);
     float *ws = static_cast<float *>(workspace);
+    int *stepc = reinterpret_cast<int *>(ws + S.stepc);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    for (int k = 0; k < epochs; ++k) {
-        cudaError_t e = gradient_all(params, d, hidden, X, t, n, ws, S, st);
-        if (e == cudaSuccess && loss_out)
-            e = cudaMemcpyAsync(loss_out + k, ws + S.loss, sizeof(float), cudaMemcpyDeviceToDevice, st);
-        if (e != cudaSuccess) return hydro::record_cuda_error(e, "hydro_mlp_train");
-        const int rc = hydro_mlp_adam(params, m, v, ws + S.grad, S.P, step0 + k + 1, lr, 0.9f,
-                                      0.999f, 1e-8f, stream);
-        if (rc) return rc;
+    // one epoch: forward, loss (advances the step counter), back-propagation, Adam
+    auto epoch = [&](cudaStream_t s) -> cudaError_t {
+        cudaError_t e = gradient_all(params, d, hidden, X, t, n, ws, S, s, stepc, step0, loss_out);
+        if (e != cudaSuccess) return e;
+        adam_kernel_dev<<<blocks(S.P), kThreads, 0, s>>>(params, m, v, ws + S.grad, S.P, lr, 0.9f,
+                                                         0.999f, 1e-8f, stepc);
+        return cudaGetLastError();
+    };
+    set_step_kernel<<<1, 1, 0, st>>>(stepc, step0);
+    cudaError_t e = cudaGetLastError();
+    const int per = epochs < kEpochsPerGraph ? epochs : kEpochsPerGraph;
+    const int reps = per > 0 ? epochs / per : 0;
+    if (e == cudaSuccess && reps > 1) {
+        // capture `per` epochs on a private stream and replay them on the caller's
+        cudaStream_t cap = nullptr;
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t x = nullptr;
+        e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t ec = cudaSuccess;
+            for (int k = 0; k < per && ec == cudaSuccess; ++k) ec = epoch(cap);
+            e = cudaStreamEndCapture(cap, &g);
+            if (e == cudaSuccess) e = ec;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&x, g, 0);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = cudaGraphLaunch(x, st);
+        if (x) cudaGraphExecDestroy(x);
+        if (g) cudaGraphDestroy(g);
+        if (cap) cudaStreamDestroy(cap);
+        for (int k = reps * per; k < epochs && e == cudaSuccess; ++k) e = epoch(st);
+    } else {
+        for (int k = 0; k < epochs && e == cudaSuccess; ++k) e = epoch(st);
     }
-    return HYDRO_OK;
+    return e == cudaSuccess ? HYDRO_OK : hydro::record_cuda_error(e, "hydro_mlp_train");
 }
 
 }  // extern "C"

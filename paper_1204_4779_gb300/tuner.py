@@ -356,7 +356,10 @@ def _over_budget(done, spent, budget_evals, budget_seconds) -> bool:
 
 
 def time_to_best(done, t_marks):
-    """Wall-clock at which the final best record was first reached."""
+    """Wall-clock at which the final best record was first reached (None if nothing was
+    benchmarked)."""
+    if not t_marks:
+        return None
     best = max(r.mu for r in done)
     for r, t in zip(done, t_marks):
         if r.mu >= best:
@@ -616,20 +619,22 @@ def study(db: DB, target, seeds: int, ga_evals: int, reps: int = 10, steps: int 
         mb, md, ms = model_guided(space, target, bench, cm, others, np.random.default_rng(s),
                                   budget_seconds=frac * W, pretrained=False, marks=mk,
                                   clock=clock)
-        rec["model_frac"] = {"evals": len(md), "seconds": ms, "best": mb.mu, "sigma": mb.sigma,
+        rec["model_frac"] = {"evals": len(mk), "seconds": ms, "best": mb.mu, "sigma": mb.sigma,
                              "time_to_best": time_to_best(md, mk),
                              "variant": space.variant(mb.genome),
                              "matches_plain_W": bool(mb.mu >= ga_best.mu - (ga_best.sigma + mb.sigma))}
         runs.append(rec)
         log(f"{target} seed {s}: W {W:.2f} s  plain_W {ga_best.mu / 1e9:.3f} G  "
             f"plain_frac {nb.mu / 1e9:.3f} G  model_frac {mb.mu / 1e9:.3f} G "
-            f"({len(md)} benchmarks, {ms:.2f} s)")
+            f"({len(mk)} benchmarks, {ms:.2f} s)")
     summary = {}
     for arm in ("plain_W", "plain_frac", "model_frac"):
         b = np.array([r[arm]["best"] for r in runs])
-        t = np.array([r[arm]["time_to_best"] for r in runs])
+        t = np.array([r[arm]["time_to_best"] if r[arm]["time_to_best"] is not None else np.nan
+                      for r in runs])
         summary[arm] = {"best_mean": float(b.mean()), "best_sd": float(b.std(ddof=1)) if len(b) > 1 else 0.0,
-                        "ttb_mean": float(t.mean()), "ttb_sd": float(t.std(ddof=1)) if len(t) > 1 else 0.0}
+                        "ttb_mean": float(np.nanmean(t)) if np.isfinite(t).any() else None,
+                        "ttb_sd": float(np.nanstd(t, ddof=1)) if np.isfinite(t).sum() > 1 else 0.0}
     summary["model_matches"] = int(sum(r["model_frac"]["matches_plain_W"] for r in runs))
     summary["seeds"] = len(runs)
     summary["W_mean"] = float(np.mean([r["W"] for r in runs]))

@@ -62,3 +62,25 @@ def test_training_reduces_loss_deterministically():
     lb = b.train(X, t, 300, lr=3e-3)
     assert la[-1] < 0.2 * la[0]
     assert np.array_equal(la, lb) and np.array_equal(a.get_params(), b.get_params())
+
+
+def test_training_equals_gradient_and_adam_steps():
+    """hydro_mlp_train (epochs replayed from a captured graph, the step number kept on the
+    device) computes the same updates as the same number of gradient + Adam calls, and its loss
+    history is the loss before each step."""
+    d, H = 10, 64
+    rng = np.random.default_rng(6)
+    X = rng.normal(0, 1, (300, d)).astype(np.float32)
+    t = rng.normal(0, 1, 300).astype(np.float32)
+    a, _ = _model(d, H, 7)
+    b, _ = _model(d, H, 7)
+    epochs = 37  # two replays of 16 captured epochs and five direct ones
+    hist = a.train(X, t, epochs, lr=3e-3)
+    losses = []
+    for _ in range(epochs):
+        g, loss = b.gradient(X, t)
+        losses.append(loss)
+        b.adam(g, lr=3e-3)
+    pa, pb = a.get_params(), b.get_params()
+    assert np.max(np.abs(pa - pb)) <= 1e-5 * max(1.0, np.max(np.abs(pb)))
+    assert np.allclose(hist, losses, rtol=1e-5, atol=1e-7)

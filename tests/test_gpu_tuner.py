@@ -1,8 +1,10 @@
 """The variant tuner on the GPU: real benchmarks of stage-kernel variants, the cost model
 trained on them by the library's CUDA kernels, and what the trained model gains: it ranks a
-held-out grid's variants (unlike the same network trained on shuffled times), and a search
-guided by it finds the best variant with fewer benchmarks than the plain evolutionary search
-with the same number of benchmarks."""
+held-out grid's variants (unlike the same network trained on shuffled times), a search guided
+by it finds the best variant with fewer benchmarks than the plain evolutionary search with the
+same number of benchmarks, and, over five seeds, with a quarter of the plain search's
+wall-clock (its own training included) it finds as good a variant as the plain search with
+that quarter and nearly as good as the plain search with all of it."""
 import math
 
 import numpy as np
@@ -31,8 +33,13 @@ def test_benchmark_records():
         assert r.ok and r.mu > 0, b2.space.variant(g)
 
 
-@pytest.mark.slow
-def test_trained_cost_model_ranks_and_guides_the_search():
+TARGET = (160, 160, 160)
+
+
+@pytest.fixture(scope="module")
+def measured():
+    """Benchmarks on five training grids (80 random variants each) and every variant of the
+    held-out target grid."""
     from paper_1204_4779_gb300 import tuner as T
     rng = np.random.default_rng(5)
     db = T.DB(None)
@@ -42,9 +49,57 @@ def test_trained_cost_model_ranks_and_guides_the_search():
         bench = T.Benchmark(sh, reps=3, steps=2)
         for i in rng.permutation(len(genomes))[:80]:
             db.add(bench(genomes[i]))
-    target = (160, 160, 160)
-    bench = T.Benchmark(target, reps=3, steps=2)
-    truth = [bench(g) for g in genomes]          # every variant of the held-out grid
+    # every variant of the held-out grid, each benchmark 5 runs of 20 steps (a benchmark of a
+    # few milliseconds would leave a quarter of the plain search's wall-clock shorter than one
+    # training of the cost model)
+    bench = T.Benchmark(TARGET, reps=5, steps=20)
+    truth = [bench(g) for g in genomes]
+    return db, truth
+
+
+@pytest.mark.slow
+def test_model_guided_search_matches_the_plain_search_at_equal_wall_clock(measured):
+    """The tuner gate on a small held-out grid, five seeds: the model-guided search given a
+    quarter of the plain search's wall-clock W, its training from scratch on the clock, against
+    the plain search given the same quarter and the plain search given W.  Benchmarks replay the
+    target's measured records (each advancing the clock by the seconds that benchmark took);
+    the model's training and every other step run for real on the same clock."""
+    import time
+
+    from paper_1204_4779_gb300 import tuner as T
+    db, truth = measured
+    space = T.Space(3)
+    lookup = {tuple(r.genome): r for r in truth}
+
+    class Replay:
+        def __init__(self):
+            self.space = space
+            self.spent = 0.0
+
+        def __call__(self, g):
+            r = lookup[tuple(g)]
+            self.spent += r.seconds
+            return r
+
+    rep = Replay()
+    clock = lambda: time.perf_counter() + rep.spent
+    out = T.study(db, TARGET, seeds=5, ga_evals=40, bench=rep, clock=clock, log=print)
+    s = out["summary"]
+    best = max(r.mu for r in truth)
+    print({k: (v["best_mean"] / best, v["best_sd"] / best) for k, v in s.items()
+           if isinstance(v, dict)}, "matches", s["model_matches"], "W", s["W_mean"])
+    assert s["model_frac"]["best_mean"] >= s["plain_frac"]["best_mean"]
+    assert s["model_frac"]["best_mean"] >= 0.95 * s["plain_W"]["best_mean"]
+
+
+@pytest.mark.slow
+def test_trained_cost_model_ranks_and_guides_the_search(measured):
+    from paper_1204_4779_gb300 import tuner as T
+    rng = np.random.default_rng(5)
+    db, truth = measured
+    space = T.Space(3)
+    genomes = space.all_genomes()
+    target = TARGET
     best = max(r.mu for r in truth)
     X, y = T.training_set(db.records)
     Xt = np.array([T.features(space, g, target) for g in genomes])
