@@ -78,8 +78,12 @@ __global__ void __launch_bounds__(kAuxThreads) cfl_kernel(const AuxT<T> A) {
     reduce_signal_and_finalize<T, kAuxThreads>(A.ctrl, smax, bad, ADVANCE, sred, A.total_blocks);
 }
 
-// Totals, level 1: CTA b sums the contiguous chunk [b*chunk, (b+1)*chunk) of each plane in
-// FP64 (fixed per-thread strides, fixed shared-memory tree) into partials[k * nparts + b].
+// Totals, level 1: CTA b sums the contiguous chunk [b*chunk, (b+1)*chunk) of each plane
+// (fixed per-thread strides, fixed shared-memory tree) into partials[k * nparts + b].  FP64
+// states are summed in FP64.  FP32 states: each thread sums its cells in double-float (every
+// FP32 value is exact in it; TwoSum and renormalisation per addition keep about 48 bits of the
+// running sum) and converts its sums to FP64 once, so that the FP64 pipe, at 1/62 of the FP32
+// rate, does not bound the pass; the tree over the threads runs in FP64.
 template <class T, int NV>
 __global__ void __launch_bounds__(kAuxThreads)
     totals_partial_kernel(const AuxT<T> A, double *partials, int nparts) {
@@ -87,9 +91,27 @@ __global__ void __launch_bounds__(kAuxThreads)
     const long long chunk = (A.ncell + nparts - 1) / nparts;
     const long long b0 = (long long)blockIdx.x * chunk;
     const long long b1 = b0 + chunk < A.ncell ? b0 + chunk : A.ncell;
+    double tsum[NV];
+    if constexpr (sizeof(T) == 4) {
+        DF acc[NV];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) acc[k] = {0.0f, 0.0f};
+        for (long long i = b0 + threadIdx.x; i < b1; i += kAuxThreads) {
+#pragma unroll
+            for (int k = 0; k < NV; ++k) acc_add(acc[k], {A.u[k][i], 0.0f});
+        }
+#pragma unroll
+        for (int k = 0; k < NV; ++k) tsum[k] = (double)acc[k].hi + (double)acc[k].lo;
+    } else {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) tsum[k] = 0.0;
+        for (long long i = b0 + threadIdx.x; i < b1; i += kAuxThreads) {
+#pragma unroll
+            for (int k = 0; k < NV; ++k) tsum[k] += (double)A.u[k][i];
+        }
+    }
     for (int k = 0; k < NV; ++k) {
-        double acc = 0.0;
-        for (long long i = b0 + threadIdx.x; i < b1; i += kAuxThreads) acc += (double)A.u[k][i];
+        const double acc = tsum[k];
         s[threadIdx.x] = acc;
         __syncthreads();
         for (int w = kAuxThreads / 2; w > 0; w >>= 1) {

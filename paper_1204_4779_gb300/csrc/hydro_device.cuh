@@ -105,6 +105,37 @@ __device__ __forceinline__ F2 f2_fma(F2 a, F2 b, F2 c) {
     return d;
 }
 
+// Double-float arithmetic: a value carried as an unevaluated sum hi + lo of two FP32 numbers
+// (Dekker's and Knuth's error-free transformations, as used in double-double arithmetic).  The
+// additions are plain IEEE operations in the order written; the translation units that use
+// them either compile with --fmad=false or use no contractible product next to them.
+struct DF {
+    float hi, lo;
+};
+// a + b exactly as hi + lo (Knuth's TwoSum, six operations, any magnitudes)
+__device__ __forceinline__ DF two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    const float e = (a - (s - bb)) + (b - bb);
+    return {s, e};
+}
+// (hi + lo)^2 as a pair: hi^2 exactly by TwoProduct with an FMA, plus 2 hi lo (lo^2 dropped)
+__device__ __forceinline__ DF square(DF x) {
+    const float p = x.hi * x.hi;
+    float e = fmaf(x.hi, x.hi, -p);
+    e = fmaf(x.hi + x.hi, x.lo, e);
+    return {p, e};
+}
+// running sum s += x: TwoSum of the high parts, low parts added, then renormalised so that
+// |lo| <= ulp(hi) / 2 (Fast2Sum)
+__device__ __forceinline__ void acc_add(DF &s, DF x) {
+    const DF t = two_sum(s.hi, x.hi);
+    const float e = t.lo + (s.lo + x.lo);
+    const float h = t.hi + e;
+    s.lo = e - (h - t.hi);
+    s.hi = h;
+}
+
 template <class T> struct Gas {
     T g;        // gamma
     T gm1;      // gamma - 1

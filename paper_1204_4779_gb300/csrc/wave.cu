@@ -21,7 +21,8 @@
 // FP32: the stencil runs in FP32 and the energy keeps FP64 accuracy without per-cell FP64
 // arithmetic (GB300's FP64 pipe runs at 1/62 of the FP32 rate).  Each cell recomputes f1 at
 // i-1, i, i+1 from f and g (one FP32 operation each, the neighbours' loads hitting cache), so
-// the tile loop has no barrier.  With D = f1[i+1] - f1[i-1] and G = g[i] + g1[i], the energy is
+// the tile loop has no barrier; where n is a multiple of four and the arrays are 16-byte
+// aligned a thread takes four consecutive cells with 128-bit loads and stores.  With D = f1[i+1] - f1[i-1] and G = g[i] + g1[i], the energy is
 // K1 sum D^2 + K2 sum G^2, K1 = c^2 dx / (8 dx^2), K2 = dx / 8.  D and G are formed exactly as
 // FP32 pairs (hi + lo) by Knuth's TwoSum, their squares as pairs by the FMA form of Dekker's
 // TwoProduct (dropping lo^2, 2^-48 of the square), and each thread adds them to two running
@@ -32,40 +33,17 @@
 #include <string.h>
 
 #include "../../include/hydro.h"
+#include "hydro_device.cuh"
 #include "hydro_internal.h"
 
 namespace {
 
+using hydro::acc_add;
+using hydro::DF;
+using hydro::square;
+using hydro::two_sum;
+
 constexpr int kWaveThreads = 256;
-
-// ---- double-float (pairs of FP32 values hi + lo) building blocks --------------------------
-
-struct DF {
-    float hi, lo;
-};
-// a + b exactly as hi + lo (Knuth's TwoSum, six operations, any magnitudes)
-__device__ __forceinline__ DF two_sum(float a, float b) {
-    const float s = a + b;
-    const float bb = s - a;
-    const float e = (a - (s - bb)) + (b - bb);
-    return {s, e};
-}
-// (hi + lo)^2 as a pair: hi^2 exactly by TwoProduct with an FMA, plus 2 hi lo (lo^2 dropped)
-__device__ __forceinline__ DF square(DF x) {
-    const float p = x.hi * x.hi;
-    float e = fmaf(x.hi, x.hi, -p);
-    e = fmaf(x.hi + x.hi, x.lo, e);
-    return {p, e};
-}
-// running sum s += x: TwoSum of the high parts, low parts added, then renormalised so that
-// |lo| <= ulp(hi) / 2 (Fast2Sum)
-__device__ __forceinline__ void acc_add(DF &s, DF x) {
-    const DF t = two_sum(s.hi, x.hi);
-    const float e = t.lo + (s.lo + x.lo);
-    const float h = t.hi + e;
-    s.lo = e - (h - t.hi);
-    s.hi = h;
-}
 
 // FP32 step with the double-float energy audit (see the file comment).  k1, k2: K1 and K2.
 __global__ void __launch_bounds__(kWaveThreads)
@@ -92,6 +70,52 @@ __global__ void __launch_bounds__(kWaveThreads)
     }
     double e = k1 * ((double)sd.hi + (double)sd.lo) + k2 * ((double)sg.hi + (double)sg.lo);
     // fixed-order tree: a butterfly within each warp, then the warp sums in warp order
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+    if ((threadIdx.x & 31) == 0) s_e[threadIdx.x >> 5] = e;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < kWaveThreads / 32; ++w) t += s_e[w];
+        partial[blockIdx.x] = t;
+    }
+}
+
+// The same step with four cells per thread: 128-bit loads and stores of f and g (n a multiple
+// of four, arrays 16-byte aligned), each cell's formulas and energy terms as in
+// wave_step_kernel_f32, the four cells added to the running sums in cell order.
+__global__ void __launch_bounds__(kWaveThreads)
+    wave_step_kernel_f32v(const float *__restrict__ f, const float *__restrict__ g,
+                          float *__restrict__ fo, float *__restrict__ go, long long n4,
+                          long long ntiles, float dt, float k, double k1, double k2,
+                          double *partial) {
+    __shared__ double s_e[kWaveThreads / 32];
+    const float4 *f4 = reinterpret_cast<const float4 *>(f);
+    const float4 *g4 = reinterpret_cast<const float4 *>(g);
+    DF sd = {0.0f, 0.0f}, sg = {0.0f, 0.0f};
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const long long q = tile * kWaveThreads + threadIdx.x;  // index of the cell quadruple
+        if (q >= n4) continue;
+        const long long n = 4 * n4;
+        const long long l = q == 0 ? n - 1 : 4 * q - 1;
+        const long long r = q == n4 - 1 ? 0 : 4 * q + 4;
+        const float4 fv = f4[q], gv = g4[q];
+        const float fi[6] = {f[l], fv.x, fv.y, fv.z, fv.w, f[r]};
+        const float gi[6] = {g[l], gv.x, gv.y, gv.z, gv.w, g[r]};
+        float f1[6], g1[4];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) f1[c] = fi[c] + dt * gi[c];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            g1[c] = gi[c + 1] + k * (f1[c + 2] + f1[c] - 2.0f * f1[c + 1]);
+            acc_add(sd, square(two_sum(f1[c + 2], -f1[c])));
+            acc_add(sg, square(two_sum(gi[c + 1], g1[c])));
+        }
+        reinterpret_cast<float4 *>(fo)[q] = make_float4(f1[1], f1[2], f1[3], f1[4]);
+        reinterpret_cast<float4 *>(go)[q] = make_float4(g1[0], g1[1], g1[2], g1[3]);
+    }
+    double e = k1 * ((double)sd.hi + (double)sd.lo) + k2 * ((double)sg.hi + (double)sg.lo);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
     if ((threadIdx.x & 31) == 0) s_e[threadIdx.x >> 5] = e;
@@ -203,14 +227,25 @@ int wave_run_t(long long n, double c, double length, double dt, T *f, T *g, int 
     const T k = T(c * c * dt / (dx * dx));
     // the FP32 energy's factors: (1/2) c^2 (D / (2 dx))^2 dx = K1 D^2, (1/2) (G / 2)^2 dx = K2 G^2
     const double k1 = c * c * dx / (8.0 * dx * dx), k2 = dx / 8.0;
+    // FP32: four cells per thread where n and the arrays allow 128-bit accesses
+    const bool vec = sizeof(T) == 4 && n % 4 == 0 && n >= 8 &&
+                     reinterpret_cast<uintptr_t>(f) % 16 == 0 && reinterpret_cast<uintptr_t>(g) % 16 == 0 &&
+                     reinterpret_cast<uintptr_t>(fb) % 16 == 0 && reinterpret_cast<uintptr_t>(gb) % 16 == 0;
+    const long long vtiles = (n / 4 + kWaveThreads - 1) / kWaveThreads;
+    const unsigned vblocks = (unsigned)(vtiles < L.nblocks ? vtiles : L.nblocks);
     for (int s = 0; s < n_steps; ++s) {
-        if constexpr (sizeof(T) == 4)
-            wave_step_kernel_f32<<<(unsigned)L.nblocks, kWaveThreads, 0, st>>>(
-                fa, ga, fb, gb, n, L.ntiles, T(dt), k, k1, k2, part);
-        else
+        if constexpr (sizeof(T) == 4) {
+            if (vec)
+                wave_step_kernel_f32v<<<vblocks, kWaveThreads, 0, st>>>(
+                    fa, ga, fb, gb, n / 4, vtiles, T(dt), k, k1, k2, part);
+            else
+                wave_step_kernel_f32<<<(unsigned)L.nblocks, kWaveThreads, 0, st>>>(
+                    fa, ga, fb, gb, n, L.ntiles, T(dt), k, k1, k2, part);
+        } else
             wave_step_kernel<T><<<(unsigned)L.nblocks, kWaveThreads, 0, st>>>(
                 fa, ga, fb, gb, n, L.ntiles, T(dt), k, c * c, dx, 1.0 / (2.0 * dx), part);
-        wave_energy_kernel<<<1, kWaveThreads, 0, st>>>(part, (int)L.nblocks, energy + s);
+        wave_energy_kernel<<<1, kWaveThreads, 0, st>>>(part, vec ? (int)vblocks : (int)L.nblocks,
+                                                       energy + s);
         T *t = fa;
         fa = fb;
         fb = t;

@@ -289,8 +289,11 @@ class Evolution:
         keys = [k for k in self.scores if k not in exclude]
         if not keys:
             return None
-        w = np.array([math.exp(-max(0.0, mu_t - self.scores[k][0] - sig_t - self.scores[k][1]) /
-                               max(T + sig_t + self.scores[k][1], 1e-30)) for k in keys])
+        # exponents of the draw probabilities; the largest is subtracted before exponentiating
+        # (the same distribution, without every weight underflowing when the spreads are tiny)
+        x = np.array([-max(0.0, mu_t - self.scores[k][0] - sig_t - self.scores[k][1]) /
+                      max(T + sig_t + self.scores[k][1], 1e-30) for k in keys])
+        w = np.exp(x - x.max())
         w = w / w.sum()
         return keys[int(self.rng.choice(len(keys), p=w))]
 

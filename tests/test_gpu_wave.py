@@ -68,13 +68,14 @@ def _fp32_steps(f, g, dt, k, c2, dx, steps):
     return f, g, np.array(E)
 
 
-def test_fp32_energy_and_state():
+@pytest.mark.parametrize("n", [1024, 1022])
+def test_fp32_energy_and_state(n):
     """FP32 against the FP64 oracle: storing f (of order one) in FP32 rounds each step's
     increment dt g (of order 2 pi / N) with relative error about eps32 N / (2 pi), 1e-5 at
     N = 1024, and the energy error is of that order (a float32 evaluation of the same steps
-    gives 3.6e-5).  The kernel's own rounding is checked exactly against that evaluation."""
+    gives 3.6e-5).  The kernel's own rounding is checked exactly against that evaluation.
+    N = 1024 runs the four-cells-per-thread kernel, N = 1022 the one-cell kernel."""
     from paper_1204_4779_gb300 import hydro
-    n = 1024
     f0, g0 = W.initial(n)
     dx = 2 * math.pi / n
     dt = dx / C

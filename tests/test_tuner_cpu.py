@@ -224,3 +224,17 @@ def test_study_arms_budgets_and_summary():
         assert s[arm]["best_mean"] > 0 and s[arm]["best_sd"] >= 0
     truth = max(synthetic_cups(space, g, target) for g in space.all_genomes())
     assert s["model_frac"]["best_mean"] >= 0.97 * truth
+
+
+def test_draw_survives_tiny_spreads():
+    """With spreads far below the score differences every weight but the top's underflows in a
+    direct evaluation; a draw that excludes the top must still return a parent (the one with
+    the largest weight)."""
+    space = T.Space(3)
+    ev = T.Evolution(space, np.random.default_rng(0))
+    gs = space.all_genomes()[:4]
+    for i, g in enumerate(gs):
+        ev.scores[g] = (20e9 - 1e9 * i, 1e3)  # 1 G apart, spreads of 1 k
+    top, _ = ev.top()
+    picks = {ev.draw(2e3, exclude=(top,)) for _ in range(20)}
+    assert picks == {gs[1]}
