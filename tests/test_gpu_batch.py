@@ -1,8 +1,8 @@
 """Batched path (hydro_batch_*): many independent 2D grids of uneven size in one persistent
 launch per RK stage.  Every grid is checked against the CPU oracle run on that grid alone:
 FP64 max relative error <= 1e-10, FP32 L1 density error <= 1e-4; the full configuration
-(4096 grids, sides log-uniform on [32, 512], 50 steps, FP32) on a seeded sample of grids,
-which the oracle computes one by one (grids do not interact)."""
+(4096 grids, sides log-uniform on [32, 512], 50 steps) in FP32 and in FP64 on a seeded sample
+of grids, which the oracle computes one by one (grids do not interact)."""
 import numpy as np
 import pytest
 
@@ -144,6 +144,30 @@ def test_full_batched_config_fp32():
         assert e <= 1e-4, (g, shapes[g], e)
         assert abs(t[g] - to) <= 1e-5 * to
     print(f"PARITY batched4096 fp32 worst_sampled_l1_rho={worst:.3e}")
+
+
+@pytest.mark.slow
+def test_full_batched_config_fp64():
+    """The same 4096-grid configuration in FP64 (50 steps): a seeded sample of grids, and the
+    largest, against the oracle run on each grid alone, max relative error <= 1e-10 and the same
+    time."""
+    shapes = [tuple(int(v) for v in s) for s in inputs.batch_shapes()]
+    Vs = [inputs.batch_grid(nx, ny, 1204477904, i) for i, (nx, ny) in enumerate(shapes)]
+    B = hydro.BatchSolver(shapes, G, dtype=F64)
+    U = _packed(B, Vs, F64)
+    t, steps = B.step(U, 50)
+    assert steps == [50] * len(shapes)
+    rng = np.random.default_rng(21)
+    sample = sorted(set(rng.choice(len(shapes), 8, replace=False).tolist()) |
+                    {int(np.argmax([a * b for a, b in shapes]))})
+    worst = 0.0
+    for g in sample:
+        O, to, so, _ = _oracle(Vs[g], (0, 0), 50)
+        e = max_rel_err(B.grid_view(U, g).cpu().numpy(), O)
+        worst = max(worst, e)
+        assert e <= 1e-10, (g, shapes[g], e)
+        assert t[g] == to, (g, t[g], to)
+    print(f"PARITY batched4096 fp64 worst_sampled_max_rel={worst:.3e}")
 
 
 # ---- row tiles: a work item is a strip of x columns marching along y -----------------------
