@@ -424,6 +424,17 @@ int hydro_step_static(const hydro_grid_t *grid, double gamma, const int32_t bc[3
  * Errors: HYDRO_EINVAL (null output, other prec), HYDRO_ECUDA. */
 int hydro_fma_rate(int32_t prec, void *stream, double *ops_per_s_out);
 
+/* Diagnostic with no counterpart in the paper: checks the bounded mbarrier wait that the
+ * TMA-staged stage kernels (variant staging 3) use.  One CTA of 32 threads waits on an mbarrier
+ * whose phase never completes (it expects an arrival nobody makes); each thread gives up after
+ * the wait's bound (2^16 tries or about one second of the GPU's global timer) and counts itself
+ * in *gave_up_device (one int32 of caller-owned device memory, zeroed by the call).  The count is
+ * copied to *gave_up_out (32 when the bound works) and the kernel's time to *elapsed_ms_out (may
+ * be NULL); the context stays usable.  Synchronises `stream`.  Errors: HYDRO_EINVAL (null
+ * pointers), HYDRO_ECUDA. */
+int hydro_wait_bound_check(int32_t *gave_up_device, void *stream, int32_t *gave_up_out,
+                           double *elapsed_ms_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -39,6 +39,13 @@ template <int BX, int BY> struct TmaBox {
 };
 
 constexpr int kMbarSpins = 1 << 16;
+constexpr unsigned long long kMbarMaxNs = 1000000000ull;  // and at most about one second
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -59,12 +66,21 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t byt
                  : "memory");
 }
 
-// Wait until the phase of parity `parity` has completed; false after kMbarSpins tries, or
-// as soon as `abort_bits` (checked every 256 tries) has STATUS_TIMEOUT set by another waiter.
+// Wait until the phase of parity `parity` has completed; false after kMbarSpins tries or about
+// kMbarMaxNs of the global timer, or as soon as `abort_bits` has STATUS_TIMEOUT set by another
+// waiter (both checked every 256 tries, so a wait that succeeds at once reads neither).
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
                                           const volatile unsigned int *abort_bits) {
+    unsigned long long t0 = 0;
     for (int i = 0; i < kMbarSpins; ++i) {
-        if ((i & 255) == 255 && (*abort_bits & STATUS_TIMEOUT)) return false;
+        if ((i & 255) == 255) {
+            if (*abort_bits & STATUS_TIMEOUT) return false;
+            const unsigned long long t = globaltimer_ns();
+            if (t0 == 0)
+                t0 = t;
+            else if (t - t0 > kMbarMaxNs)
+                return false;
+        }
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"

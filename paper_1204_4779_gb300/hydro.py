@@ -37,7 +37,7 @@ EXPORTS = (
     "hydro_batch_offsets", "hydro_batch_set_stream", "hydro_batch_step", "hydro_batch_totals",
     "hydro_batch_set_profiling", "hydro_batch_kernel_times",
     "hydro_mlp_sizes", "hydro_mlp_forward", "hydro_mlp_gradient", "hydro_mlp_adam", "hydro_mlp_train",
-    "hydro_wave_workspace_bytes", "hydro_wave_run", "hydro_fma_rate",
+    "hydro_wave_workspace_bytes", "hydro_wave_run", "hydro_fma_rate", "hydro_wait_bound_check",
 )
 
 
@@ -126,6 +126,7 @@ def load_library(path: str = LIB_PATH, build_if_missing: bool = True):
             "hydro_batch_kernel_times": ([vp, P(dbl), P(i64), i32, i32], ctypes.c_int),
             "hydro_mlp_sizes": ([i32, i32, i64, P(i64), P(ctypes.c_size_t)], ctypes.c_int),
             "hydro_fma_rate": ([i32, vp, P(dbl)], ctypes.c_int),
+            "hydro_wait_bound_check": ([vp, vp, P(i32), P(dbl)], ctypes.c_int),
             "hydro_wave_workspace_bytes": ([i64, i32, i32, P(ctypes.c_size_t)], ctypes.c_int),
             "hydro_wave_run": ([i32, i64, dbl, dbl, dbl, vp, vp, i32, P(dbl), vp, ctypes.c_size_t, vp],
                                ctypes.c_int),
@@ -489,6 +490,19 @@ def fma_rate(dtype=torch.float32, device=None) -> float:
     with torch.cuda.device(dev):
         _check(lib.hydro_fma_rate(_prec(dtype), _stream_ptr(dev), ctypes.byref(out)), "hydro_fma_rate")
     return out.value
+
+
+def wait_bound_check(device=None):
+    """hydro_wait_bound_check: (threads of 32 that gave up waiting on an mbarrier phase that never
+    completes, the kernel's milliseconds)."""
+    lib = load_library()
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    buf = torch.zeros(1, dtype=torch.int32, device=dev)
+    n, ms = ctypes.c_int32(), ctypes.c_double()
+    with torch.cuda.device(dev):
+        _check(lib.hydro_wait_bound_check(ctypes.c_void_p(buf.data_ptr()), _stream_ptr(dev),
+                                          ctypes.byref(n), ctypes.byref(ms)), "hydro_wait_bound_check")
+    return n.value, ms.value
 
 
 def wave_run(f: torch.Tensor, g: torch.Tensor, c: float, length: float, dt: float, n_steps: int):

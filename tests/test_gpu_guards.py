@@ -116,3 +116,19 @@ def test_batched_and_conversion_guards():
                                                    torch.cuda.current_stream().cuda_stream) == 0
     torch.cuda.synchronize()
     assert _intact(cbuf, n2)
+
+
+def test_bounded_mbarrier_wait_gives_up_and_the_context_stays_usable():
+    """The bounded wait of the TMA-staged kernels, on an mbarrier phase that never completes (an
+    arrival nobody makes): every thread gives up within the bound (2^16 tries or about a second
+    of the global timer) instead of hanging, and the device runs a step afterwards."""
+    from paper_1204_4779_gb300 import hydro, inputs
+    gave_up, ms = hydro.wait_bound_check()
+    assert gave_up == 32
+    assert 0.0 < ms < 3000.0, ms
+    V = inputs.blast_3d(shape=(32, 24, 16), radius_cells=4.0)
+    U = hydro.prim_to_cons(torch.from_numpy(V).cuda(), 1.4).float().contiguous()
+    S = hydro.Solver((32, 24, 16), 1.4, bc="periodic", dtype=torch.float32, cfl=0.4,
+                     variant=dict(staging=3))
+    t, n = S.step(U, 3)
+    assert n == 3 and S.status() == hydro.HYDRO_OK and bool(torch.isfinite(U).all())
