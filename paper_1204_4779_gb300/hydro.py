@@ -230,8 +230,8 @@ class Solver:
     shape: cells per axis (nx, [ny, [nz]]); bc: per-axis "periodic"/"outflow"/"analytic"/
     "exchange" (or 0-3; analytic boundaries take their solution from set_analytic; exchange
     boundaries wrap through the ghost pack/unpack kernels);
-    variant: dict(tile=(bx, by), march=m, split=0|1|2, staging=0|1|2, occupancy=0|2|3,
-    manifest=0|1|2|3) or None for the default.
+    variant: dict(tile=(bx, by), march=m, split=0|1|2, staging=0|1|2|3, occupancy=0|2|3,
+    manifest=0|1|2|3) or None for the default (staging 3: TMA plane staging, 3D FP32 tiles).
     """
 
     def __init__(self, shape, gamma: float, bc="periodic", dtype=torch.float32, cfl: float = 0.4,

@@ -201,20 +201,23 @@ def test_single_cell_axes_and_tiny_grids():
         assert sg == so and np.allclose(G, O, rtol=1e-12, atol=1e-12)
 
 
-@pytest.mark.parametrize("n_steps,t_end,shape,bc", [
-    (1, 0.0, (40, 36, 100), (0, 0, 0)), (3, 0.0, (40, 36, 100), (0, 0, 0)),
-    (5, 0.002, (40, 36, 100), (0, 0, 0)),
-    (1, 0.0, (40, 36, 100), (0, 1, 1)),   # outflow along z
-    (2, 0.0, (24, 20, 57), (0, 0, 0)),    # a last slab of one plane: stage 1 whole first
-    (1, 0.0, (24, 20, 11), (0, 0, 0))])   # two march chunks: two slabs
-def test_host_stepping_3d_overlapped_copy_back(n_steps, t_end, shape, bc):
+@pytest.mark.parametrize("n_steps,t_end,shape,bc,staging", [
+    (1, 0.0, (40, 36, 100), (0, 0, 0), 1), (3, 0.0, (40, 36, 100), (0, 0, 0), 1),
+    (5, 0.002, (40, 36, 100), (0, 0, 0), 1),
+    (1, 0.0, (40, 36, 100), (0, 1, 1), 1),   # outflow along z
+    (2, 0.0, (24, 20, 57), (0, 0, 0), 1),    # a last slab of one plane: stage 1 whole first
+    (1, 0.0, (24, 20, 11), (0, 0, 0), 1),    # two march chunks: two slabs
+    # TMA plane staging: the slab launches start at march chunk zchunk0 > 0
+    (3, 0.0, (40, 36, 100), (0, 0, 0), 3), (1, 0.0, (40, 36, 100), (0, 1, 1), 3),
+    (2, 0.0, (24, 20, 57), (1, 0, 0), 3)])
+def test_host_stepping_3d_overlapped_copy_back(n_steps, t_end, shape, bc, staging):
     """In 3D hydro_step_host copies the state in by z-slabs with the first CFL pass split over
     them, and runs the last step's two stages slab by slab, copying each slab back while later
     slabs compute (e.g. 13 march chunks of 8 planes, the last one ragged, in 8 slabs): the host
-    result, time and step count equal stepping on the device."""
+    result, time and step count equal stepping on the device, with either plane staging."""
     V = inputs.blast_3d(shape=shape, radius_cells=6.0)
     U = gpu_state(V, 1.4, F32)
-    var = dict(march=8)
+    var = dict(march=8, staging=staging)
     S = hydro.Solver(shape, 1.4, bc=list(bc), dtype=F32, variant=var)
     Ud = U.clone()
     td, nd = S.step(Ud, n_steps, t_end=t_end)
