@@ -402,8 +402,7 @@ int hydro_mlp_train(float *params, float *m, float *v, int32_t d, int32_t hidden
  *   rounded up to 256 bytes, must fit in HYDRO_STATIC_SCRATCH_BYTES (for example a 1D grid of
  *   10^5 cells in FP64, or 59^3 cells in FP32); larger grids return HYDRO_EINVAL.
  *   Set-up: the first call on each device (that device current) looks up the array's device
- *   address with cudaGetSymbolAddress and sets kernel attributes; make that first call
- *   before any stream capture.
+ *   address with cudaGetSymbolAddress and sets kernel attributes; later calls reuse both.
  *   Time: *t_inout (NULL: 0) is read on the host when the call is made.  With t_inout or
  *   steps_done non-NULL the call copies the control block back and synchronises the stream
  *   (as hydro_step does); with both NULL it only enqueues work and returns.

@@ -11,8 +11,7 @@
 // Host code cannot use that array's name as a device address (in host code it names a host
 // stand-in), so the first call on each device, with that device current, looks the address
 // up once with cudaGetSymbolAddress and sets the stage kernels' shared-memory attributes;
-// later calls reuse it.  Because of that set-up, make the first call on a device before any
-// stream capture.
+// later calls reuse it.
 //
 // The kernels are one fixed variant (not the tuned defaults of hydro_create): 32 x 8 tiles in
 // 2D and 3D (3D marching up to 64 planes), 128-cell rows in 1D, look-ahead staging, the
