@@ -526,8 +526,8 @@ def run_wave(args):
                        "energy_drift": drift},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": None,
-                         "kernel": "wave_step_kernel" if f64 else (
-                             "wave_step_kernel_f32v" if n % 4 == 0 else "wave_step_kernel_f32"),
+                         "kernel": ("wave_step_kernel_f64v" if n % 2 == 0 else "wave_step_kernel")
+                         if f64 else ("wave_step_kernel_f32v" if n % 4 == 0 else "wave_step_kernel_f32"),
                          "scope": "whole call (step kernels and the per-step energy sums)",
                          "bytes_per_cell_update": 4 * esz,
                          "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"},

@@ -12,11 +12,16 @@
 // arrays and two workspace arrays.  The translation unit is compiled with --fmad=false: every
 // product and sum of the update formulas is its own IEEE operation, in the formulas' order.
 //
-// FP64: a tile's f1 (plus one halo cell each side) goes through shared memory; each cell's
-// energy term is evaluated in FP64 (the centred difference multiplied by a precomputed
-// 1 / (2 dx) rather than divided by 2 dx, which changes its rounding by at most an ulp, well
-// inside the 1e-13 relative agreement the tests require with the oracle's division), the tile's
-// terms reduced by a fixed tree and summed in tile order into the CTA's partial.
+// FP64, n even and arrays 16-byte aligned (wave_step_kernel_f64v): two cells per thread with
+// 128-bit loads and stores, the neighbours' f1 from the adjacent lanes by warp shuffles; the
+// energy as K1 sum D^2 + K2 sum G^2 (below), each thread's two sums kept in FP64 by fused
+// multiply-adds, so a cell costs 11 FP64 operations (the update's 7, the energy's 4) on
+// GB300's FP64 pipe (1/62 of the FP32 rate).  Otherwise (wave_step_kernel) a tile's f1 (plus
+// one halo cell each side) goes through shared memory and each cell's energy term is evaluated
+// as the formula reads (the centred difference multiplied by a precomputed 1 / (2 dx) rather
+// than divided by 2 dx), the tile's terms reduced by a fixed tree and summed in tile order into
+// the CTA's partial.  Either energy differs from the oracle's evaluation by rounding only, well
+// inside the 1e-13 relative agreement the tests require; the states are identical.
 //
 // FP32: the stencil runs in FP32 and the energy keeps FP64 accuracy without per-cell FP64
 // arithmetic (GB300's FP64 pipe runs at 1/62 of the FP32 rate).  Each cell recomputes f1 at
@@ -128,6 +133,80 @@ __global__ void __launch_bounds__(kWaveThreads)
     }
 }
 
+// FP64 step with two cells per thread: 128-bit loads and stores of f and g (n even, arrays
+// 16-byte aligned).  The update formulas are evaluated exactly as in wave_step_kernel (the same
+// IEEE operations in the same order, so the states are identical); the neighbours' f1 come
+// from the adjacent lanes by warp shuffles (the warp's first and last lanes and the last pair
+// of the grid compute theirs from memory), so the loop has no barrier and evaluates each f1
+// once.  Energy: with D = f1[i+1] - f1[i-1] and G = g[i] + g1[i], E = K1 sum D^2 + K2 sum G^2
+// (K1 = c^2 dx / (8 dx^2), K2 = dx / 8), each thread keeping its two sums in FP64 by fused
+// multiply-adds in cell order; once per CTA they go through the fixed tree and are scaled.
+__global__ void __launch_bounds__(kWaveThreads)
+    wave_step_kernel_f64v(const double *__restrict__ f, const double *__restrict__ g,
+                          double *__restrict__ fo, double *__restrict__ go, long long n2,
+                          long long ntiles, double dt, double k, double k1, double k2,
+                          double *partial) {
+    __shared__ double s_d[kWaveThreads / 32], s_g[kWaveThreads / 32];
+    const double2 *f2 = reinterpret_cast<const double2 *>(f);
+    const double2 *g2 = reinterpret_cast<const double2 *>(g);
+    const long long n = 2 * n2;
+    const int lane = threadIdx.x & 31;
+    double sd = 0.0, sg = 0.0;  // this thread's sums of D^2 and G^2, cell order
+    // every thread of the CTA walks the same tiles, so the shuffles below are warp-uniform
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const long long q = tile * kWaveThreads + threadIdx.x;  // index of the cell pair
+        const bool active = q < n2;
+        double2 fv = make_double2(0.0, 0.0), gv = make_double2(0.0, 0.0);
+        if (active) {
+            fv = f2[q];
+            gv = g2[q];
+        }
+        const double f1a = fv.x + dt * gv.x;  // cells 2q, 2q + 1
+        const double f1b = fv.y + dt * gv.y;
+        double fl = __shfl_up_sync(0xffffffffu, f1b, 1);    // f1 of cell 2q - 1
+        double fr = __shfl_down_sync(0xffffffffu, f1a, 1);  // f1 of cell 2q + 2
+        if (!active) continue;
+        if (lane == 0) {
+            const long long l = q == 0 ? n - 1 : 2 * q - 1;
+            fl = f[l] + dt * g[l];
+        }
+        if (lane == 31 || q == n2 - 1) {
+            const long long r = q == n2 - 1 ? 0 : 2 * q + 2;
+            fr = f[r] + dt * g[r];
+        }
+        const double g1a = gv.x + k * (f1b + fl - 2.0 * f1a);
+        const double g1b = gv.y + k * (fr + f1a - 2.0 * f1b);
+        reinterpret_cast<double2 *>(fo)[q] = make_double2(f1a, f1b);
+        reinterpret_cast<double2 *>(go)[q] = make_double2(g1a, g1b);
+        const double da = f1b - fl, db = fr - f1a;
+        const double ga = gv.x + g1a, gb = gv.y + g1b;
+        sd = fma(da, da, sd);
+        sd = fma(db, db, sd);
+        sg = fma(ga, ga, sg);
+        sg = fma(gb, gb, sg);
+    }
+    // fixed-order tree: a butterfly within each warp, then the warp sums in warp order
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sd += __shfl_xor_sync(0xffffffffu, sd, o);
+        sg += __shfl_xor_sync(0xffffffffu, sg, o);
+    }
+    if (lane == 0) {
+        s_d[threadIdx.x >> 5] = sd;
+        s_g[threadIdx.x >> 5] = sg;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double td = 0.0, tg = 0.0;
+#pragma unroll
+        for (int w = 0; w < kWaveThreads / 32; ++w) {
+            td += s_d[w];
+            tg += s_g[w];
+        }
+        partial[blockIdx.x] = k1 * td + k2 * tg;
+    }
+}
+
 template <class T>
 __global__ void __launch_bounds__(kWaveThreads)
     wave_step_kernel(const T *__restrict__ f, const T *__restrict__ g, T *__restrict__ fo,
@@ -233,6 +312,13 @@ int wave_run_t(long long n, double c, double length, double dt, T *f, T *g, int 
                      reinterpret_cast<uintptr_t>(fb) % 16 == 0 && reinterpret_cast<uintptr_t>(gb) % 16 == 0;
     const long long vtiles = (n / 4 + kWaveThreads - 1) / kWaveThreads;
     const unsigned vblocks = (unsigned)(vtiles < L.nblocks ? vtiles : L.nblocks);
+    // FP64: two cells per thread where n is even and the arrays allow 128-bit accesses
+    const bool vec2 = sizeof(T) == 8 && n % 2 == 0 && reinterpret_cast<uintptr_t>(f) % 16 == 0 &&
+                      reinterpret_cast<uintptr_t>(g) % 16 == 0 && reinterpret_cast<uintptr_t>(fb) % 16 == 0 &&
+                      reinterpret_cast<uintptr_t>(gb) % 16 == 0;
+    const long long ptiles = (n / 2 + kWaveThreads - 1) / kWaveThreads;
+    const unsigned pblocks = (unsigned)(ptiles < L.nblocks ? ptiles : L.nblocks);
+    const int nparts = vec ? (int)vblocks : (vec2 ? (int)pblocks : (int)L.nblocks);
     for (int s = 0; s < n_steps; ++s) {
         if constexpr (sizeof(T) == 4) {
             if (vec)
@@ -241,11 +327,15 @@ int wave_run_t(long long n, double c, double length, double dt, T *f, T *g, int 
             else
                 wave_step_kernel_f32<<<(unsigned)L.nblocks, kWaveThreads, 0, st>>>(
                     fa, ga, fb, gb, n, L.ntiles, T(dt), k, k1, k2, part);
+        } else if (vec2) {
+            wave_step_kernel_f64v<<<pblocks, kWaveThreads, 0, st>>>(
+                reinterpret_cast<const double *>(fa), reinterpret_cast<const double *>(ga),
+                reinterpret_cast<double *>(fb), reinterpret_cast<double *>(gb), n / 2, ptiles,
+                (double)dt, (double)k, k1, k2, part);
         } else
             wave_step_kernel<T><<<(unsigned)L.nblocks, kWaveThreads, 0, st>>>(
                 fa, ga, fb, gb, n, L.ntiles, T(dt), k, c * c, dx, 1.0 / (2.0 * dx), part);
-        wave_energy_kernel<<<1, kWaveThreads, 0, st>>>(part, vec ? (int)vblocks : (int)L.nblocks,
-                                                       energy + s);
+        wave_energy_kernel<<<1, kWaveThreads, 0, st>>>(part, nparts, energy + s);
         T *t = fa;
         fa = fb;
         fb = t;

@@ -14,8 +14,11 @@ torch = pytest.importorskip("torch")
 C = 3.43
 
 
-@pytest.mark.parametrize("n", [8, 9, 256, 257, 3072])
+@pytest.mark.parametrize("n", [4, 8, 9, 66, 256, 257, 3072])
 def test_fp64_matches_oracle(n):
+    """Even N runs the two-cells-per-thread kernel (N = 4: two pairs, each the other's neighbour
+    on both sides; N = 66: a warp whose only pair is the grid's last), odd N the one-cell
+    kernel."""
     from paper_1204_4779_gb300 import hydro
     f0, g0 = W.initial(n)
     dx = 2 * math.pi / n
@@ -41,7 +44,7 @@ def test_energy_conserved_at_large_size():
     x = np.arange(n) * (2 * math.pi / n)
     f0, g0 = np.sin(x), np.cos(3 * x)
     dt = (2 * math.pi / n) / C
-    _, _, Eo = W.run(f0, g0, C, 2 * math.pi, dt, 200)
+    fo, go, Eo = W.run(f0, g0, C, 2 * math.pi, dt, 200)
     f, g = torch.from_numpy(f0).cuda(), torch.from_numpy(g0).cuda()
     E = np.array(hydro.wave_run(f, g, C, 2 * math.pi, dt, 200))
     drift_o = (Eo.max() - Eo.min()) / Eo.mean()
@@ -49,6 +52,33 @@ def test_energy_conserved_at_large_size():
     assert drift_o < 1e-11
     assert drift <= 10 * drift_o, (drift, drift_o)
     assert np.max(np.abs(E - Eo)) <= 1e-11 * Eo.mean()
+    # the states: every CTA walks several tiles at this size
+    assert np.array_equal(f.cpu().numpy(), fo)
+    assert np.array_equal(g.cpu().numpy(), go)
+
+
+@pytest.mark.parametrize("n", [3072, 1 << 20])
+def test_fp64_two_cell_kernel_equals_one_cell_kernel(n):
+    """The same even N through both FP64 kernels: arrays starting 8 bytes past a 16-byte
+    boundary cannot take 128-bit accesses and run the one-cell kernel.  The states are
+    identical (the same operations in the same order); the energies, summed in different
+    orders and groupings, agree to rounding."""
+    from paper_1204_4779_gb300 import hydro
+    x = np.arange(n) * (2 * math.pi / n)
+    f0, g0 = np.sin(x) + 0.25 * np.sin(5 * x), np.cos(3 * x)
+    dt = (2 * math.pi / n) / C
+    f, g = torch.from_numpy(f0).cuda(), torch.from_numpy(g0).cuda()
+    assert f.data_ptr() % 16 == 0 and g.data_ptr() % 16 == 0
+    Ev = np.array(hydro.wave_run(f, g, C, 2 * math.pi, dt, 101))
+    fb = torch.zeros(n + 1, dtype=torch.float64, device="cuda")
+    gb = torch.zeros(n + 1, dtype=torch.float64, device="cuda")
+    fs, gs = fb[1:], gb[1:]
+    assert fs.data_ptr() % 16 == 8
+    fs.copy_(torch.from_numpy(f0))
+    gs.copy_(torch.from_numpy(g0))
+    Es = np.array(hydro.wave_run(fs, gs, C, 2 * math.pi, dt, 101))
+    assert torch.equal(f, fs) and torch.equal(g, gs)
+    assert np.max(np.abs(Ev - Es)) <= 1e-13 * Es.mean()
 
 
 def _fp32_steps(f, g, dt, k, c2, dx, steps):
