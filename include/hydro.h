@@ -261,6 +261,22 @@ int hydro_step_host(hydro_ctx_t *ctx, const hydro_state_t *dev_state,
                     const void *const host_in[5], void *const host_out[5], int32_t n_steps,
                     double t_end, double *t_inout, int32_t *steps_done);
 
+/* hydro_step_host without waiting (no counterpart in the paper): the same copy in, steps and
+ * copy back, all enqueued on the context's stream (and its private copy stream), and the call
+ * returns.  t: time of the state in host_in (as *t_inout of hydro_step_host).  The host
+ * buffers must stay allocated, host_in unchanged and host_out unread until the context's
+ * stream has reached the end of the call (cudaStreamSynchronize on it, or hydro_status, which
+ * also returns the status of the steps).  All n_steps steps are launched (those after t_end or
+ * after a failed step return at once on the device).  Calls on one context run one after the
+ * other; calls on contexts with different streams overlap, so two problems in flight keep the
+ * CPU-GPU link busy in both directions (one problem's copy in during another's copy back).
+ * Setting up a copy of the control block from host memory may wait for the context's stream
+ * to finish its earlier work.  Errors: HYDRO_EINVAL (as hydro_step_host, or t or t_end NaN),
+ * HYDRO_ECUDA; a failed step is reported by the next synchronising call. */
+int hydro_step_host_async(hydro_ctx_t *ctx, const hydro_state_t *dev_state,
+                          const void *const host_in[5], void *const host_out[5],
+                          int32_t n_steps, double t_end, double t);
+
 /* dt = cfl / max_i sum_a (|v_a| + c_s)/dr_a of `state` (FP64 result).  Synchronises. */
 int hydro_cfl_dt(hydro_ctx_t *ctx, const hydro_state_t *state, double *dt_out);
 

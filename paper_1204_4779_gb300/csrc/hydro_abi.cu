@@ -907,16 +907,20 @@ static int copy_in_overlapped(hydro_ctx *c, const hydro_state_t *dev,
     return HYDRO_OK;
 }
 
-int hydro_step_host(hydro_ctx_t *c, const hydro_state_t *dev, const void *const host_in[5],
-                    void *const host_out[5], int32_t n_steps, double t_end, double *t_inout,
-                    int32_t *steps_done) {
+// hydro_step_host and hydro_step_host_async: the copy in, the steps and the copy back,
+// enqueued on the context's stream (and its private copy stream).  sync: stop launching once
+// no further step is to be taken, then wait for the stream and return the time, the steps
+// taken and the status; otherwise enqueue everything and return.
+static int step_host_impl(hydro_ctx_t *c, const hydro_state_t *dev, const void *const host_in[5],
+                          void *const host_out[5], int32_t n_steps, double t_end, double t,
+                          bool sync, double *t_out, int32_t *steps_done) {
     if (!c || !state_ok(c, dev) || !host_in || !host_out || n_steps < 0) return HYDRO_EINVAL;
+    if (t_end != t_end || t != t) return HYDRO_EINVAL;
     if (c->ana_axes && !c->ana_kind) return HYDRO_EINVAL;
     for (int k = 0; k < c->dim + 2; ++k)
         if (!host_in[k] || !host_out[k]) return HYDRO_EINVAL;
     DeviceGuard dg(c->device);
     const size_t bytes = (size_t)c->ncell * (c->prec == HYDRO_F32 ? 4 : 8);
-    double t = t_inout ? *t_inout : 0.0;
     int32_t done = 0;
     // dim 3 outside profiling: the copy in overlaps the CFL pass and the last step's stage 2
     // overlaps the copy back
@@ -929,16 +933,30 @@ int hydro_step_host(hydro_ctx_t *c, const hydro_state_t *dev, const void *const 
             CK(cudaMemcpyAsync(dev->plane[k], host_in[k], bytes, cudaMemcpyHostToDevice, c->stream));
         rc = begin_steps(c, dev, t, t_end);
     }
-    if (!rc) rc = run_steps(c, dev, overlap ? n_steps - 1 : n_steps, /*stop_early=*/true);
+    if (!rc) rc = run_steps(c, dev, overlap ? n_steps - 1 : n_steps, /*stop_early=*/sync);
     if (!rc && overlap) rc = last_step_overlapped(c, dev, host_out);
     if (rc) return rc;
     if (!overlap)
         for (int k = 0; k < c->dim + 2; ++k)
             CK(cudaMemcpyAsync(host_out[k], dev->plane[k], bytes, cudaMemcpyDeviceToHost, c->stream));
+    if (!sync) return HYDRO_OK;
     rc = finish_steps(c, &t, &done);
-    if (t_inout) *t_inout = t;
+    if (t_out) *t_out = t;
     if (steps_done) *steps_done = done;
     return rc;
+}
+
+int hydro_step_host(hydro_ctx_t *c, const hydro_state_t *dev, const void *const host_in[5],
+                    void *const host_out[5], int32_t n_steps, double t_end, double *t_inout,
+                    int32_t *steps_done) {
+    return step_host_impl(c, dev, host_in, host_out, n_steps, t_end, t_inout ? *t_inout : 0.0,
+                          /*sync=*/true, t_inout, steps_done);
+}
+
+int hydro_step_host_async(hydro_ctx_t *c, const hydro_state_t *dev, const void *const host_in[5],
+                          void *const host_out[5], int32_t n_steps, double t_end, double t) {
+    return step_host_impl(c, dev, host_in, host_out, n_steps, t_end, t, /*sync=*/false, nullptr,
+                          nullptr);
 }
 
 int hydro_cfl_dt(hydro_ctx_t *c, const hydro_state_t *state, double *dt_out) {

@@ -31,7 +31,7 @@ EXPORTS = (
     "hydro_workspace_bytes", "hydro_workspace_bytes_variant", "hydro_create", "hydro_get_variant",
     "hydro_destroy", "hydro_set_stream",
     "hydro_step",
-    "hydro_step_host", "hydro_set_scheme", "hydro_set_analytic", "hydro_analytic_state", "hydro_cfl_dt", "hydro_totals", "hydro_status", "hydro_prim_to_cons",
+    "hydro_step_host", "hydro_step_host_async", "hydro_set_scheme", "hydro_set_analytic", "hydro_analytic_state", "hydro_cfl_dt", "hydro_totals", "hydro_status", "hydro_prim_to_cons",
     "hydro_cons_to_prim", "hydro_set_profiling", "hydro_kernel_times", "hydro_step_static",
     "hydro_batch_workspace_bytes", "hydro_batch_create", "hydro_batch_destroy",
     "hydro_batch_offsets", "hydro_batch_set_stream", "hydro_batch_step", "hydro_batch_totals",
@@ -104,6 +104,7 @@ def load_library(path: str = LIB_PATH, build_if_missing: bool = True):
                                      ctypes.c_int),
             "hydro_step": ([vp, P(State), i32, dbl, P(dbl), P(i32)], ctypes.c_int),
             "hydro_step_host": ([vp, P(State), P(vp), P(vp), i32, dbl, P(dbl), P(i32)], ctypes.c_int),
+            "hydro_step_host_async": ([vp, P(State), P(vp), P(vp), i32, dbl, dbl], ctypes.c_int),
             "hydro_cfl_dt": ([vp, P(State), P(dbl)], ctypes.c_int),
             "hydro_totals": ([vp, P(State), P(dbl)], ctypes.c_int),
             "hydro_status": ([vp], ctypes.c_int),
@@ -342,6 +343,20 @@ class Solver:
                                         float(t_end), ctypes.byref(tt), ctypes.byref(done)),
                "hydro_step_host")
         return tt.value, done.value
+
+    def step_host_async(self, U_dev: torch.Tensor, host_in: torch.Tensor, host_out: torch.Tensor,
+                        n_steps: int, t_end: float = 0.0, t: float = 0.0):
+        """hydro_step_host_async: enqueue the copy in, the steps and the copy back on the current
+        torch stream and return; host_in and host_out stay untouched until that stream has
+        finished (status() waits for it)."""
+        self._sync_stream()
+        s = self._state(U_dev)
+        hi = state_struct(host_in, self.nv)
+        ho = state_struct(host_out, self.nv)
+        pin = (ctypes.c_void_p * 5)(*hi.plane)
+        pout = (ctypes.c_void_p * 5)(*ho.plane)
+        _check(self.lib.hydro_step_host_async(self.ctx, ctypes.byref(s), pin, pout, int(n_steps),
+                                              float(t_end), float(t)), "hydro_step_host_async")
 
     def cfl_dt(self, U: torch.Tensor) -> float:
         self._sync_stream()

@@ -92,6 +92,8 @@ def test_null_context_calls_fail_cleanly():
     lib = hydro.load_library()
     E = hydro.HYDRO_EINVAL
     assert lib.hydro_step(None, None, 1, 0.0, None, None) == E
+    assert lib.hydro_step_host(None, None, None, None, 1, 0.0, None, None) == E
+    assert lib.hydro_step_host_async(None, None, None, None, 1, 0.0, 0.0) == E
     assert lib.hydro_cfl_dt(None, None, None) == E
     assert lib.hydro_totals(None, None, None) == E
     assert lib.hydro_destroy(None) == E

@@ -231,6 +231,39 @@ def test_host_stepping_3d_overlapped_copy_back(n_steps, t_end, shape, bc, stagin
     assert torch.equal(dev, Ud)
 
 
+@pytest.mark.parametrize("shape,bc", [((40, 36, 100), (0, 0, 0)), ((96, 70), (0, 1))])
+def test_host_stepping_async_two_problems_in_flight(shape, bc):
+    """hydro_step_host_async on two contexts with their own streams, calls interleaved
+    (problem a's next copy in queued while b's step and copy back are in flight), each state
+    copied in and back in place every call: after three calls each host state equals three
+    one-step hydro_step calls on the device, bit for bit (3D: the overlapped slab path; 2D:
+    whole-plane copies)."""
+    Va = inputs.blast_3d(shape=shape, radius_cells=6.0) if len(shape) == 3 else \
+        inputs.kh_2d(shape[0], seed=3)[:, :shape[1], :].copy()
+    Vb = inputs.smooth(shape, seed=11)
+    Ua, Ub = gpu_state(Va, 1.4, F32), gpu_state(Vb, 1.4, F32)
+    var = dict(march=8) if len(shape) == 3 else None
+    ref = hydro.Solver(shape, 1.4, bc=list(bc), dtype=F32, variant=var)
+    Ra, Rb = Ua.clone(), Ub.clone()
+    for _ in range(3):
+        ref.step(Ra, 1)
+        ref.step(Rb, 1)
+    A = hydro.Solver(shape, 1.4, bc=list(bc), dtype=F32, variant=var)
+    B = hydro.Solver(shape, 1.4, bc=list(bc), dtype=F32, variant=var)
+    sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
+    ha, hb = Ua.cpu().pin_memory(), Ub.cpu().pin_memory()
+    da, db = torch.empty_like(Ua), torch.empty_like(Ub)
+    torch.cuda.synchronize()
+    for _ in range(3):
+        with torch.cuda.stream(sa):
+            A.step_host_async(da, ha, ha, 1)
+        with torch.cuda.stream(sb):
+            B.step_host_async(db, hb, hb, 1)
+    assert A.status() == 0 and B.status() == 0
+    assert torch.equal(ha, Ra.cpu()) and torch.equal(hb, Rb.cpu())
+    assert torch.equal(da, Ra) and torch.equal(db, Rb)
+
+
 def test_host_stepping_with_separate_host_planes():
     """Host planes in separate allocations (not one tensor): the copies go plane by plane
     instead of one strided copy per slab, with the same result."""
