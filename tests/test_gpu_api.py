@@ -264,6 +264,30 @@ def test_host_stepping_async_two_problems_in_flight(shape, bc):
     assert torch.equal(da, Ra) and torch.equal(db, Rb)
 
 
+def test_host_stepping_async_reports_status_and_clips_at_t_end():
+    """An asynchronous host step reports a failed step through the next synchronising call
+    (hydro_status), and with t_end it launches every step but stops advancing at t_end, as
+    hydro_step_host does."""
+    V = inputs.uniform((40, 36, 24), rho=1.0, v=(0.1, 0.0, 0.0), p=1.0)
+    U = gpu_state(V, 1.4, F32)
+    U[4, 3, 7, 11] = float("nan")
+    S = hydro.Solver((40, 36, 24), 1.4, dtype=F32, variant=dict(march=8))
+    h = U.cpu().pin_memory()
+    S.step_host_async(torch.empty_like(U), h, h, 2)
+    assert S.status() == hydro.HYDRO_ENONFINITE
+    Vb = inputs.blast_3d(shape=(40, 36, 24), radius_cells=5.0)
+    Ub = gpu_state(Vb, 1.4, F32)
+    Ud = Ub.clone()
+    td, nd = S.step(Ud, 50, t_end=0.003)
+    assert 1 < nd < 50
+    hb = Ub.cpu().pin_memory()
+    out = torch.full_like(hb, float("nan")).pin_memory()
+    dev = torch.empty_like(Ub)
+    S.step_host_async(dev, hb, out, 50, t_end=0.003)
+    assert S.status() == 0
+    assert torch.equal(out, Ud.cpu()) and torch.equal(dev, Ud)
+
+
 def test_host_stepping_with_separate_host_planes():
     """Host planes in separate allocations (not one tensor): the copies go plane by plane
     instead of one strided copy per slab, with the same result."""
