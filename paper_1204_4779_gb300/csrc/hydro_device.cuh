@@ -317,6 +317,11 @@ __device__ __forceinline__ int remap(int i, int n, int periodic) {
     if (periodic) i = i < 0 ? i + n : (i >= n ? i - n : i);
     return min(max(i, 0), n - 1);
 }
+// The same for an index known to be >= 0 (the planes ahead of a marching tile): only the
+// upper side can be outside, and the result equals remap(i, n, periodic).
+__device__ __forceinline__ int remap_ahead(int i, int n, int periodic) {
+    return min((periodic && i >= n) ? i - n : i, n - 1);
+}
 
 // ------------------------------------------------------------- dt finalisation ------------
 

@@ -616,6 +616,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int x0, int y0
     }
     __syncthreads();
 
+    // planes z + 1 ... z + 3 of the loop lie at or above 0: remap_ahead
     for (int z = zb; z < ze; ++z) {
         const bool odd = ((z - zb) & 1) != 0;
         T *const sVc = odd ? sV1 : sV0;
@@ -630,10 +631,10 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int x0, int y0
         }
         T Vnn[NV];
         if constexpr (MARCH && !TMA) {
-            if constexpr (PF == 0) load_u(pown, remap(z + 2, nz, pz), own_off);
+            if constexpr (PF == 0) load_u(pown, remap_ahead(z + 2, nz, pz), own_off);
             recover(pown, Vnn);  // V(z+2)
             if constexpr (PF == 1) {
-                if (z + 1 < ze) load_u(pown, remap(z + 3, nz, pz), own_off);
+                if (z + 1 < ze) load_u(pown, remap_ahead(z + 3, nz, pz), own_off);
             }
         }
 
@@ -653,7 +654,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int x0, int y0
 #pragma unroll
                     for (int k = 0; k < NV; ++k) u[k] = b[k * TB::cells + own_b];
                 } else {
-                    load_u(u, remap(z + 2, nz, pz), own_off);
+                    load_u(u, remap_ahead(z + 2, nz, pz), own_off);
                 }
                 recover(u, Vnn);
             }
@@ -664,7 +665,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int x0, int y0
                 if constexpr (PF == 0) {
 #pragma unroll
                     for (int j = 0; j < HPT; ++j)
-                        if (h_ok[j]) load_u(phalo[j], remap(z + 1, nz, pz), h_off[j]);
+                        if (h_ok[j]) load_u(phalo[j], remap_ahead(z + 1, nz, pz), h_off[j]);
                 }
                 if constexpr (TMA) {  // the halo of plane z+1 from its box
                     const float *b = wait_box(z + 1);
@@ -675,7 +676,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int x0, int y0
 #pragma unroll
                             for (int k = 0; k < NV; ++k) phalo[j][k] = b[k * TB::cells + h_b[j]];
                         } else {
-                            load_u(phalo[j], remap(z + 1, nz, pz), h_off[j]);
+                            load_u(phalo[j], remap_ahead(z + 1, nz, pz), h_off[j]);
                         }
                     }
                 }
@@ -683,7 +684,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int x0, int y0
                 if (PF == 1 && z + 2 < ze) {
 #pragma unroll
                     for (int j = 0; j < HPT; ++j)
-                        if (h_ok[j]) load_u(phalo[j], remap(z + 2, nz, pz), h_off[j]);
+                        if (h_ok[j]) load_u(phalo[j], remap_ahead(z + 2, nz, pz), h_off[j]);
                 }
             }
         }
