@@ -24,7 +24,7 @@ constexpr int kGraphSlots = 8;
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct BatchLayout {
-    size_t ctrl_off, t0_off, grids_off, items_off, sig_off, u1_off, plane_bytes, total;
+    size_t ctrl_off, t0_off, grids_off, items_off, sig_off, claim_off, u1_off, plane_bytes, total;
     long long ncell, n_items;
 };
 
@@ -74,7 +74,8 @@ BatchLayout batch_layout(int32_t n_grids, const int64_t *nx, const int64_t *ny, 
     L.grids_off = L.t0_off + align_up(sizeof(double) * (size_t)n_grids);
     L.items_off = L.grids_off + align_up(sizeof(BatchGrid) * (size_t)n_grids);
     L.sig_off = L.items_off + align_up(sizeof(BatchItem) * (size_t)L.n_items);
-    L.u1_off = L.sig_off + align_up(sizeof(double) * (size_t)L.n_items);
+    L.claim_off = L.sig_off + align_up(sizeof(double) * (size_t)L.n_items);
+    L.u1_off = L.claim_off + align_up(2 * sizeof(unsigned int));
     L.plane_bytes = align_up((size_t)L.ncell * esz);
     L.total = L.u1_off + 4 * L.plane_bytes;
     return L;
@@ -102,6 +103,7 @@ struct hydro_batch {
     BatchGrid *grids = nullptr;
     BatchItem *items = nullptr;
     void *tile_sig = nullptr;
+    unsigned int *claim = nullptr;
     void *u1[4] = {};
     double gamma = 1.4, cfl = 0.4;
     int periodic[2] = {1, 1};
@@ -141,6 +143,7 @@ BatchLaunch launch_args(const hydro_batch *b, const hydro_state_t *s, int kind, 
     L.n_grids = b->n_grids;
     L.ctrl = b->ctrl;
     L.tile_sig = b->tile_sig;
+    L.claim = b->claim;
     L.t0 = t0;
     L.t_end = t_end;
     L.cfl = b->cfl;
@@ -299,6 +302,7 @@ int hydro_batch_create(int32_t n_grids, const int64_t *nx, const int64_t *ny, do
     b->grids = reinterpret_cast<BatchGrid *>(b->ws + lay.grids_off);
     b->items = reinterpret_cast<BatchItem *>(b->ws + lay.items_off);
     b->tile_sig = b->ws + lay.sig_off;
+    b->claim = reinterpret_cast<unsigned int *>(b->ws + lay.claim_off);
     for (int k = 0; k < 4; ++k) b->u1[k] = b->ws + lay.u1_off + lay.plane_bytes * (size_t)k;
 
     // host tables: grid geometry and the (grid, tile) work list, grid by grid, row-major

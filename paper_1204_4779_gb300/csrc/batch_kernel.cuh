@@ -29,6 +29,7 @@ template <class T> struct BatchArgs {
     const BatchGrid *grids;
     Ctrl *ctrl;  // one per grid
     T *tile_sig;       // CFL-signal maximum of each work item (NaN: a bad cell)
+    unsigned int *claim;  // row kernels: next work item of stage 1 / stage 2, minus gridDim.x
     const double *t0;  // per-grid start time (init kernel), may be null
     double t_end, cfl;
     int periodic[2];
@@ -174,14 +175,25 @@ __global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY>::value))
 
 // Row tiles: a work item is a strip of BX columns of one grid and a chunk of `rows` rows,
 // advanced by the single-grid kernels' per-tile code (stage_tile) marching along y, with the
-// same per-tile CFL slot as the tile kernel above.
+// same per-tile CFL slot as the tile kernel above.  Items are claimed dynamically: CTA b takes
+// item b first, then the next unclaimed item from a counter (items differ in size -- ragged
+// strips and chunks, grids of 32 to 512 cells a side -- so a fixed stride leaves CTAs idle at
+// the end of the launch); items are still taken in list order, grid by grid.  Every item's
+// result and CFL slot are the same whichever CTA computes it.
 template <class T, int BX, int STAGE, int OCC>
 __global__ void __launch_bounds__(BX, (MinBlocks<T, BX, OCC>::value))
     batch_row_kernel(const BatchArgs<T> A) {
     using S = StageShape<T, 2, BX, 1>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *const sRed = reinterpret_cast<T *>(smem_raw) + 2 * S::NV * S::PL + 2 * S::NV * S::NF;
-    for (int it = blockIdx.x; it < A.n_items; it += gridDim.x) {
+    __shared__ int s_next;
+    auto claim_next = [&]() -> int {
+        __syncthreads();  // every thread has read the previous claim
+        if (threadIdx.x == 0) s_next = (int)gridDim.x + (int)atomicAdd(A.claim + (STAGE - 1), 1u);
+        __syncthreads();
+        return s_next;
+    };
+    for (int it = blockIdx.x; it < A.n_items; it = claim_next()) {
         const BatchItem W = A.items[it];
         const BatchGrid R = A.grids[W.g];
         Ctrl *ctrl = A.ctrl + W.g;
@@ -222,8 +234,9 @@ __global__ void __launch_bounds__(BX, (MinBlocks<T, BX, OCC>::value))
 
 // Per-grid start of a step call: control block of grid g reset, time t0[g] (or 0).
 static __global__ void batch_init_kernel(Ctrl *ctrl, const BatchGrid *grids, int n_grids,
-                                  const double *t0, double t_end, double cfl) {
+                                  const double *t0, double t_end, double cfl, unsigned int *claim) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g == 0 && claim) claim[0] = claim[1] = 0u;
     if (g >= n_grids) return;
     Ctrl z = {};
     z.t = t0 ? t0[g] : 0.0;
@@ -278,6 +291,9 @@ __global__ void __launch_bounds__(256) batch_finalize_kernel(const BatchArgs<T> 
     using U = typename std::conditional<sizeof(T) == 4, unsigned int, unsigned long long>::type;
     const int g = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
+    // the row kernels' work-item counters, for the next stage launches (this kernel runs after
+    // a step's stage 2 and before the next stage 1)
+    if (blockIdx.x == 0 && threadIdx.x == 0 && A.claim) A.claim[0] = A.claim[1] = 0u;
     if (g >= n_grids) return;
     const BatchGrid R = A.grids[g];
     U m = 0;
@@ -342,6 +358,7 @@ template <class T> BatchArgs<T> make_batch_args(const BatchLaunch &L) {
     A.grids = L.grids;
     A.ctrl = static_cast<Ctrl *>(L.ctrl);
     A.tile_sig = static_cast<T *>(L.tile_sig);
+    A.claim = L.claim;
     A.t0 = L.t0;
     A.t_end = L.t_end;
     A.cfl = L.cfl;
@@ -384,7 +401,7 @@ cudaError_t batch_dispatch_tile(const BatchLaunch &L, cudaStream_t st, int kind,
     }
     const BatchArgs<T> A = make_batch_args<T>(L);
     switch (kind) {
-        case 0: batch_init_kernel<<<(L.n_grids + 255) / 256, 256, 0, st>>>(A.ctrl, A.grids, L.n_grids, A.t0, A.t_end, A.cfl); break;
+        case 0: batch_init_kernel<<<(L.n_grids + 255) / 256, 256, 0, st>>>(A.ctrl, A.grids, L.n_grids, A.t0, A.t_end, A.cfl, A.claim); break;
         case 1: batch_cfl_kernel<T, BX, BY><<<L.n_blocks, S::NT, 0, st>>>(A); break;
         case 2: s1<<<L.n_blocks, S::NT, smem, st>>>(A); break;
         case 3: s2<<<L.n_blocks, S::NT, smem, st>>>(A); break;

@@ -132,6 +132,8 @@ struct BatchLaunch {
     int n_grids;
     void *ctrl;          // n_grids control blocks
     void *tile_sig;      // n_items CFL-signal maxima, one per work item (element type)
+    unsigned int *claim; // work-item counters of the row kernels' stages 1 and 2 (zero before
+                         // each stage launch: the init and finaliser kernels reset them)
     const double *t0;    // per-grid start times (init), may be null
     double t_end, cfl, gamma;
     int periodic[2];
