@@ -220,6 +220,7 @@ __global__ void __launch_bounds__(BX, (MinBlocks<T, BX, OCC>::value))
         V.gas = A.gas;
         V.ctrl = ctrl;
         V.ana = 0;  // the batch's grids are periodic or outflow
+        V.items = 0;
         __syncthreads();  // the previous item's last shared-memory reads are done
         T smax = T(0);
         bool bad = false;

@@ -33,11 +33,14 @@ struct Ctrl {
     unsigned int status;       // bit 0: non-finite / non-positive value seen
     int steps;              // steps completed since the CFL pass
     int clipped;            // the next step is clipped onto t_end
+    unsigned int claim;       // persistent stage launches: work items claimed beyond the first
+    unsigned int claim_done;  // CTAs of the current persistent launch that stopped claiming
     int pad;
     double totals[5];       // output of the totals reduction
     double dr[3];           // cell sizes (set by the host with t, t_end, cfl)
     double coef[2][3];      // (dt/2)/dr_a and dt/dr_a of the next step, for RK stages 1 and 2
 };
+static_assert(sizeof(Ctrl) <= 256, "the control block has 256 bytes in every workspace");
 
 enum : unsigned int {
     STATUS_NONFINITE = 1u,  // non-finite, rho <= 0 or p <= 0 seen

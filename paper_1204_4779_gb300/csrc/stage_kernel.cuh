@@ -52,6 +52,9 @@ template <class T> struct StageArgs {
                         // stage's time
     int ana;            // bit a set: axis a takes its ghost cells from the frame (one-plane
                         // tiles of dim 1 and 2 only)
+    int items;          // > 0: persistent launch over `items` (tile, march chunk) work items,
+                        // tiles_x x tiles_y tiles per chunk, x fastest; 0: one item per CTA
+    int tiles_x, tiles_y;
 };
 
 // Position of ghost cell (gx, gy) of an nx x ny grid (dim 1: ny = 1, gy = 0) in the frame ring
@@ -779,6 +782,54 @@ __global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY, OCC>::value))
     bool bad = false;
     constexpr bool CFL = STAGE == 2 && FUSED && MAN != 2;
     stage_tile<T, D, BX, BY, STAGE, PF, CFL, MAN>(A, x0, y0, zb, ze, smem_raw, cx, cy, cz, smax, bad);
+    if constexpr (CFL) reduce_signal_and_finalize<T, S::NT>(ctrl, smax, bad, true, sRed);
+}
+
+// The same stage over a persistent grid of resident CTAs (marching tiles, nothing manifest):
+// A.items work items (tile, march chunk), A.tiles_x x A.tiles_y tiles per chunk, x fastest.
+// CTA b takes item b, then claims the next unclaimed item from the control block's counter
+// until none is left, so the last wave of a launch with few items per SM does not leave SMs
+// idle.  The last CTA to stop claiming resets the counters for the next launch on the same
+// control block.  Used where the items make only a few waves of CTAs (the row tiles of 2D
+// grids): over many waves the hardware's own scheduling loses nothing and the claiming loop
+// costs instructions.
+template <class T, int D, int BX, int BY, int STAGE, int PF, bool FUSED = true, int OCC = 2>
+__global__ void __launch_bounds__(BX * BY, (MinBlocks<T, BX * BY, OCC>::value))
+    stage_kernel_persistent(const StageArgs<T> A) {
+    using S = StageShape<T, D, BX, BY>;
+    using GM = Geom<D, BY>;
+    static_assert(GM::march, "persistent launches are compiled for marching tiles");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *const sRed = reinterpret_cast<T *>(smem_raw) + 2 * S::NV * S::PL + 2 * S::NV * S::NF;
+    __shared__ int s_item;
+
+    Ctrl *ctrl = A.ctrl;
+    const double dt = __ldcg(&ctrl->dt);
+    if (!(dt > 0.0)) return;  // uniform over the grid: no step to take (and nothing claimed)
+    const T cx = T(__ldcg(&ctrl->coef[STAGE - 1][0]));
+    const T cy = (GM::IN >= 2) ? T(__ldcg(&ctrl->coef[STAGE - 1][1])) : T(0);
+    const T cz = T(__ldcg(&ctrl->coef[STAGE - 1][GM::MA]));
+    T smax = T(0);
+    bool bad = false;
+    constexpr bool CFL = STAGE == 2 && FUSED;
+    for (int item = (int)blockIdx.x; item < A.items;) {
+        const int ix = item % A.tiles_x;
+        const int r = item / A.tiles_x;
+        const int x0 = ix * BX;
+        const int y0 = (GM::IN >= 2) ? (r % A.tiles_y) * BY : 0;
+        const int zb = (r / A.tiles_y + A.zchunk0) * A.march;
+        const int ze = min(zb + A.march, A.n[GM::MA]);
+        stage_tile<T, D, BX, BY, STAGE, PF, CFL, 0>(A, x0, y0, zb, ze, smem_raw, cx, cy, cz, smax,
+                                                    bad);
+        __syncthreads();  // the tile's last shared-memory reads are done; s_item is free
+        if (threadIdx.x == 0) s_item = (int)gridDim.x + (int)atomicAdd(&ctrl->claim, 1u);
+        __syncthreads();
+        item = s_item;
+    }
+    if (threadIdx.x == 0 && atomicAdd(&ctrl->claim_done, 1u) == gridDim.x - 1) {
+        atomicExch(&ctrl->claim, 0u);
+        atomicExch(&ctrl->claim_done, 0u);
+    }
     if constexpr (CFL) reduce_signal_and_finalize<T, S::NT>(ctrl, smax, bad, true, sRed);
 }
 

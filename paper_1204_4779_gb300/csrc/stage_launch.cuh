@@ -30,6 +30,8 @@ template <class T> static StageArgs<T> make_stage_args(const StageLaunch &L) {
     A.ctrl = static_cast<Ctrl *>(L.ctrl);
     A.ana = L.ana;
     for (int k = 0; k < 5; ++k) A.frame[k] = static_cast<const T *>(L.frame[k]);
+    A.items = 0;
+    A.tiles_x = A.tiles_y = 0;
     return A;
 }
 
@@ -41,6 +43,27 @@ template <class T, int D, int BX, int BY, int PF, int OCC, int MAN = 0> struct S
     static constexpr auto s2 = stage_kernel<T, D, BX, BY, 2, PF, true, OCC, MAN>;
     static constexpr auto s2_split = stage_kernel<T, D, BX, BY, 2, PF, false, OCC, MAN>;
 };
+// Their persistent forms (2D row tiles).
+template <class T, int D, int BX, int BY, int PF, int OCC> struct PersistentKernels {
+    static constexpr auto s1 = stage_kernel_persistent<T, D, BX, BY, 1, PF, true, OCC>;
+    static constexpr auto s2 = stage_kernel_persistent<T, D, BX, BY, 2, PF, true, OCC>;
+    static constexpr auto s2_split = stage_kernel_persistent<T, D, BX, BY, 2, PF, false, OCC>;
+};
+
+// CTAs of each persistent stage kernel that the whole GPU holds at once (SMs x resident CTAs
+// per SM), measured when the kernels are prepared; 0 = unknown (the one-item-per-CTA kernels
+// run then).
+template <class T, int D, int BX, int BY, int PF, int OCC> struct ResidentCtas {
+    static inline int s1 = 0, s2 = 0, s2_split = 0;
+};
+
+template <class F> static int resident_ctas(F kernel, int nt, size_t smem) {
+    int dev = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, nt, smem) != cudaSuccess) return 0;
+    return sms * per;
+}
 
 // Grid of a manifest pass: enough CTAs to fill every SM several times.
 inline unsigned pass_blocks(long long ncell) {
@@ -82,6 +105,27 @@ static cudaError_t launch_stage_pf(const StageLaunch &L, const StageArgs<T> &A0,
             addflux_kernel<T, 2, true><<<pass_blocks(ncell), kPassThreads, 0, st>>>(A);
         return cudaGetLastError();
     } else {
+        // 2D row tiles with more work items than resident CTAs: a persistent grid of the
+        // resident CTAs claims the items (stage_kernel_persistent)
+        if constexpr (GM::rows && MAN == 0) {
+            using R = ResidentCtas<T, D, BX, BY, PF, OCC>;
+            using P = PersistentKernels<T, D, BX, BY, PF, OCC>;
+            const int slots = L.stage == 1 ? R::s1 : (L.split ? R::s2_split : R::s2);
+            const long long items = (long long)grid.x * grid.y * grid.z;
+            if (slots > 0 && items > slots && items < (1LL << 31)) {
+                A.items = (int)items;
+                A.tiles_x = (int)grid.x;
+                A.tiles_y = (int)grid.y;
+                const dim3 g((unsigned)slots);
+                if (L.stage == 1)
+                    P::s1<<<g, S::NT, smem, st>>>(A);
+                else if (L.split)
+                    P::s2_split<<<g, S::NT, smem, st>>>(A);
+                else
+                    P::s2<<<g, S::NT, smem, st>>>(A);
+                return cudaGetLastError();
+            }
+        }
         if (L.stage == 1)
             K::s1<<<grid, S::NT, smem, st>>>(A);
         else if (L.split)
@@ -102,6 +146,22 @@ static cudaError_t prepare_stage_pf() {
             e = cudaFuncSetAttribute(K::s2, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(K::s2_split, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    }
+    if constexpr (Geom<D, BY>::rows && MAN == 0) {
+        using P = PersistentKernels<T, D, BX, BY, PF, OCC>;
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(P::s1, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(P::s2, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(P::s2_split, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess) {
+            using R = ResidentCtas<T, D, BX, BY, PF, OCC>;
+            constexpr int nt = StageShape<T, D, BX, BY>::NT;
+            R::s1 = resident_ctas(P::s1, nt, (size_t)smem);
+            R::s2 = resident_ctas(P::s2, nt, (size_t)smem);
+            R::s2_split = resident_ctas(P::s2_split, nt, (size_t)smem);
+        }
     }
     return e;
 }
