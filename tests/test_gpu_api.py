@@ -326,7 +326,7 @@ def test_resolved_default_variants():
     """hydro_get_variant: the library defaults per dimension and precision, and the defaults a
     variant that names another tile gets (that tile's march and register budget)."""
     cases = [
-        ((40, 36, 30), F32, None, dict(tile=(16, 8), march=30, split=2, staging=1, occupancy=3)),
+        ((40, 36, 30), F32, None, dict(tile=(16, 8), march=8, split=2, staging=1, occupancy=3)),
         ((40, 36, 100), F64, None, dict(tile=(32, 8), march=64, split=2, staging=1, occupancy=2)),
         ((300, 77), F32, None, dict(tile=(256, 1), march=16, split=2, staging=1, occupancy=3)),
         ((300, 77), F64, None, dict(tile=(32, 8), march=1, split=1, staging=1, occupancy=2)),
@@ -335,14 +335,30 @@ def test_resolved_default_variants():
                                                   occupancy=2)),
         ((300, 77), F32, dict(tile=(64, 1)), dict(tile=(64, 1), march=16, split=2, staging=1,
                                                   occupancy=2)),
-        ((40, 36, 100), F32, dict(tile=(32, 8)), dict(tile=(32, 8), march=64, split=2, staging=1,
+        ((40, 36, 100), F32, dict(tile=(32, 8)), dict(tile=(32, 8), march=8, split=2, staging=1,
                                                       occupancy=3)),
+        ((40, 36, 100), F32, dict(march=20), dict(tile=(16, 8), march=20, split=2, staging=1,
+                                                  occupancy=3)),
     ]
     for shape, dt, var, want in cases:
         S = hydro.Solver(shape, 1.4, dtype=dt, variant=var)
         got = S.variant()
         S.close()
         assert got == dict(want, manifest=1), (shape, dt, var, got)
+
+
+@pytest.mark.parametrize("n,march", [(512, 64), (384, 32), (256, 16), (192, 16), (128, 8)])
+def test_default_march_follows_the_grid_size(n, march):
+    """3D FP32 without a named march: the largest of 64, 32, 16, 8 whose (tile, chunk) work
+    items fill the GPU's resident CTAs (152 SMs x six 128-thread CTAs on GB300) at least 8
+    times, else 3.5 times, else 8."""
+    props = torch.cuda.get_device_properties(0)
+    if props.multi_processor_count != 152:
+        pytest.skip("the expected marches are those of a 152-SM GPU")
+    S = hydro.Solver((n, n, n), 1.4, dtype=F32)
+    got = S.variant()["march"]
+    S.close()
+    assert got == march
 
 
 def test_host_stepping_with_a_manifest_form():
