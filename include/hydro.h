@@ -96,9 +96,9 @@ typedef struct {
  *   march:          marching tiles only (dim 3, dim-2 row tiles): planes one CTA marches
  *                   through (>= 1), i.e. the cells each thread updates per stage; 0 = default
  *                   (16 for row tiles; in dim 3 FP32 chosen by hydro_create from the grid:
- *                   the largest of 64, 32, 16, 8 whose (tile, chunk) work items fill the
- *                   GPU's resident CTAs at least 8 times, else 3.5 times, else 8; 64 in dim 3
- *                   FP64).
+ *                   among 8, 16, 32, 48, ..., 128 the marches whose (tile, chunk) work items
+ *                   fill the GPU's resident CTAs three times, the one with the least
+ *                   0.5 x chunks + 0.3 x planes of the last chunk, else 8; 64 in dim 3 FP64).
  *   split:          fusion split.  0 = library default (fused for marching tiles, separate
  *                   for one-plane tiles); 1 = a separate CFL pass after RK stage 2 (one more
  *                   launch and one more read of the state per step); 2 = the CFL signal and
@@ -128,8 +128,8 @@ typedef struct {
  *                   16 x 8, 32 x 8, 16 x 16; FP64 32 x 8), with look-ahead staging and the
  *                   precision's default budget; 2 and 3 need more workspace
  *                   (hydro_workspace_bytes_variant).
- * Library defaults (measured on GB300): dim 3 FP32 tile 16 x 8 (march from the grid size, 64
- * for large grids), FP64 32 x 8, march 64; dim 2 FP32 row tile 256 x 1, march 16; dim 2 FP64
+ * Library defaults (measured on GB300): dim 3 FP32 tile 16 x 8 (march from the grid size: 96
+ * at 512^3), FP64 32 x 8, march 64; dim 2 FP32 row tile 256 x 1, march 16; dim 2 FP64
  * tile 32 x 8; dim 1 tile 128.  A variant that names a tile other than the default gets that
  * tile's default march (as above in dim 3, 16 for row tiles) and budget unless it names them
  * too.

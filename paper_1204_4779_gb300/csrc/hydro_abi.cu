@@ -176,24 +176,35 @@ void default_variant(int prec, int dim, hydro_variant_t *v) {
     }
 }
 
-// Default march of a 3D FP32 grid (a variant that names no march): each CTA advances one tile
-// through `march` planes after a prologue of four, and a launch's (tile, chunk) work items
-// should fill the GPU's resident CTAs many times over, so that the last wave leaves few SMs
-// idle.  The largest march of 64, 32, 16, 8 that gives at least 8 waves of items; else the
-// largest giving 3.5 waves; else 8.  Measured on GB300 (blast on grids of n^3 cells, G
-// cell-updates/s, chosen march marked): 512: 23.17 (64*) 23.08 (32); 384: 22.63 (64) 22.87
-// (32*); 320: 21.95 (64) 22.49 (32*); 256: 20.63 (64) 21.99 (32) 21.90 (16*); 192: 18.84 (64)
-// 20.60 (16*) 20.11 (8); 128: 11.56 (64) 15.74 (16) 17.41 (8*); 96: 5.59 (64) 14.22 (8*).
+// Default march of a 3D FP32 grid (a variant that names no march).  A CTA advances one tile
+// through `march` planes after a short prologue; the launch's (tile, chunk) work items run in
+// order, chunk by chunk, so the last chunk's items (shorter where the march does not divide
+// the extent) finish the launch.  Among marches 8, 16, 32, ..., 128 whose items fill the GPU's
+// resident CTAs at least three times, the one with the least modelled overhead: 0.5 plane per
+// chunk (the prologue) plus 0.3 times the last chunk's planes (the launch's tail); 8 when none
+// fills them three times.  The weights were fitted to blast runs on GB300 (marches 16-128, n =
+// 256 ... 640); G cell-updates/s, the chosen march marked: 512^3 23.14 (64) 23.29 (80) 23.32
+// (96*); 448^3 22.90 (64) 23.25 (48*); 384^3 22.62 (64) 22.87 (32*); 256^3 20.56 (64) 21.85
+// (16) 22.08 (48*); 128^3 11.56 (64) 15.74 (16) 17.41 (8*).
 int default_march_3d(const int64_t n[3], const hydro_variant_t &v, int sm_count) {
     const long long tiles = ((n[0] + v.tile_x - 1) / v.tile_x) * ((n[1] + v.tile_y - 1) / v.tile_y);
     int per_sm = v.occupancy * 256 / (v.tile_x * v.tile_y);
     if (per_sm < 1) per_sm = 1;
     const double slots = (double)(sm_count > 0 ? sm_count : 1) * per_sm;
-    static const int kMarch[4] = {64, 32, 16, 8};
-    for (double need : {8.0, 3.5})
-        for (int m : kMarch)
-            if ((double)tiles * (double)((n[2] + m - 1) / m) >= need * slots) return m;
-    return 8;
+    static const int kMarch[] = {8, 16, 32, 48, 64, 80, 96, 112, 128};
+    int best = 0;
+    double best_cost = 0.0;
+    for (int m : kMarch) {
+        const long long chunks = (n[2] + m - 1) / m;
+        if ((double)tiles * (double)chunks < 3.0 * slots) continue;
+        const long long last = n[2] - (chunks - 1) * m;
+        const double cost = 0.5 * (double)chunks + 0.3 * (double)last;
+        if (best == 0 || cost < best_cost) {
+            best = m;
+            best_cost = cost;
+        }
+    }
+    return best ? best : 8;
 }
 
 // Resolve a (possibly partial) variant against the defaults; false if not compiled.

@@ -347,11 +347,12 @@ def test_resolved_default_variants():
         assert got == dict(want, manifest=1), (shape, dt, var, got)
 
 
-@pytest.mark.parametrize("n,march", [(512, 64), (384, 32), (256, 16), (192, 16), (128, 8)])
+@pytest.mark.parametrize("n,march", [(512, 96), (448, 48), (384, 32), (256, 48), (192, 16),
+                                     (128, 8)])
 def test_default_march_follows_the_grid_size(n, march):
-    """3D FP32 without a named march: the largest of 64, 32, 16, 8 whose (tile, chunk) work
-    items fill the GPU's resident CTAs (152 SMs x six 128-thread CTAs on GB300) at least 8
-    times, else 3.5 times, else 8."""
+    """3D FP32 without a named march: among 8, 16, 32, ..., 128 the marches whose (tile, chunk)
+    work items fill the GPU's resident CTAs (152 SMs x six 128-thread CTAs on GB300) three
+    times, the one with the least 0.5 x chunks + 0.3 x (planes of the last chunk); else 8."""
     props = torch.cuda.get_device_properties(0)
     if props.multi_processor_count != 152:
         pytest.skip("the expected marches are those of a 152-SM GPU")
