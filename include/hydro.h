@@ -95,10 +95,11 @@ typedef struct {
  *                   are compiled is answered by hydro_variant_supported().
  *   march:          marching tiles only (dim 3, dim-2 row tiles): planes one CTA marches
  *                   through (>= 1), i.e. the cells each thread updates per stage; 0 = default
- *                   (16 for row tiles; in dim 3 FP32 chosen by hydro_create from the grid:
- *                   among 8, 16, 32, 48, ..., 128 the marches whose (tile, chunk) work items
- *                   fill the GPU's resident CTAs three times, the one with the least
- *                   0.5 x chunks + 0.3 x planes of the last chunk, else 8; 64 in dim 3 FP64).
+ *                   (FP32: chosen by hydro_create from the grid: among 8, 16, 32, 48, ...,
+ *                   128 in dim 3 (8, 16, 32, 64, 128 for row tiles) the marches whose
+ *                   (tile, chunk) work items fill the GPU's resident CTAs three times (row
+ *                   tiles: twice), the one with the least 0.5 x chunks + 0.3 x planes of the
+ *                   last chunk, else 8 (row tiles: 16); FP64: 64 in dim 3, 16 for row tiles).
  *   split:          fusion split.  0 = library default (fused for marching tiles, separate
  *                   for one-plane tiles); 1 = a separate CFL pass after RK stage 2 (one more
  *                   launch and one more read of the state per step); 2 = the CFL signal and
@@ -129,8 +130,8 @@ typedef struct {
  *                   precision's default budget; 2 and 3 need more workspace
  *                   (hydro_workspace_bytes_variant).
  * Library defaults (measured on GB300): dim 3 FP32 tile 16 x 8 (march from the grid size: 96
- * at 512^3), FP64 32 x 8, march 64; dim 2 FP32 row tile 256 x 1, march 16; dim 2 FP64
- * tile 32 x 8; dim 1 tile 128.  A variant that names a tile other than the default gets that
+ * at 512^3), FP64 32 x 8, march 64; dim 2 FP32 row tile 256 x 1 (march from the grid size: 16
+ * at 2048^2, 64 at 4096^2); dim 2 FP64 tile 32 x 8; dim 1 tile 128.  A variant that names a tile other than the default gets that
  * tile's default march (as above in dim 3, 16 for row tiles) and budget unless it names them
  * too.
  * Every variant computes the same step; they differ in speed only. */

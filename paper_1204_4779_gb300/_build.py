@@ -91,6 +91,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
     with cf.ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
         objs = list(ex.map(lambda u: _compile(u, force, verbose), UNITS))
+    # objects of earlier sources or flags are never linked again: drop them
+    keep = {os.path.basename(o) for o in objs}
+    for name in os.listdir(OUT_DIR):
+        if name.endswith(".o") and name not in keep:
+            try:
+                os.remove(os.path.join(OUT_DIR, name))
+            except OSError:
+                pass
     stamp = os.path.join(OUT_DIR, "lib.stamp")
     key = "|".join(objs)
     if not force and os.path.exists(LIB) and os.path.exists(stamp) and open(stamp).read() == key:

@@ -186,25 +186,49 @@ void default_variant(int prec, int dim, hydro_variant_t *v) {
 // 256 ... 640); G cell-updates/s, the chosen march marked: 512^3 23.14 (64) 23.29 (80) 23.32
 // (96*); 448^3 22.90 (64) 23.25 (48*); 384^3 22.62 (64) 22.87 (32*); 256^3 20.56 (64) 21.85
 // (16) 22.08 (48*); 128^3 11.56 (64) 15.74 (16) 17.41 (8*).
-int default_march_3d(const int64_t n[3], const hydro_variant_t &v, int sm_count) {
-    const long long tiles = ((n[0] + v.tile_x - 1) / v.tile_x) * ((n[1] + v.tile_y - 1) / v.tile_y);
-    int per_sm = v.occupancy * 256 / (v.tile_x * v.tile_y);
-    if (per_sm < 1) per_sm = 1;
-    const double slots = (double)(sm_count > 0 ? sm_count : 1) * per_sm;
-    static const int kMarch[] = {8, 16, 32, 48, 64, 80, 96, 112, 128};
+// The march of `tiles` tiles marching through `extent` planes: among `marches` those whose
+// work items fill `slots` resident CTAs `waves` times, the one with the least
+// 0.5 chunks + 0.3 (planes of the last chunk); `fallback` when none does.
+static int choose_march(long long tiles, long long extent, double slots, double waves,
+                        const int *marches, int n_marches, int fallback) {
     int best = 0;
     double best_cost = 0.0;
-    for (int m : kMarch) {
-        const long long chunks = (n[2] + m - 1) / m;
-        if ((double)tiles * (double)chunks < 3.0 * slots) continue;
-        const long long last = n[2] - (chunks - 1) * m;
+    for (int i = 0; i < n_marches; ++i) {
+        const int m = marches[i];
+        const long long chunks = (extent + m - 1) / m;
+        if ((double)tiles * (double)chunks < waves * slots) continue;
+        const long long last = extent - (chunks - 1) * m;
         const double cost = 0.5 * (double)chunks + 0.3 * (double)last;
         if (best == 0 || cost < best_cost) {
             best = m;
             best_cost = cost;
         }
     }
-    return best ? best : 8;
+    return best ? best : fallback;
+}
+
+static double resident_slots(const hydro_variant_t &v, int sm_count) {
+    int per_sm = v.occupancy * 256 / (v.tile_x * v.tile_y);
+    if (per_sm < 1) per_sm = 1;
+    return (double)(sm_count > 0 ? sm_count : 1) * per_sm;
+}
+
+int default_march_3d(const int64_t n[3], const hydro_variant_t &v, int sm_count) {
+    static const int kMarch[] = {8, 16, 32, 48, 64, 80, 96, 112, 128};
+    const long long tiles = ((n[0] + v.tile_x - 1) / v.tile_x) * ((n[1] + v.tile_y - 1) / v.tile_y);
+    return choose_march(tiles, n[2], resident_slots(v, sm_count), 3.0, kMarch, 9, 8);
+}
+
+// Default march of the 2D FP32 row tiles (a variant that names no march), with the same cost
+// and marches 8, 16, 32, 64, 128 whose items fill the resident CTAs twice (launches of more
+// items than resident CTAs run persistently, so a short last wave costs little); 16 when none
+// does.  Measured on GB300 (shear layer, tile 256 x 1, G cell-updates/s, marches 8 / 16 / 32 /
+// 64, chosen marked): 4096^2 32.3 / 34.3 / 34.0 / 35.6*; 2048^2 28.4 / 30.2* / 25.6 / 24.9;
+// 1024^2 (no march fills them twice) 19.5 / 20.4* / 15.5 / -.
+int default_march_rows(const int64_t n[3], const hydro_variant_t &v, int sm_count) {
+    static const int kMarch[] = {8, 16, 32, 64, 128};
+    const long long strips = (n[0] + v.tile_x - 1) / v.tile_x;
+    return choose_march(strips, n[1], resident_slots(v, sm_count), 2.0, kMarch, 5, 16);
 }
 
 // Resolve a (possibly partial) variant against the defaults; false if not compiled.
@@ -658,11 +682,13 @@ int hydro_create(const hydro_grid_t *grid, double gamma, const int32_t bc[3], in
         if (hydro::frame_cells(grid->dim, grid->n[0], grid->dim >= 2 ? grid->n[1] : 1) >= (1LL << 31))
             return HYDRO_EUNSUPPORTED;  // the ring's int indices
     }
-    if (grid->dim == 3 && prec == HYDRO_F32 && !(variant && variant->march)) {
+    const bool rows = grid->dim == 2 && var.tile_y == 1;
+    if ((grid->dim == 3 || rows) && prec == HYDRO_F32 && !(variant && variant->march)) {
         int dev = 0, sms = 0;
         if (cudaGetDevice(&dev) == cudaSuccess &&
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
-            var.march = default_march_3d(grid->n, var, sms);
+            var.march = rows ? default_march_rows(grid->n, var, sms)
+                             : default_march_3d(grid->n, var, sms);
     }
     const Layout lay = layout_for(grid->dim, grid->n, ncell, prec, var.manifest);
     if (workspace_bytes < lay.total) return HYDRO_EINVAL;

@@ -362,6 +362,20 @@ def test_default_march_follows_the_grid_size(n, march):
     assert got == march
 
 
+@pytest.mark.parametrize("n,march", [(4096, 64), (2048, 16), (1024, 16)])
+def test_default_row_march_follows_the_grid_size(n, march):
+    """2D FP32 row tiles without a named march: among 8, 16, 32, 64, 128 the marches whose work
+    items fill the resident CTAs (152 SMs x three 256-thread CTAs) twice, the one with the
+    least 0.5 x chunks + 0.3 x (rows of the last chunk); else 16."""
+    props = torch.cuda.get_device_properties(0)
+    if props.multi_processor_count != 152:
+        pytest.skip("the expected marches are those of a 152-SM GPU")
+    S = hydro.Solver((n, n), 5.0 / 3.0, dtype=F32)
+    got = S.variant()
+    S.close()
+    assert got["tile"] == (256, 1) and got["march"] == march
+
+
 def test_host_stepping_with_a_manifest_form():
     V = inputs.blast_3d(shape=(40, 36, 30), radius_cells=6.0)
     U = gpu_state(V, 1.4, F32)
